@@ -1,0 +1,514 @@
+"""CPU oracle for exact critical-point tracking on the simplicial spacetime mesh.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the product path.  It
+shares no code with the CUDA path (the only common module is the seeded
+field sampler ``paper_2011_08697_gb300.synth``, which holds no arithmetic of
+the method).
+
+Plain, slow, step-by-step statement of the method (paper Sec. 3.3, Sec. 4):
+
+1. quantise     F = rint(f * 2^S) (round half to even), FP64       (Sec. 4.3)
+2. gradient     G_a = F[i+1] - F[i-1]; boundary 2(F[1]-F[0]),
+                2(F[N-1]-F[N-2]); each time slice on its own        (Sec. 4.3, 4.7)
+3. mesh         Kuhn/Freudenthal subdivision of each unit (n+1)-cube
+                (Sec. 3.3): a k-simplex is a base vertex plus a chain
+                0 < m_1 < ... < m_k of axis bitmasks
+4. predicate    SoS point-in-simplex test, C core ``ftk_oracle.c``  (Sec. 4.3, Eq. 1)
+5. location     mu_k = D_k / D from Eq. (1) in FP64 (exact D_k)
+6. type         Morse index of the barycentrically weighted,
+                symmetrised finite-difference Hessian, exact ints  (Sec. 4.1, Sec. 7)
+7. linking      union the punctured faces of every spacetime cell
+                (Algorithm 1, left column), label = min face id
+8. streaming    ordinal faces at t=k and interval faces of slab
+                [k-1, k] become known when slice k arrives          (Sec. 3.2)
+
+Readings where the paper is silent (each listed in the design notes):
+the SoS exponent order eps^(2^(g*n+r)); quantise-then-difference; the
+one-sided boundary rule; the Hessian-based classification; centroid location
+for a fully degenerate puncture.
+
+Every function here is pinned by ``tests/test_oracle_*.py`` against closed
+forms, exact rational arithmetic, brute force or the paper's printed tables.
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import os
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(HERE, "libftk_oracle.so")
+_SRC = os.path.join(HERE, "ftk_oracle.c")
+
+RANGE_LIMIT = 1 << 28   # |F| must not exceed 2^28, so |G|, |H| <= 2^30 / 2^31
+
+
+class OracleRangeError(ValueError):
+    pass
+
+
+# ----------------------------------------------------------------------------
+# C core loader
+# ----------------------------------------------------------------------------
+_lib = None
+
+
+def build_clib(force: bool = False) -> str:
+    """Compile ftk_oracle.c into libftk_oracle.so next to it (gcc, -O2)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", _SO])
+    return _SO
+
+
+def clib():
+    global _lib
+    if _lib is None:
+        build_clib()
+        lib = ctypes.CDLL(_SO)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i8p = ctypes.POINTER(ctypes.c_int8)
+        lib.oracle_sos_det_sign.argtypes = [ctypes.c_int, i64p]
+        lib.oracle_sos_det_sign.restype = ctypes.c_int
+        lib.oracle_face_punctured.argtypes = [ctypes.c_int, i64p]
+        lib.oracle_face_punctured.restype = ctypes.c_int
+        lib.oracle_scan.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, i32p,
+                                    ctypes.c_int64, ctypes.c_int64, i64p, ctypes.c_int64]
+        lib.oracle_scan.restype = ctypes.c_int64
+        lib.oracle_test_faces.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, i32p,
+                                          i64p, ctypes.c_int64, i8p]
+        lib.oracle_test_faces.restype = None
+        _lib = lib
+    return _lib
+
+
+def _p64(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+# ----------------------------------------------------------------------------
+# 3. Mesh (Sec. 3.3): chains of axis bitmasks
+# ----------------------------------------------------------------------------
+def chains(d: int, k: int):
+    """All chains 0 < m_1 < m_2 < ... < m_k <= full of nonempty nested axis
+    subsets of {0..d-1}, as tuples of bitmasks, in lexicographic order.
+
+    A k-simplex of the subdivided unit d-cube with base vertex v has vertices
+    v, v + bits(m_1), ..., v + bits(m_k); the type id of a simplex is the
+    index of its chain in this list.
+    """
+    full = (1 << d) - 1
+    out = []
+    for combo in itertools.product(range(1, full + 1), repeat=k):
+        ok = True
+        prev = 0
+        for m in combo:
+            # strictly nested: prev is a proper subset of m
+            if (m & prev) != prev or m == prev:
+                ok = False
+                break
+            prev = m
+        if ok:
+            out.append(tuple(combo))
+    out.sort()
+    return out
+
+
+def face_types(n: int):
+    return chains(n + 1, n)
+
+
+def cell_types(n: int):
+    return chains(n + 1, n + 1)
+
+
+def chain_table(n: int) -> np.ndarray:
+    return np.asarray(face_types(n), dtype=np.int32).reshape(-1, n)
+
+
+class Grid:
+    """Spacetime grid: spatial dims (x, y[, z]) plus nt; row-major vertex ids
+    g = ((t*Nz + z)*Ny + y)*Nx + x."""
+
+    def __init__(self, dims, nt):
+        self.n = len(dims)
+        self.d = self.n + 1
+        self.dims = tuple(int(v) for v in dims) + (int(nt),)
+        self.stride = [1]
+        for a in range(1, self.d):
+            self.stride.append(self.stride[-1] * self.dims[a - 1])
+        self.nverts = self.stride[-1] * self.dims[-1]
+        self.ftypes = face_types(self.n)
+        self.ctypes_ = cell_types(self.n)
+        self.T = len(self.ftypes)
+        self.ftype_index = {c: i for i, c in enumerate(self.ftypes)}
+
+    def coords(self, g):
+        return tuple((g // self.stride[a]) % self.dims[a] for a in range(self.d))
+
+    def gid(self, c):
+        return sum(int(c[a]) * self.stride[a] for a in range(self.d))
+
+    def in_bounds(self, c):
+        return all(0 <= c[a] < self.dims[a] for a in range(self.d))
+
+    @staticmethod
+    def add_bits(c, m):
+        return tuple(c[a] + ((m >> a) & 1) for a in range(len(c)))
+
+    def simplex_vertices(self, base, chain):
+        """Vertex coordinates of the simplex (base, chain), in chain order."""
+        return [tuple(base)] + [self.add_bits(base, m) for m in chain]
+
+    def face_exists(self, base, chain):
+        return self.in_bounds(base) and self.in_bounds(self.add_bits(base, chain[-1]))
+
+    def face_id(self, base, chain):
+        return self.gid(base) * self.T + self.ftype_index[tuple(chain)]
+
+    def decode_face(self, fid):
+        g, tt = divmod(int(fid), self.T)
+        return self.coords(g), self.ftypes[tt]
+
+    # -- cofaces / sides (Sec. 3.2 "side_of()", "sides()") ------------------
+    def cofaces(self, base, chain):
+        """Cells (base, full chain) that contain the face (base, chain)."""
+        d = self.d
+        full = (1 << d) - 1
+        out = []
+        steps = [chain[0]] + [chain[i] ^ chain[i - 1] for i in range(1, len(chain))]
+        if chain[-1] == full:
+            i = next(j for j, s in enumerate(steps) if bin(s).count("1") == 2)
+            prev = chain[i - 1] if i > 0 else 0
+            for a in range(d):
+                if (steps[i] >> a) & 1:
+                    mid = prev | (1 << a)
+                    cell = tuple(chain[:i]) + (mid,) + tuple(chain[i:])
+                    out.append((tuple(base), cell))
+        else:
+            a = (full ^ chain[-1]).bit_length() - 1
+            # insert the missing axis first: base moves back by e_a
+            if base[a] >= 1:
+                b2 = tuple(base[j] - (1 if j == a else 0) for j in range(d))
+                cell = ((1 << a),) + tuple(m | (1 << a) for m in chain)
+                out.append((b2, cell))
+            # insert it last
+            if base[a] + 1 < self.dims[a]:
+                out.append((tuple(base), tuple(chain) + (full,)))
+        return out
+
+    def cell_sides(self, base, cell):
+        """The d+1 faces (base, chain) of a cell, by dropping one vertex."""
+        d = self.d
+        out = []
+        for k in range(d + 1):
+            if k == 0:
+                nb = self.add_bits(base, cell[0])
+                ch = tuple(m ^ cell[0] for m in cell[1:])
+                out.append((nb, ch))
+            elif k == d:
+                out.append((tuple(base), tuple(cell[:-1])))
+            else:
+                out.append((tuple(base), tuple(cell[:k - 1]) + tuple(cell[k:])))
+        return out
+
+
+# ----------------------------------------------------------------------------
+# 1-2. Quantise and gradient
+# ----------------------------------------------------------------------------
+def quantise(f: np.ndarray, shift: int = 20) -> np.ndarray:
+    """F = rint(f * 2^shift), round half to even, computed in FP64."""
+    f64 = np.asarray(f, dtype=np.float32).astype(np.float64)
+    if not np.all(np.isfinite(f64)):
+        raise OracleRangeError("non-finite sample")
+    F = np.rint(f64 * float(2.0 ** shift))
+    if np.any(np.abs(F) > RANGE_LIMIT):
+        raise OracleRangeError("|f * 2^shift| exceeds 2^28")
+    return F.astype(np.int64)
+
+
+def _fd(A: np.ndarray, axis: int) -> np.ndarray:
+    """Integer difference along one array axis: A[i+1]-A[i-1] inside,
+    2(A[1]-A[0]) and 2(A[N-1]-A[N-2]) at the two ends."""
+    N = A.shape[axis]
+    if N < 2:
+        raise ValueError("every spatial axis needs at least 2 samples")
+    out = np.empty_like(A)
+
+    def sl(s):
+        return tuple(s if i == axis else slice(None) for i in range(A.ndim))
+
+    if N > 2:
+        out[sl(slice(1, N - 1))] = A[sl(slice(2, N))] - A[sl(slice(0, N - 2))]
+    out[sl(slice(0, 1))] = 2 * (A[sl(slice(1, 2))] - A[sl(slice(0, 1))])
+    out[sl(slice(N - 1, N))] = 2 * (A[sl(slice(N - 1, N))] - A[sl(slice(N - 2, N - 1))])
+    return out
+
+
+def gradient(F: np.ndarray, n: int) -> np.ndarray:
+    """G[..., a] for spatial axis a (0 = x = last array axis)."""
+    return np.stack([_fd(F, F.ndim - 1 - a) for a in range(n)], axis=-1)
+
+
+def hessian(G: np.ndarray, n: int) -> np.ndarray:
+    """H[..., a, b] = difference of G_a along spatial axis b (same rule)."""
+    base = G.ndim - 1  # array axes of the field come first
+    H = np.empty(G.shape + (n,), dtype=np.int64)
+    for a in range(n):
+        for b in range(n):
+            H[..., a, b] = _fd(G[..., a], base - 1 - b)
+    return H
+
+
+# ----------------------------------------------------------------------------
+# 4. Predicate (C core) and whole-field scan
+# ----------------------------------------------------------------------------
+def sos_det_sign(M) -> int:
+    """SoS sign of det(M) (columns sorted by vertex id); M is n x n, M[r][c]."""
+    M = np.asarray(M, dtype=np.int64)
+    n = M.shape[0]
+    colmajor = np.ascontiguousarray(M.T).reshape(-1)
+    return int(clib().oracle_sos_det_sign(n, _p64(colmajor)))
+
+
+def face_punctured(V) -> bool:
+    """V[k][r]: vector of the k-th vertex (sorted by id). SoS puncture test."""
+    V = np.ascontiguousarray(np.asarray(V, dtype=np.int64))
+    n = V.shape[1]
+    return bool(clib().oracle_face_punctured(n, _p64(V.reshape(-1))))
+
+
+def scan_faces(G: np.ndarray, grid: Grid, t_lo: int = 0, t_hi: int | None = None) -> np.ndarray:
+    """Ids (ascending) of all punctured faces with base slice in [t_lo, t_hi)."""
+    t_hi = grid.dims[-1] if t_hi is None else t_hi
+    Gf = np.ascontiguousarray(G.reshape(-1, grid.n).astype(np.int64))
+    dims = np.asarray(grid.dims, dtype=np.int64)
+    tab = chain_table(grid.n)
+    lib = clib()
+    cap = 1 << 16
+    while True:
+        out = np.empty(cap, dtype=np.int64)
+        cnt = lib.oracle_scan(grid.n, _p64(dims), _p64(Gf), grid.T,
+                              tab.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                              t_lo, t_hi, _p64(out), cap)
+        if cnt <= cap:
+            return out[:cnt].copy()
+        cap = int(cnt)
+
+
+def test_faces(G: np.ndarray, grid: Grid, face_ids) -> np.ndarray:
+    """Puncture verdict (1/0, -1 if no such face) for a list of face ids."""
+    Gf = np.ascontiguousarray(G.reshape(-1, grid.n).astype(np.int64))
+    dims = np.asarray(grid.dims, dtype=np.int64)
+    tab = chain_table(grid.n)
+    ids = np.ascontiguousarray(np.asarray(face_ids, dtype=np.int64))
+    res = np.empty(len(ids), dtype=np.int8)
+    clib().oracle_test_faces(grid.n, _p64(dims), _p64(Gf), grid.T,
+                             tab.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                             _p64(ids), len(ids),
+                             res.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)))
+    return res
+
+
+# ----------------------------------------------------------------------------
+# 5-6. Location and classification (exact integers, then FP64)
+# ----------------------------------------------------------------------------
+def det_exact(M) -> int:
+    """Leibniz formula over permutations, Python integers."""
+    n = len(M)
+    total = 0
+    for p in itertools.permutations(range(n)):
+        inv = sum(1 for i in range(n) for j in range(i + 1, n) if p[i] > p[j])
+        prod = -1 if inv & 1 else 1
+        for r in range(n):
+            prod *= int(M[r][p[r]])
+        total += prod
+    return total
+
+
+def cramer_numerators(V):
+    """D_k = (-1)^(n+k) det(V without vertex k) for Eq. (1); V[k][r]."""
+    n = len(V[0])
+    out = []
+    for k in range(n + 1):
+        cols = [V[j] for j in range(n + 1) if j != k]
+        M = [[int(cols[c][r]) for c in range(n)] for r in range(n)]
+        out.append((-1) ** (n + k) * det_exact(M))
+    return out
+
+
+def barycentric(V):
+    """mu_k = D_k / D as exact Fractions (centroid when every D_k is 0)."""
+    D = cramer_numerators(V)
+    tot = sum(D)
+    n1 = len(D)
+    if tot == 0:
+        return [Fraction(1, n1)] * n1, D
+    return [Fraction(dk, tot) for dk in D], D
+
+
+def morse_index(S) -> int:
+    """Number of negative eigenvalues of the symmetric integer matrix S, by
+    Descartes' rule on det(lambda I + S) (exact for real-rooted
+    polynomials); -1 when det S = 0."""
+    n = len(S)
+    coeffs = [1]
+    for k in range(1, n + 1):
+        # e_k = sum of the k x k principal minors
+        e = 0
+        for idx in itertools.combinations(range(n), k):
+            e += det_exact([[S[i][j] for j in idx] for i in idx])
+        coeffs.append(e)
+    if coeffs[-1] == 0:
+        return -1
+    nz = [c for c in coeffs if c != 0]
+    return sum(1 for a, b in zip(nz, nz[1:]) if (a > 0) != (b > 0))
+
+
+def classify(D, Hs) -> int:
+    """Morse index at a puncture: S = sign(D) * sum_k D_k (H_k + H_k^T)."""
+    n = len(Hs[0])
+    tot = sum(D)
+    sgn = 1 if tot > 0 else (-1 if tot < 0 else 0)
+    S = [[0] * n for _ in range(n)]
+    for dk, H in zip(D, Hs):
+        for a in range(n):
+            for b in range(n):
+                S[a][b] += sgn * dk * (int(H[a][b]) + int(H[b][a]))
+    return morse_index(S)
+
+
+# ----------------------------------------------------------------------------
+# 7. Linking (Algorithm 1, second pass) with a plain union-find
+# ----------------------------------------------------------------------------
+class UnionFind:
+    def __init__(self):
+        self.parent = {}
+
+    def add(self, x):
+        self.parent.setdefault(x, x)
+
+    def find(self, x):
+        root = x
+        while self.parent[root] != root:
+            root = self.parent[root]
+        while self.parent[x] != root:
+            self.parent[x], x = root, self.parent[x]
+        return root
+
+    def unite(self, a, b):
+        ra, rb = self.find(a), self.find(b)
+        if ra != rb:
+            if ra < rb:
+                self.parent[rb] = ra
+            else:
+                self.parent[ra] = rb
+
+
+class PairingError(AssertionError):
+    """A spacetime cell had a punctured-face count other than 0 or 2."""
+
+
+def link(grid: Grid, punct_ids, cell_filter=None):
+    """Union the punctured sides of every cell that has one; returns
+    {face_id: label} with label = min face id of the component.
+
+    Only cells that contain at least one punctured face can contribute, so
+    visiting the cofaces of punctured faces visits every such cell.
+    ``cell_filter(base, cell)`` can restrict the cells (streaming prefixes).
+    """
+    S = set(int(x) for x in punct_ids)
+    uf = UnionFind()
+    for f in S:
+        uf.add(f)
+    seen = set()
+    for f in sorted(S):
+        base, chain = grid.decode_face(f)
+        for cb, cc in grid.cofaces(base, chain):
+            key = (cb, cc)
+            if key in seen:
+                continue
+            seen.add(key)
+            if cell_filter is not None and not cell_filter(cb, cc):
+                continue
+            T = [grid.face_id(sb, sc) for sb, sc in grid.cell_sides(cb, cc)]
+            hit = [x for x in T if x in S]
+            if len(hit) not in (0, 2):
+                raise PairingError(f"cell {key} has {len(hit)} punctured sides")
+            if len(hit) == 2:
+                uf.unite(hit[0], hit[1])
+    return {f: uf.find(f) for f in S}
+
+
+# ----------------------------------------------------------------------------
+# Whole pipeline
+# ----------------------------------------------------------------------------
+def track(f: np.ndarray, shift: int = 20, t_lo: int = 0, t_hi: int | None = None,
+          with_types: bool = True, with_links: bool = True):
+    """Exact critical-point tracking of a 2D (nt, ny, nx) or 3D
+    (nt, nz, ny, nx) float32 field.
+
+    Returns a dict of numpy arrays, ordered by face id:
+      face_id (int64), base (int32, [P, 4] = x, y, z, t), off (float64,
+      [P, 4] in-cell offsets), morse (int8), ordinal (uint8), label (int64).
+    ``t_lo/t_hi`` restrict the base slices of the faces (a bounded sample).
+    """
+    f = np.asarray(f, dtype=np.float32)
+    n = f.ndim - 1
+    nt = f.shape[0]
+    dims = tuple(reversed(f.shape[1:]))
+    grid = Grid(dims, nt)
+    F = quantise(f, shift)
+    G = gradient(F, n)
+    ids = scan_faces(G, grid, t_lo, t_hi)
+    Gflat = G.reshape(-1, n)
+    H = hessian(G, n).reshape(-1, n, n) if with_types else None
+    P = len(ids)
+    base = np.zeros((P, 4), dtype=np.int32)
+    off = np.zeros((P, 4), dtype=np.float64)
+    morse = np.full(P, -2, dtype=np.int8)
+    ordinal = np.zeros(P, dtype=np.uint8)
+    tbit = 1 << n
+    for i, fid in enumerate(ids):
+        bc, chain = grid.decode_face(fid)
+        verts = grid.simplex_vertices(bc, chain)
+        gids = [grid.gid(v) for v in verts]
+        V = [[int(Gflat[g][r]) for r in range(n)] for g in gids]
+        mu, D = barycentric(V)
+        for a in range(n):
+            base[i, a] = bc[a]
+        base[i, 3] = bc[n]
+        ms = [0] + list(chain)
+        for a in range(grid.d):
+            o = sum(float(mu[k]) for k in range(n + 1) if (ms[k] >> a) & 1)
+            off[i, a if a < n else 3] = o
+        ordinal[i] = 0 if (chain[-1] & tbit) else 1
+        if with_types:
+            morse[i] = classify(D, [H[g] for g in gids])
+    label = np.full(P, -1, dtype=np.int64)
+    if with_links and P:
+        lab = link(grid, ids)
+        label = np.asarray([lab[int(x)] for x in ids], dtype=np.int64)
+    return dict(face_id=ids, base=base, off=off, morse=morse, ordinal=ordinal,
+                label=label, T=grid.T, grid=grid)
+
+
+def stream_push_index(grid: Grid, fid: int) -> int:
+    """Push (time slice) after which a face becomes known in a stream:
+    ordinal faces at slice t with slice t, interval faces of slab [t, t+1]
+    with slice t+1 (Sec. 3.2, ordinal/interval elements)."""
+    base, chain = grid.decode_face(fid)
+    tbit = 1 << grid.n
+    return base[-1] + (1 if chain[-1] & tbit else 0)
+
+
+def stream_labels(grid: Grid, punct_ids, k: int):
+    """Provisional labels known after push k: components over the faces known
+    so far, linked through the cells of slabs [t, t+1] with t+1 <= k."""
+    known = [int(f) for f in punct_ids if stream_push_index(grid, int(f)) <= k]
+    return link(grid, known, cell_filter=lambda cb, cc: cb[-1] + 1 <= k)

@@ -1,0 +1,219 @@
+"""Seeded synthetic scalar fields for critical-point tracking.
+
+This module only *samples* fields; it holds none of the tracking method's
+arithmetic (no quantisation, no gradients, no predicates).  It is the single
+piece of code shared by the CUDA path's tests/bench and the CPU oracle, so
+that both sides always see the same float32 array.
+
+Layout of every field: C-contiguous float32, ``f[t][y][x]`` in 2D and
+``f[t][z][y][x]`` in 3D (x fastest).
+
+Workloads (shapes follow the paper's synthetic and application data):
+
+* spiral woven (Sec. 4.4, "2D spiral woven with perturbations"):
+  f = cos(x cos t - y sin t) * sin(x sin t + y cos t) on an inclusive
+  linspace grid over [-4, 4]^2, t_k = k/(nt-1) over [0, 1], optional i.i.d.
+  Gaussian noise added in FP64 before a single cast to float32.
+* moving minimum (Sec. 4.4, "3D moving minimum"):
+  f = |x - (x0 + d t)|^2 on an integer grid, t = step index; with dyadic d
+  every sample is exact in float32.
+* moving Gaussian blobs: a seeded sum of Gaussians moving on linear paths,
+  standing in for the 128^3 turbulent-vortex data of Sec. 4.5 (the dataset
+  itself is not available).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "spiral_woven",
+    "moving_minimum",
+    "gaussian_blobs",
+    "random_levels",
+    "BlobSet",
+    "blob_set",
+    "blob_slice",
+    "batch_fields",
+    "stream_specs",
+    "poisson_arrivals",
+]
+
+
+def spiral_woven(n: int, nt: int, sigma: float = 0.0, seed: int = 0,
+                 lo: float = -4.0, hi: float = 4.0, ny: int | None = None) -> np.ndarray:
+    """Spiral woven field sampled on an ``ny x n`` grid over ``nt`` steps.
+
+    x_i = lo + (hi-lo) i/(n-1) (inclusive linspace), t_k = k/(nt-1).
+    Noise N(0, sigma^2) is drawn slice by slice from ``default_rng(seed)``.
+    """
+    ny = n if ny is None else ny
+    x = np.linspace(lo, hi, n)
+    y = np.linspace(lo, hi, ny)
+    ts = np.linspace(0.0, 1.0, nt) if nt > 1 else np.zeros(1)
+    rng = np.random.default_rng(seed)
+    out = np.empty((nt, ny, n), dtype=np.float32)
+    X = x[None, :]
+    Y = y[:, None]
+    for k, t in enumerate(ts):
+        c, s = math.cos(t), math.sin(t)
+        f = np.cos(X * c - Y * s) * np.sin(X * s + Y * c)
+        if sigma > 0.0:
+            f = f + sigma * rng.standard_normal((ny, n))
+        out[k] = f
+    return out
+
+
+def moving_minimum(n: int, nt: int, x0, d, ndim: int = 3) -> np.ndarray:
+    """f(x, t) = |x - (x0 + d t)|^2 on the integer grid {0..n-1}^ndim, t = 0..nt-1.
+
+    With x0 and d dyadic (e.g. multiples of 1/4) every value is exact in
+    float32, so the minimum's trajectory x0 + d t is known exactly.
+    """
+    x0 = np.asarray(x0, dtype=np.float64)
+    d = np.asarray(d, dtype=np.float64)
+    assert x0.shape == (ndim,) and d.shape == (ndim,)
+    idx = np.arange(n, dtype=np.float64)
+    shape = (nt,) + (n,) * ndim
+    out = np.empty(shape, dtype=np.float32)
+    for k in range(nt):
+        c = x0 + d * k
+        f = np.zeros((n,) * ndim, dtype=np.float64)
+        for a in range(ndim):
+            # axis a of the point maps to array axis (ndim-1-a): x is fastest
+            sh = [1] * ndim
+            sh[ndim - 1 - a] = n
+            f = f + ((idx - c[a]) ** 2).reshape(sh)
+        out[k] = f
+    return out
+
+
+def random_levels(shape, levels=(-1.0, 0.0, 1.0), seed: int = 0) -> np.ndarray:
+    """A field whose samples are drawn uniformly from a few levels.
+
+    With levels {-1, 0, 1} almost every simplex is degenerate, which is the
+    hardest case for the symbolic perturbation.
+    """
+    rng = np.random.default_rng(seed)
+    lv = np.asarray(levels, dtype=np.float32)
+    return lv[rng.integers(0, len(lv), size=shape)].astype(np.float32)
+
+
+@dataclass
+class BlobSet:
+    """Parameters of a sum of moving Gaussians (grid-index units)."""
+    centre: np.ndarray     # (nb, ndim) at t=0, axis order x, y, (z)
+    sigma: np.ndarray      # (nb,)
+    amp: np.ndarray        # (nb,)
+    vel: np.ndarray        # (nb, ndim) cells per step
+    dims: tuple            # (nx, ny[, nz])
+
+
+def blob_set(dims, nblobs: int, seed: int, sigma_range=(4.0, 12.0),
+             amp_range=(0.5, 1.0), vmax: float = 1.0) -> BlobSet:
+    """Draw centres U[0,N) per axis, sigma U[sigma_range], amplitude
+    +-U[amp_range] with a random sign, velocity = uniform random direction
+    times U[0, vmax] cells/step."""
+    rng = np.random.default_rng(seed)
+    ndim = len(dims)
+    centre = rng.uniform(0.0, 1.0, size=(nblobs, ndim)) * np.asarray(dims, dtype=np.float64)
+    sigma = rng.uniform(sigma_range[0], sigma_range[1], size=nblobs)
+    amp = rng.uniform(amp_range[0], amp_range[1], size=nblobs)
+    amp = amp * np.where(rng.integers(0, 2, size=nblobs) == 0, -1.0, 1.0)
+    direc = rng.standard_normal((nblobs, ndim))
+    direc /= np.linalg.norm(direc, axis=1, keepdims=True)
+    speed = rng.uniform(0.0, vmax, size=nblobs)
+    vel = direc * speed[:, None]
+    return BlobSet(centre, sigma, amp, vel, tuple(int(v) for v in dims))
+
+
+def blob_slice(bs: BlobSet, k: int) -> np.ndarray:
+    """One time slice (float32, z/y/x order) of a moving blob field at step k."""
+    dims = bs.dims
+    ndim = len(dims)
+    out = np.zeros(tuple(reversed(dims)), dtype=np.float64)
+    for b in range(len(bs.sigma)):
+        c = bs.centre[b] + bs.vel[b] * k
+        inv = 1.0 / (2.0 * bs.sigma[b] ** 2)
+        term = None
+        for a in range(ndim):
+            coord = np.arange(dims[a], dtype=np.float64)
+            e = np.exp(-((coord - c[a]) ** 2) * inv)
+            sh = [1] * ndim
+            sh[ndim - 1 - a] = dims[a]
+            e = e.reshape(sh)
+            term = e if term is None else term * e
+        out += bs.amp[b] * term
+    return out.astype(np.float32)
+
+
+def gaussian_blobs(dims, nt: int, nblobs: int = 32, seed: int = 0, **kw) -> np.ndarray:
+    """A full (nt, [nz,] ny, nx) float32 field of moving Gaussian blobs."""
+    bs = blob_set(dims, nblobs, seed, **kw)
+    out = np.empty((nt,) + tuple(reversed(dims)), dtype=np.float32)
+    for k in range(nt):
+        out[k] = blob_slice(bs, k)
+    return out
+
+
+def batch_fields(count: int = 256, n_lo: int = 64, n_hi: int = 512, nt_lo: int = 8,
+                 nt_hi: int = 32, nb_lo: int = 8, nb_hi: int = 64, seed0: int = 0,
+                 materialise: bool = True):
+    """Many independent 2D blob fields of uneven size and length.
+
+    Field i uses seed ``seed0 + i``: N = round(exp(U[ln n_lo, ln n_hi])) for a
+    square N x N grid, nt ~ U{nt_lo..nt_hi}, nblobs ~ U{nb_lo..nb_hi}, sigma
+    scaled by N/128.  Returns a list of (nx, ny, nt, array-or-None, BlobSet).
+    """
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        nt = int(rng.integers(nt_lo, nt_hi + 1))
+        nb = int(rng.integers(nb_lo, nb_hi + 1))
+        scale = n / 128.0
+        bs = blob_set((n, n), nb, seed=10_000 + seed0 + i,
+                      sigma_range=(4.0 * scale, 12.0 * scale), vmax=1.0)
+        arr = None
+        if materialise:
+            arr = np.empty((nt, n, n), dtype=np.float32)
+            for k in range(nt):
+                arr[k] = blob_slice(bs, k)
+        out.append((n, n, nt, arr, bs))
+    return out
+
+
+def stream_specs(count: int = 32, n_lo: int = 256, n_hi: int = 2048, seed0: int = 0,
+                 nb_lo: int = 8, nb_hi: int = 64):
+    """Per-stream grid size (log-uniform square N) and blob parameters."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(50_000 + seed0 + i)
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        nb = int(rng.integers(nb_lo, nb_hi + 1))
+        scale = n / 128.0
+        bs = blob_set((n, n), nb, seed=60_000 + seed0 + i,
+                      sigma_range=(4.0 * scale, 12.0 * scale), vmax=1.0)
+        out.append((n, bs))
+    return out
+
+
+def poisson_arrivals(nstreams: int, rate_total: float, duration_s: float, seed: int = 0):
+    """Merged Poisson arrival process: list of (time_s, stream_index), sorted.
+
+    Each stream gets an independent Poisson process of rate rate_total/nstreams.
+    """
+    rng = np.random.default_rng(seed)
+    lam = rate_total / nstreams
+    events = []
+    for s in range(nstreams):
+        t = 0.0
+        while True:
+            t += rng.exponential(1.0 / lam)
+            if t > duration_s:
+                break
+            events.append((t, s))
+    events.sort()
+    return events
