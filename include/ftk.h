@@ -1,0 +1,149 @@
+/*
+ * ftk.h -- C ABI of the GB300 critical-point tracker.
+ *
+ * The library tracks critical points of a time-varying scalar field on a
+ * regular grid (2D + time or 3D + time) exactly, following the method of
+ * "FTK: A Simplicial Spacetime Meshing Framework for Robust and Scalable
+ * Feature Tracking" (arXiv 2011.08697):
+ *
+ *   1. every time slice is quantised to fixed point, F = rint(f * 2^S), and
+ *      differentiated with integer central differences (Sec. 4.3: gradients
+ *      of integer or central-difference data are the degenerate case SoS
+ *      must handle; one-sided differences at the domain boundary);
+ *   2. the spacetime grid is subdivided implicitly into simplices (Sec. 3.3,
+ *      each unit (n+1)-cube split into (n+1)! simplices); every n-simplex
+ *      ("face") is tested for a puncture by the critical-point trajectory
+ *      with the exact point-in-simplex predicate of Sec. 4.3 / Eq. (1),
+ *      with Simulation of Simplicity breaking ties by global vertex index;
+ *   3. each punctured face is located (barycentric coordinates of Eq. (1))
+ *      and classified (Morse index of the interpolated Hessian, Sec. 4.1);
+ *   4. punctured faces that share a spacetime cell ((n+1)-simplex) are
+ *      linked into trajectories (Algorithm 1, left column), each labelled by
+ *      the smallest face id it contains.
+ *
+ * Conventions
+ *   Field layout: C-contiguous float32, f[t][y][x] (2D) or f[t][z][y][x]
+ *   (3D), x fastest.  Every spatial extent must be >= 2.
+ *   Global vertex id g = ((t*nz + z)*ny + y)*nx + x   (nz = 1 in 2D).
+ *   Face id = g * T + type, T = 12 (2D) or 60 (3D); the type is the rank of
+ *   the face's chain of axis bitmasks in lexicographic order (axis bit 0 = x,
+ *   1 = y, 2 = z in 3D, and the last bit = t).
+ *
+ * Errors: every call returns an ftk_status; nothing is thrown or aborted
+ * across the ABI.  On error every output pointer is set to NULL, and
+ * ftk_last_error() describes the failure (thread-local string).
+ *
+ * Memory: input pointers are borrowed.  A device pointer must stay valid
+ * until the work queued on the given CUDA stream has completed; a host
+ * pointer is copied before the call returns.  Results (ftk_result) are
+ * library-owned host arrays released with ftk_result_free().
+ */
+#ifndef FTK_GB300_H
+#define FTK_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FTK_OK = 0,
+    FTK_ERR_ARG = 1,        /* invalid argument (null pointer, extent < 2, ...) */
+    FTK_ERR_RANGE = 2,      /* a sample is non-finite or |f * 2^S| > 2^28 */
+    FTK_ERR_NOMEM = 3,      /* device or host allocation failed */
+    FTK_ERR_CUDA = 4,       /* a CUDA runtime call failed */
+    FTK_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+    FTK_ERR_BUSY = 6,       /* admission refused (device memory budget) */
+    FTK_ERR_INVARIANT = 7,  /* a spacetime cell had a punctured-side count other than 0 or 2 */
+    FTK_ERR_STATE = 8       /* call not valid in the object's current state */
+} ftk_status;
+
+#define FTK_FLAG_STAGE_TIMES 1u
+
+/* Tracking parameters.  ftk_params_default() fills the defaults. */
+typedef struct {
+    double   origin[3];      /* physical coordinate of grid index 0 (x, y, z) */
+    double   spacing[3];     /* physical grid spacing (x, y, z) */
+    double   t0, dt;         /* physical time of slice 0 and slice spacing */
+    int32_t  quant_shift;    /* fixed-point scale 2^quant_shift; default 20 */
+    uint32_t flags;          /* bit 0 (FTK_FLAG_STAGE_TIMES): record per-stage device
+                                times; other bits reserved, must be 0 */
+    int64_t  max_punctures;  /* initial device capacity; 0 = automatic (grows on demand) */
+} ftk_params;
+
+/* One punctured face (one point of a critical-point trajectory). */
+typedef struct {
+    int64_t face_id;      /* g * T + type */
+    int64_t label;        /* trajectory label: smallest face id of its component */
+    int32_t base[4];      /* grid indices x, y, z, t of the face's base vertex (z = 0 in 2D) */
+    float   off[4];       /* in-cell offsets along x, y, z, t (position = base + off) */
+    int8_t  morse_index;  /* number of negative Hessian eigenvalues: 0 = minimum,
+                             n = maximum, else saddle; -1 = degenerate Hessian */
+    uint8_t ordinal;      /* 1 if all vertices of the face lie in one time slice */
+    uint8_t ndim;         /* 2 or 3 */
+    uint8_t reserved[5];
+} ftk_cp;                 /* 56 bytes */
+
+/* Device-side view of a plan's results (structure of arrays, valid until the
+ * next execute or destroy).  Arrays are ordered by increasing face id. */
+typedef struct {
+    int64_t        count;
+    const int64_t *face_id;   /* [count] */
+    const int64_t *label;     /* [count] */
+    const float   *off;       /* [count][4] */
+    const int8_t  *morse;     /* [count] */
+} ftk_device_view;
+
+typedef struct ftk_result ftk_result;
+typedef struct ftk_plan ftk_plan;
+typedef struct ftk_stream ftk_stream;
+
+void        ftk_params_default(ftk_params *p);
+const char *ftk_status_string(ftk_status s);
+const char *ftk_last_error(void);
+/* Library version string, e.g. "ftk-gb300 0.1 sm_103a". */
+const char *ftk_version(void);
+
+/* ---------------------------------------------------------------------
+ * One-shot tracking (paper Sec. 8, post hoc analysis of a whole field).
+ * f: device or host pointer to nt slices of ny*nx (2D) or nz*ny*nx (3D)
+ * floats.  *out receives all punctured faces sorted by face_id.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  The call
+ * returns after the results are on the host.
+ * ------------------------------------------------------------------- */
+ftk_status ftk_track_cp2d(const float *f, int64_t nx, int64_t ny, int64_t nt,
+                          const ftk_params *p, ftk_result **out, void *cuda_stream);
+ftk_status ftk_track_cp3d(const float *f, int64_t nx, int64_t ny, int64_t nz, int64_t nt,
+                          const ftk_params *p, ftk_result **out, void *cuda_stream);
+
+/* Result access.  ftk_result_data() entries are sorted by face_id. */
+size_t        ftk_result_count(const ftk_result *r);
+const ftk_cp *ftk_result_data(const ftk_result *r);
+void          ftk_result_free(ftk_result *r);
+
+/* ---------------------------------------------------------------------
+ * Plans: device workspace for repeated tracking of fields of one shape.
+ * ftk_plan_execute queues the whole pipeline on cuda_stream and returns
+ * without synchronising; results stay in device memory.  f may be a device
+ * pointer or a host pointer (copied to a plan-owned device buffer on the
+ * same stream).  ftk_plan_count / ftk_plan_download synchronise the plan's
+ * last stream, re-run the pipeline with a larger capacity if the punctures
+ * outgrew it, and report device-side errors.
+ * ------------------------------------------------------------------- */
+ftk_status ftk_plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt,
+                           const ftk_params *p, ftk_plan **plan);
+ftk_status ftk_plan_execute(ftk_plan *plan, const float *f, void *cuda_stream);
+ftk_status ftk_plan_count(ftk_plan *plan, int64_t *count);
+ftk_status ftk_plan_download(ftk_plan *plan, ftk_result **out);
+ftk_status ftk_plan_device_view(ftk_plan *plan, ftk_device_view *view);
+/* Per-stage device times (ms) of the last synchronised execute, in the order
+ * detect, scan, finalize, link, label; n = number of entries written. */
+ftk_status ftk_plan_stage_times(ftk_plan *plan, float *ms, int cap, int *n);
+ftk_status ftk_plan_destroy(ftk_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTK_GB300_H */

@@ -1,0 +1,418 @@
+// Host side of the C ABI declared in include/ftk.h: argument checking,
+// blocking choice, device workspace (plans), result download, error codes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/ftk.h"
+#include "ftk_kernels.cuh"
+
+using namespace ftk;
+
+namespace {
+
+thread_local std::string g_err;
+
+ftk_status fail(ftk_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+ftk_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return FTK_ERR_CUDA;
+}
+
+#define FTK_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e__ = (call);                        \
+        if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+    } while (0)
+
+constexpr size_t kSmemBudget = 110 * 1024;   // two detect CTAs per SM
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct ftk_result {
+    ftk_cp *data;
+    size_t count;
+};
+
+struct ftk_plan {
+    int ndim;
+    int device;
+    Field F;
+    Blocking B;
+    ftk_params p;
+    long long nverts;
+    Workspace W;
+    float *d_input;
+    RunCounters *h_ctr;        // pinned mirror of the device counters
+    cudaStream_t stream;
+    const float *last_f;
+    bool last_host;
+    bool executed;
+    bool timing;
+    cudaEvent_t ev[6];
+    float stage_ms[5];
+    int nstage;
+};
+
+namespace {
+
+void free_workspace(Workspace &W) {
+    cudaFree(W.ctr);
+    cudaFree(W.seg_cnt);
+    cudaFree(W.seg_stage);
+    cudaFree(W.seg_off);
+    cudaFree(W.staging);
+    cudaFree(W.face);
+    cudaFree(W.parent);
+    cudaFree(W.off);
+    cudaFree(W.morse);
+    cudaFree(W.label);
+    cudaFree(W.packed);
+    std::memset(&W, 0, sizeof(W));
+}
+
+ftk_status alloc_capacity(Workspace &W, long long cap) {
+    cudaFree(W.staging); W.staging = nullptr;
+    cudaFree(W.face); W.face = nullptr;
+    cudaFree(W.parent); W.parent = nullptr;
+    cudaFree(W.off); W.off = nullptr;
+    cudaFree(W.morse); W.morse = nullptr;
+    cudaFree(W.label); W.label = nullptr;
+    cudaFree(W.packed); W.packed = nullptr;
+    W.cap = 0;
+    if (cudaMalloc(&W.staging, cap * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&W.face, cap * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&W.parent, cap * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&W.off, cap * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&W.morse, cap * sizeof(int8_t)) != cudaSuccess ||
+        cudaMalloc(&W.label, cap * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&W.packed, cap * sizeof(ftk_cp)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FTK_ERR_NOMEM, "device allocation of the puncture arrays failed");
+    }
+    W.cap = cap;
+    return FTK_OK;
+}
+
+ftk_status choose_blocking(int ndim, const Field &F, Blocking &B) {
+    static const int cand2[] = {16, 8, 4, 2, 1};
+    static const int cand3[][2] = {{8, 4}, {8, 2}, {4, 4}, {4, 2}, {2, 2}, {2, 1}, {1, 1}};
+    bool ok = false;
+    if (ndim == 2) {
+        for (int ry : cand2) {
+            B.ry = ry; B.rz = 1;
+            if (detect_smem_bytes(2, F, B) <= kSmemBudget) { ok = true; break; }
+        }
+    } else {
+        for (auto &c : cand3) {
+            B.ry = c[0]; B.rz = c[1];
+            if (detect_smem_bytes(3, F, B) <= kSmemBudget) { ok = true; break; }
+        }
+    }
+    if (!ok) return fail(FTK_ERR_ARG, "grid rows too wide for the detect tile (nx too large)");
+    B.nyb = (F.ny + B.ry - 1) / B.ry;
+    B.nzb = ndim == 3 ? (F.nz + B.rz - 1) / B.rz : 1;
+    // enough units to fill the GPU: split time into chunks if the spatial
+    // blocks alone are too few
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long spatial = (long long)B.nyb * B.nzb;
+    const long long want = 4LL * sms;
+    long long chunks = spatial >= want ? 1 : (want + spatial - 1) / spatial;
+    chunks = std::min<long long>(chunks, F.nt);
+    B.tc = (int)((F.nt + chunks - 1) / chunks);
+    B.ntc = (F.nt + B.tc - 1) / B.tc;
+    return FTK_OK;
+}
+
+ftk_status check_params(const ftk_params *p) {
+    if (p && (p->quant_shift < 0 || p->quant_shift > 40))
+        return fail(FTK_ERR_ARG, "quant_shift must lie in [0, 40]");
+    if (p && p->flags & ~1u) return fail(FTK_ERR_ARG, "unknown flag bits");
+    if (p && p->max_punctures < 0) return fail(FTK_ERR_ARG, "max_punctures must be >= 0");
+    return FTK_OK;
+}
+
+ftk_status read_counters(ftk_plan *pl) {
+    FTK_CUDA(cudaStreamSynchronize(pl->stream));
+    FTK_CUDA(cudaMemcpy(pl->h_ctr, pl->W.ctr, sizeof(RunCounters), cudaMemcpyDeviceToHost));
+    return FTK_OK;
+}
+
+ftk_status status_of(unsigned st) {
+    if (st & ST_RANGE) return fail(FTK_ERR_RANGE, "a sample is non-finite or |f * 2^quant_shift| exceeds 2^28");
+    if (st & ST_TIMEOUT) return fail(FTK_ERR_TIMEOUT, "a bounded device loop gave up");
+    if (st & ST_PAIRING) return fail(FTK_ERR_INVARIANT, "a spacetime cell had other than 0 or 2 punctured sides");
+    return FTK_OK;
+}
+
+ftk_status launch(ftk_plan *pl, const float *dev_f, cudaStream_t s) {
+    pl->F.f = dev_f;
+    cudaError_t e = launch_pipeline(pl->ndim, pl->F, pl->B, pl->W, s, pl->timing ? pl->ev : nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline launch");
+    pl->stream = s;
+    pl->executed = true;
+    return FTK_OK;
+}
+
+// synchronise, grow and re-run on overflow, check device status
+ftk_status settle(ftk_plan *pl) {
+    if (!pl->executed) return fail(FTK_ERR_STATE, "plan has not been executed");
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        ftk_status s = read_counters(pl);
+        if (s != FTK_OK) return s;
+        const unsigned st = pl->h_ctr->status;
+        if (st & ST_RANGE) return status_of(st);
+        if (!(st & ST_OVERFLOW)) {
+            if (pl->timing) {
+                pl->nstage = 5;
+                for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&pl->stage_ms[i], pl->ev[i], pl->ev[i + 1]);
+            }
+            return status_of(st);
+        }
+        const long long need = (long long)pl->h_ctr->staged;
+        long long cap = std::max<long long>(need + need / 4 + 1024, 2 * pl->W.cap);
+        s = alloc_capacity(pl->W, cap);
+        if (s != FTK_OK) return s;
+        const float *src = pl->last_host ? pl->d_input : pl->last_f;
+        s = launch(pl, src, pl->stream);
+        if (s != FTK_OK) return s;
+    }
+    return fail(FTK_ERR_NOMEM, "puncture capacity did not converge");
+}
+
+ftk_status make_result(ftk_plan *pl, ftk_result **out) {
+    const long long P = pl->h_ctr->punctures;
+    ftk_result *r = new (std::nothrow) ftk_result;
+    if (!r) return fail(FTK_ERR_NOMEM, "host allocation failed");
+    r->count = (size_t)P;
+    r->data = (ftk_cp *)std::malloc(std::max<size_t>(1, (size_t)P) * sizeof(ftk_cp));
+    if (!r->data) {
+        delete r;
+        return fail(FTK_ERR_NOMEM, "host allocation failed");
+    }
+    if (P > 0) {
+        cudaError_t e = cudaMemcpy(r->data, pl->W.packed, (size_t)P * sizeof(ftk_cp), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            std::free(r->data);
+            delete r;
+            return cuda_fail(e, "result download");
+        }
+    }
+    *out = r;
+    return FTK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ftk_params_default(ftk_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    for (int a = 0; a < 3; ++a) p->spacing[a] = 1.0;
+    p->dt = 1.0;
+    p->quant_shift = 20;
+}
+
+const char *ftk_status_string(ftk_status s) {
+    switch (s) {
+        case FTK_OK: return "ok";
+        case FTK_ERR_ARG: return "invalid argument";
+        case FTK_ERR_RANGE: return "sample out of fixed-point range";
+        case FTK_ERR_NOMEM: return "out of memory";
+        case FTK_ERR_CUDA: return "CUDA error";
+        case FTK_ERR_TIMEOUT: return "device wait timed out";
+        case FTK_ERR_BUSY: return "admission refused";
+        case FTK_ERR_INVARIANT: return "pairing invariant violated";
+        case FTK_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char *ftk_last_error(void) { return g_err.c_str(); }
+
+const char *ftk_version(void) { return "ftk-gb300 0.1 sm_103a"; }
+
+ftk_status ftk_plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt,
+                           const ftk_params *p, ftk_plan **plan) {
+    if (plan) *plan = nullptr;
+    if (!plan) return fail(FTK_ERR_ARG, "plan is NULL");
+    if (ndim != 2 && ndim != 3) return fail(FTK_ERR_ARG, "ndim must be 2 or 3");
+    if (ndim == 2) nz = 1;
+    if (nx < 2 || ny < 2 || (ndim == 3 && nz < 2) || nt < 1)
+        return fail(FTK_ERR_ARG, "every spatial extent must be >= 2 and nt >= 1");
+    if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30) || nt > (1 << 30))
+        return fail(FTK_ERR_ARG, "extent too large");
+    const long long T = ndim == 2 ? 12 : 60;
+    const double nv = (double)nx * ny * nz * nt;
+    if (nv * T > 9.0e18) return fail(FTK_ERR_ARG, "face ids would overflow int64");
+    ftk_status s = check_params(p);
+    if (s != FTK_OK) return s;
+
+    ftk_plan *pl = new (std::nothrow) ftk_plan;
+    if (!pl) return fail(FTK_ERR_NOMEM, "host allocation failed");
+    std::memset(pl, 0, sizeof(*pl));
+    if (p) pl->p = *p;
+    else ftk_params_default(&pl->p);
+    pl->ndim = ndim;
+    cudaGetDevice(&pl->device);
+    pl->F.nx = (int)nx; pl->F.ny = (int)ny; pl->F.nz = (int)nz; pl->F.nt = (int)nt;
+    pl->F.scale = (float)std::ldexp(1.0, pl->p.quant_shift);
+    pl->nverts = (long long)nx * ny * nz * nt;
+    s = choose_blocking(ndim, pl->F, pl->B);
+    if (s != FTK_OK) { delete pl; return s; }
+    pl->W.nseg = (long long)nt * nz * pl->B.nyb;
+    pl->timing = (pl->p.flags & 1u) != 0;
+
+    Workspace &W = pl->W;
+    if (cudaMalloc(&W.ctr, sizeof(RunCounters)) != cudaSuccess ||
+        cudaMalloc(&W.seg_cnt, W.nseg * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&W.seg_stage, W.nseg * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&W.seg_off, W.nseg * sizeof(long long)) != cudaSuccess ||
+        cudaMallocHost(&pl->h_ctr, sizeof(RunCounters)) != cudaSuccess) {
+        cudaGetLastError();
+        free_workspace(W);
+        if (pl->h_ctr) cudaFreeHost(pl->h_ctr);
+        delete pl;
+        return fail(FTK_ERR_NOMEM, "device allocation failed");
+    }
+    long long cap = pl->p.max_punctures > 0
+                        ? pl->p.max_punctures
+                        : std::max<long long>(1 << 16, std::min<long long>(pl->nverts / 32, 1LL << 26));
+    s = alloc_capacity(W, cap);
+    if (s != FTK_OK) {
+        free_workspace(W);
+        cudaFreeHost(pl->h_ctr);
+        delete pl;
+        return s;
+    }
+    if (pl->timing)
+        for (int i = 0; i < 6; ++i) cudaEventCreate(&pl->ev[i]);
+    *plan = pl;
+    return FTK_OK;
+}
+
+ftk_status ftk_plan_execute(ftk_plan *pl, const float *f, void *cuda_stream) {
+    if (!pl || !f) return fail(FTK_ERR_ARG, "plan and field must be non-NULL");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const bool host = !is_device_pointer(f);
+    const float *src = f;
+    if (host) {
+        const size_t bytes = (size_t)pl->nverts * sizeof(float);
+        if (!pl->d_input) {
+            if (cudaMalloc(&pl->d_input, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FTK_ERR_NOMEM, "device input buffer allocation failed");
+            }
+        }
+        FTK_CUDA(cudaMemcpyAsync(pl->d_input, f, bytes, cudaMemcpyHostToDevice, s));
+        src = pl->d_input;
+    }
+    pl->last_f = f;
+    pl->last_host = host;
+    return launch(pl, src, s);
+}
+
+ftk_status ftk_plan_count(ftk_plan *pl, int64_t *count) {
+    if (!pl || !count) return fail(FTK_ERR_ARG, "plan and count must be non-NULL");
+    ftk_status s = settle(pl);
+    if (s != FTK_OK) return s;
+    *count = pl->h_ctr->punctures;
+    return FTK_OK;
+}
+
+ftk_status ftk_plan_download(ftk_plan *pl, ftk_result **out) {
+    if (out) *out = nullptr;
+    if (!pl || !out) return fail(FTK_ERR_ARG, "plan and out must be non-NULL");
+    ftk_status s = settle(pl);
+    if (s != FTK_OK) return s;
+    return make_result(pl, out);
+}
+
+ftk_status ftk_plan_device_view(ftk_plan *pl, ftk_device_view *v) {
+    if (!pl || !v) return fail(FTK_ERR_ARG, "plan and view must be non-NULL");
+    ftk_status s = settle(pl);
+    if (s != FTK_OK) return s;
+    v->count = pl->h_ctr->punctures;
+    v->face_id = (const int64_t *)pl->W.face;
+    v->label = (const int64_t *)pl->W.label;
+    v->off = (const float *)pl->W.off;
+    v->morse = pl->W.morse;
+    return FTK_OK;
+}
+
+ftk_status ftk_plan_stage_times(ftk_plan *pl, float *ms, int cap, int *n) {
+    if (!pl || !ms || !n) return fail(FTK_ERR_ARG, "NULL argument");
+    if (!pl->timing) return fail(FTK_ERR_STATE, "plan created without the stage-timing flag");
+    *n = std::min(cap, pl->nstage);
+    for (int i = 0; i < *n; ++i) ms[i] = pl->stage_ms[i];
+    return FTK_OK;
+}
+
+ftk_status ftk_plan_destroy(ftk_plan *pl) {
+    if (!pl) return FTK_OK;
+    if (pl->executed) cudaStreamSynchronize(pl->stream);
+    free_workspace(pl->W);
+    cudaFree(pl->d_input);
+    if (pl->h_ctr) cudaFreeHost(pl->h_ctr);
+    if (pl->timing)
+        for (int i = 0; i < 6; ++i) cudaEventDestroy(pl->ev[i]);
+    delete pl;
+    return FTK_OK;
+}
+
+static ftk_status track_once(int ndim, const float *f, int64_t nx, int64_t ny, int64_t nz, int64_t nt,
+                             const ftk_params *p, ftk_result **out, void *stream) {
+    if (out) *out = nullptr;
+    if (!f || !out) return fail(FTK_ERR_ARG, "field and out must be non-NULL");
+    ftk_plan *pl = nullptr;
+    ftk_status s = ftk_plan_create(ndim, nx, ny, nz, nt, p, &pl);
+    if (s != FTK_OK) return s;
+    s = ftk_plan_execute(pl, f, stream);
+    if (s == FTK_OK) s = ftk_plan_download(pl, out);
+    std::string keep = g_err;
+    ftk_plan_destroy(pl);
+    g_err = keep;
+    return s;
+}
+
+ftk_status ftk_track_cp2d(const float *f, int64_t nx, int64_t ny, int64_t nt, const ftk_params *p,
+                          ftk_result **out, void *stream) {
+    return track_once(2, f, nx, ny, 1, nt, p, out, stream);
+}
+
+ftk_status ftk_track_cp3d(const float *f, int64_t nx, int64_t ny, int64_t nz, int64_t nt,
+                          const ftk_params *p, ftk_result **out, void *stream) {
+    return track_once(3, f, nx, ny, nz, nt, p, out, stream);
+}
+
+size_t ftk_result_count(const ftk_result *r) { return r ? r->count : 0; }
+const ftk_cp *ftk_result_data(const ftk_result *r) { return r ? r->data : nullptr; }
+void ftk_result_free(ftk_result *r) {
+    if (!r) return;
+    std::free(r->data);
+    delete r;
+}
+
+}  // extern "C"

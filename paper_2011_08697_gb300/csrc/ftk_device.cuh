@@ -1,0 +1,245 @@
+// Device building blocks of the GB300 critical-point tracker.
+//
+//  * MeshTables<N>: the implicit simplicial spacetime mesh of a regular grid
+//    (paper Sec. 3.3).  Each unit (N+1)-cube is split into (N+1)! simplices
+//    (monotone chains of axis flips, the "recursive extrusion" of Sec. 3.3 /
+//    Table 1); a k-simplex is a base vertex plus a strictly nested chain of
+//    k nonempty axis bitmasks.  Face (N-simplex) types are ranked in
+//    lexicographic chain order; the tables are generated at compile time.
+//  * Exact puncture predicate (Sec. 4.3, Eq. 1): 0 lies in the interior of
+//    the simplex spanned by the N+1 gradient vectors iff the signed
+//    determinants (-1)^k det(V without column k) all agree.  Determinants
+//    are exact (int64 in 2D, int128 in 3D).  Zero determinants are decided
+//    by Simulation of Simplicity: entry (row r, column c) of a determinant
+//    whose columns are sorted by global vertex id is perturbed by
+//    eps^(2^(c*N + r)); the sign is that of the first nonzero coefficient
+//    in increasing exponent order, read from a compile-time term table.
+//  * BigInt<W>: fixed-width two's-complement integers for the exact Morse
+//    classification (products up to ~2^390 in 3D).
+#pragma once
+#include <cstdint>
+
+namespace ftk {
+
+// ----------------------------------------------------------------------------
+// Mesh tables
+// ----------------------------------------------------------------------------
+template <int N>
+struct MeshDims {
+    static constexpr int D = N + 1;                 // spacetime dimension
+    static constexpr int FULL = (1 << D) - 1;
+    static constexpr int TBIT = 1 << N;             // time axis bit
+    static constexpr int T = (N == 2) ? 12 : 60;    // face (N-simplex) types per vertex
+    static constexpr int C = (N == 2) ? 6 : 24;     // cell ((N+1)-simplex) types
+};
+
+template <int N>
+struct MeshTables {
+    using M = MeshDims<N>;
+    uint8_t face[M::T][N];        // face chains m_1..m_N
+    uint8_t lookup[1 << (4 * N)]; // chain key (4 bits per mask) -> type, 255 if none
+
+    __host__ __device__ constexpr MeshTables() : face{}, lookup{} {
+        for (int i = 0; i < (1 << (4 * N)); ++i) lookup[i] = 255;
+        // odometer over (m_1, .., m_N) in [1, FULL]^N in lexicographic order,
+        // keeping strictly nested chains; the visiting order is the rank order
+        int idx[N] = {};
+        for (int i = 0; i < N; ++i) idx[i] = 1;
+        int cnt = 0;
+        while (true) {
+            bool ok = true;
+            int prev = 0;
+            for (int i = 0; i < N; ++i) {
+                const int m = idx[i];
+                if ((m & prev) != prev || m == prev) { ok = false; break; }
+                prev = m;
+            }
+            if (ok) {
+                int key = 0;
+                for (int i = 0; i < N; ++i) {
+                    face[cnt][i] = (uint8_t)idx[i];
+                    key |= idx[i] << (4 * i);
+                }
+                lookup[key] = (uint8_t)cnt;
+                ++cnt;
+            }
+            int p = N - 1;
+            while (p >= 0 && idx[p] == M::FULL) { idx[p] = 1; --p; }
+            if (p < 0) break;
+            ++idx[p];
+        }
+    }
+};
+
+template <int N>
+__host__ __device__ constexpr int chain_key(const int (&m)[N]) {
+    int key = 0;
+    for (int i = 0; i < N; ++i) key |= m[i] << (4 * i);
+    return key;
+}
+
+// ----------------------------------------------------------------------------
+// SoS term table: the perturbed-entry sets (partial permutations) of an N x N
+// determinant in increasing exponent order, each with the permutations that
+// contain it.  Bit c*N + r of `mask` marks entry (row r, column c).
+// ----------------------------------------------------------------------------
+template <int N>
+struct SosTable {
+    static constexpr int NP = (N == 2) ? 2 : 6;
+    static constexpr int MAXT = (N == 2) ? 6 : 33;
+    int8_t perm[NP][N];
+    int8_t psign[NP];
+    uint16_t mask[MAXT];
+    uint8_t pset[MAXT];   // bit p set: permutation p contains the entry set
+    uint8_t ncols[MAXT];  // bitmask of columns whose entry is perturbed
+    int nterms;
+
+    __host__ __device__ constexpr SosTable() : perm{}, psign{}, mask{}, pset{}, ncols{}, nterms(0) {
+        // permutations of {0..N-1}, lexicographic
+        int p[N] = {};
+        for (int i = 0; i < N; ++i) p[i] = i;
+        int np = 0;
+        while (true) {
+            int inv = 0;
+            for (int i = 0; i < N; ++i)
+                for (int j = i + 1; j < N; ++j)
+                    if (p[i] > p[j]) ++inv;
+            for (int i = 0; i < N; ++i) perm[np][i] = (int8_t)p[i];
+            psign[np] = (inv & 1) ? -1 : 1;
+            ++np;
+            int i = N - 2;
+            while (i >= 0 && p[i] >= p[i + 1]) --i;
+            if (i < 0) break;
+            int j = N - 1;
+            while (p[j] <= p[i]) --j;
+            int t = p[i]; p[i] = p[j]; p[j] = t;
+            for (int a = i + 1, b = N - 1; a < b; ++a, --b) { t = p[a]; p[a] = p[b]; p[b] = t; }
+        }
+        // masks in increasing order = increasing exponent sum_{keys} 2^key
+        for (int m = 1; m < (1 << (N * N)); ++m) {
+            int rows = 0, cols = 0;
+            bool ok = true;
+            for (int c = 0; c < N && ok; ++c)
+                for (int r = 0; r < N && ok; ++r)
+                    if ((m >> (c * N + r)) & 1) {
+                        if (((rows >> r) & 1) || ((cols >> c) & 1)) ok = false;
+                        rows |= 1 << r;
+                        cols |= 1 << c;
+                    }
+            if (!ok) continue;
+            int ps = 0;
+            for (int q = 0; q < NP; ++q) {
+                bool has = true;
+                for (int c = 0; c < N; ++c)
+                    if (((cols >> c) & 1) && !((m >> (c * N + perm[q][c])) & 1)) has = false;
+                if (has) ps |= 1 << q;
+            }
+            mask[nterms] = (uint16_t)m;
+            pset[nterms] = (uint8_t)ps;
+            ncols[nterms] = (uint8_t)cols;
+            ++nterms;
+        }
+    }
+};
+
+// ----------------------------------------------------------------------------
+// Exact determinants and the SoS sign
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int sgn128(__int128 v) { return (v > 0) - (v < 0); }
+
+// M[c][r]: column c = vertex (sorted by id), row r = vector component
+__device__ __forceinline__ __int128 det_exact(const int32_t (&M)[2][2]) {
+    return (__int128)((int64_t)M[0][0] * M[1][1] - (int64_t)M[0][1] * M[1][0]);
+}
+__device__ __forceinline__ __int128 det_exact(const int32_t (&M)[3][3]) {
+    // expansion along the first component row; 2x2 minors fit in int64
+    const int64_t m0 = (int64_t)M[1][1] * M[2][2] - (int64_t)M[1][2] * M[2][1];
+    const int64_t m1 = (int64_t)M[0][1] * M[2][2] - (int64_t)M[0][2] * M[2][1];
+    const int64_t m2 = (int64_t)M[0][1] * M[1][2] - (int64_t)M[0][2] * M[1][1];
+    return (__int128)M[0][0] * m0 - (__int128)M[1][0] * m1 + (__int128)M[2][0] * m2;
+}
+
+template <int N>
+__device__ __noinline__ int sos_fallback(const int32_t (&M)[N][N]);
+
+template <int N>
+__device__ __forceinline__ int sos_det_sign(const int32_t (&M)[N][N]) {
+    const __int128 d = det_exact(M);
+    if (d != 0) return d > 0 ? 1 : -1;
+    return sos_fallback<N>(M);
+}
+
+// ----------------------------------------------------------------------------
+// Fixed-width two's-complement big integers (little-endian 32-bit limbs)
+// ----------------------------------------------------------------------------
+template <int W>
+struct BigInt {
+    uint32_t w[W];
+};
+
+template <int W>
+__device__ __forceinline__ BigInt<W> big_from(__int128 v) {
+    BigInt<W> r;
+    const uint32_t fill = v < 0 ? 0xffffffffu : 0u;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        r.w[i] = i < 4 ? (uint32_t)((unsigned __int128)v >> (32 * i)) : fill;
+    }
+    return r;
+}
+
+template <int W>
+__device__ __forceinline__ BigInt<W> big_add(const BigInt<W> &a, const BigInt<W> &b) {
+    BigInt<W> r;
+    uint64_t c = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const uint64_t s = (uint64_t)a.w[i] + b.w[i] + c;
+        r.w[i] = (uint32_t)s;
+        c = s >> 32;
+    }
+    return r;
+}
+
+template <int W>
+__device__ __forceinline__ BigInt<W> big_sub(const BigInt<W> &a, const BigInt<W> &b) {
+    BigInt<W> r;
+    uint64_t borrow = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const uint64_t s = (uint64_t)a.w[i] - b.w[i] - borrow;
+        r.w[i] = (uint32_t)s;
+        borrow = (s >> 32) & 1;
+    }
+    return r;
+}
+
+// product modulo 2^(32W); exact whenever the signed product fits in W limbs
+template <int W>
+__device__ __forceinline__ BigInt<W> big_mul(const BigInt<W> &a, const BigInt<W> &b) {
+    BigInt<W> r;
+#pragma unroll
+    for (int i = 0; i < W; ++i) r.w[i] = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        uint64_t c = 0;
+#pragma unroll
+        for (int j = 0; i + j < W; ++j) {
+            const uint64_t t = (uint64_t)a.w[i] * b.w[j] + r.w[i + j] + c;
+            r.w[i + j] = (uint32_t)t;
+            c = t >> 32;
+        }
+    }
+    return r;
+}
+
+template <int W>
+__device__ __forceinline__ int big_sign(const BigInt<W> &a) {
+    if (a.w[W - 1] >> 31) return -1;
+    uint32_t any = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) any |= a.w[i];
+    return any ? 1 : 0;
+}
+
+}  // namespace ftk

@@ -1,0 +1,830 @@
+// CUDA kernels of the exact critical-point tracking pipeline (sm_103a).
+//
+// Pipeline of one field (paper Algorithm 1, left column, plus Sec. 4.1/4.3):
+//   k_detect   dense, HBM-bound: per unit (y-block x z-block x time chunk)
+//              march through the time slices; per slice load the tile,
+//              quantise F = rint(f 2^S), integer central-difference gradient,
+//              2N sign bits per vertex; per spacetime cube AND the sign bits
+//              of its corners -- a component that keeps one strict sign on
+//              every corner rules out every face owned by the cube, exactly,
+//              because the symbolic perturbation is infinitesimal.  Surviving
+//              cubes (rare) run the exact SoS predicate on each of their
+//              faces; punctured faces are compacted in face-id order per
+//              segment (t, z, y-block).
+//   k_scan     exclusive scan of the per-segment counts (segment order is
+//              face-id order), total count.
+//   k_finalize per puncture: its rank in face-id order, location from the
+//              barycentric coordinates of Eq. (1) (FP32), Morse index of the
+//              interpolated Hessian (exact multiword integers).
+//   k_link     per puncture: its <= 2 spacetime cells, the other punctured
+//              side of each (binary search), lock-free union-find.
+//   k_label    label = smallest face id of the component; pack records.
+#include <cuda_runtime.h>
+
+#include "ftk_device.cuh"
+#include "ftk_kernels.cuh"
+
+namespace ftk {
+
+__constant__ MeshTables<2> c_mesh2 = MeshTables<2>();
+__constant__ MeshTables<3> c_mesh3 = MeshTables<3>();
+__constant__ SosTable<2> c_sos2 = SosTable<2>();
+__constant__ SosTable<3> c_sos3 = SosTable<3>();
+
+template <int N> __device__ __forceinline__ const MeshTables<N> &mesh();
+template <> __device__ __forceinline__ const MeshTables<2> &mesh<2>() { return c_mesh2; }
+template <> __device__ __forceinline__ const MeshTables<3> &mesh<3>() { return c_mesh3; }
+template <int N> __device__ __forceinline__ const SosTable<N> &sos();
+template <> __device__ __forceinline__ const SosTable<2> &sos<2>() { return c_sos2; }
+template <> __device__ __forceinline__ const SosTable<3> &sos<3>() { return c_sos3; }
+
+constexpr int NT = 256;              // threads per CTA of every kernel here
+constexpr float RANGE_LIMIT = 268435456.0f;   // 2^28
+constexpr int UF_LIMIT = 1 << 22;    // bound on union-find retries / path steps
+
+// ----------------------------------------------------------------------------
+// SoS fallback: first nonzero coefficient of det(M + E(eps)) in increasing
+// exponent order (the exact determinant has already been found to be 0).
+// ----------------------------------------------------------------------------
+template <int N>
+__device__ __noinline__ int sos_fallback(const int32_t (&M)[N][N]) {
+    const SosTable<N> &S = sos<N>();
+    for (int t = 0; t < S.nterms; ++t) {
+        long long coef = 0;
+        for (int q = 0; q < SosTable<N>::NP; ++q) {
+            if (!((S.pset[t] >> q) & 1)) continue;
+            long long term = S.psign[q];
+            for (int c = 0; c < N; ++c)
+                if (!((S.ncols[t] >> c) & 1)) term *= (long long)M[c][S.perm[q][c]];
+            coef += term;
+        }
+        if (coef != 0) return coef > 0 ? 1 : -1;
+    }
+    return -1;  // not reached: the fully perturbed terms have coefficient +-1
+}
+
+// Exact SoS puncture test of one face; V[k] = gradient at the k-th vertex in
+// increasing global-id order.
+template <int N>
+__device__ bool face_punctured(const int32_t (&V)[N + 1][N]) {
+    // a component with one strict sign on every vertex excludes the origin
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        bool allp = true, alln = true;
+#pragma unroll
+        for (int k = 0; k <= N; ++k) {
+            allp &= V[k][r] > 0;
+            alln &= V[k][r] < 0;
+        }
+        if (allp || alln) return false;
+    }
+    int ref = 0;
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        int32_t M[N][N];
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j <= N; ++j) {
+            if (j == k) continue;
+#pragma unroll
+            for (int r = 0; r < N; ++r) M[c][r] = V[j][r];
+            ++c;
+        }
+        const int s = sos_det_sign<N>(M);
+        const int val = (k & 1) ? -s : s;
+        if (k == 0) ref = val;
+        else if (val != ref) return false;
+    }
+    return true;
+}
+
+// ----------------------------------------------------------------------------
+// Block-wide exclusive scan (NT threads); red needs NT/32 + 1 ints.
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *red, T &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) red[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < NT / 32 ? red[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < NT / 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NT / 32) red[lane] = w;
+    }
+    __syncthreads();
+    const T before = warp ? red[warp - 1] : T(0);
+    total = red[NT / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// ----------------------------------------------------------------------------
+// Detect kernel
+// ----------------------------------------------------------------------------
+struct TileGeom {
+    int nx, ny, nz;
+    int y0, z0;
+    int PY, PZ;     // tile rows / planes (with halo)
+    int WY, WZ;     // word rows / planes
+    int tile;       // ints per F tile
+    int wtile;      // bytes per word tile
+};
+
+__device__ __forceinline__ int quantise(float f, float scale, unsigned *status) {
+    const float v = f * scale;   // exact: scale is a power of two
+    if (!(fabsf(v) <= RANGE_LIMIT)) {
+        atomicOr(status, ST_RANGE);
+        return 0;
+    }
+    return __float2int_rn(v);
+}
+
+// gradient at (x, y, z) from an F tile; ty/tz are the tile row/plane of (y, z)
+template <int N>
+__device__ __forceinline__ void grad_tile(const int32_t *T, const TileGeom &g, int x, int y, int z,
+                                          int ty, int tz, int32_t (&G)[N]) {
+    const int32_t *row = T + (tz * g.PY + ty) * g.nx;
+    G[0] = x == 0 ? 2 * (row[1] - row[0])
+         : x == g.nx - 1 ? 2 * (row[x] - row[x - 1])
+         : row[x + 1] - row[x - 1];
+    const int32_t *up = row + g.nx, *dn = row - g.nx;
+    G[1] = y == 0 ? 2 * (up[x] - row[x])
+         : y == g.ny - 1 ? 2 * (row[x] - dn[x])
+         : up[x] - dn[x];
+    if (N == 3) {
+        const int ps = g.PY * g.nx;
+        const int32_t *fw = row + ps, *bk = row - ps;
+        G[N - 1] = z == 0 ? 2 * (fw[x] - row[x])
+                 : z == g.nz - 1 ? 2 * (row[x] - bk[x])
+                 : fw[x] - bk[x];
+    }
+}
+
+template <int N>
+__device__ void load_tile(const Field &F, const TileGeom &g, int s, int32_t *T, unsigned *status) {
+    const int rows = g.PZ * g.PY;
+    for (int i = threadIdx.x; i < rows * g.nx; i += NT) {
+        const int x = i % g.nx;
+        const int r = i / g.nx;
+        const int ty = r % g.PY;
+        const int tz = r / g.PY;
+        const int y = g.y0 - 1 + ty;
+        const int z = N == 3 ? g.z0 - 1 + tz : 0;
+        if (y < 0 || y >= g.ny || z < 0 || z >= g.nz) continue;
+        const long long idx = (((long long)s * g.nz + z) * g.ny + y) * g.nx + x;
+        T[i] = quantise(__ldg(F.f + idx), F.scale, status);
+    }
+}
+
+template <int N>
+__device__ void make_words(const TileGeom &g, const int32_t *T, uint8_t *Wd) {
+    for (int i = threadIdx.x; i < g.WZ * g.WY * g.nx; i += NT) {
+        const int x = i % g.nx;
+        const int r = i / g.nx;
+        const int wy = r % g.WY;
+        const int wz = r / g.WY;
+        const int y = g.y0 + wy;
+        const int z = g.z0 + wz;
+        if (y >= g.ny || z >= g.nz) continue;
+        int32_t G[N];
+        grad_tile<N>(T, g, x, y, z, wy + 1, N == 3 ? wz + 1 : 0, G);
+        uint32_t w = 0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) w |= ((uint32_t)(G[c] < 0) << (2 * c)) | ((uint32_t)(G[c] > 0) << (2 * c + 1));
+        Wd[i] = (uint8_t)w;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ bool eval_face(const TileGeom &g, const int32_t *T0, const int32_t *T1,
+                                          bool has_next, int x, int y, int z, int ly, int lz, int tt) {
+    constexpr int TB = MeshDims<N>::TBIT;
+    const uint8_t *ch = mesh<N>().face[tt];
+    const int last = ch[N - 1];
+    if ((last & 1) && x + 1 >= g.nx) return false;
+    if ((last & 2) && y + 1 >= g.ny) return false;
+    if (N == 3 && (last & 4) && z + 1 >= g.nz) return false;
+    if ((last & TB) && !has_next) return false;
+    int32_t V[N + 1][N];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        const int m = k == 0 ? 0 : ch[k - 1];
+        const int dx = m & 1, dy = (m >> 1) & 1, dz = N == 3 ? (m >> 2) & 1 : 0;
+        const int32_t *T = (m & TB) ? T1 : T0;
+        grad_tile<N>(T, g, x + dx, y + dy, z + dz, ly + dy + 1, N == 3 ? lz + dz + 1 : 0, V[k]);
+    }
+    return face_punctured<N>(V);
+}
+
+__host__ __device__ inline int round_up16(int v) { return (v + 15) & ~15; }
+
+struct DetectLayout {
+    int tile, wtile, plane_bits, plane_words, flag_words;
+    int off_words, off_bm, off_sv, off_flags, off_red, total;
+};
+
+template <int N>
+__host__ __device__ inline DetectLayout detect_layout(int nx, int ry, int rz) {
+    DetectLayout L;
+    const int PY = ry + 3, PZ = N == 3 ? rz + 3 : 1;
+    const int WY = ry + 1, WZ = N == 3 ? rz + 1 : 1;
+    const int RZ = N == 3 ? rz : 1;
+    L.tile = PZ * PY * nx;
+    L.wtile = WZ * WY * nx;
+    L.plane_bits = ry * nx;
+    L.plane_words = (L.plane_bits + 31) / 32;
+    L.flag_words = (L.plane_bits * MeshDims<N>::T + 31) / 32;
+    L.off_words = 2 * L.tile * 4;
+    L.off_bm = round_up16(L.off_words + 2 * L.wtile);
+    L.off_sv = round_up16(L.off_bm + RZ * L.plane_words * 4);
+    L.off_flags = round_up16(L.off_sv + L.plane_bits * 4);
+    L.off_red = round_up16(L.off_flags + L.flag_words * 4);
+    L.total = round_up16(L.off_red + 64 * 8);
+    return L;
+}
+
+template <int N>
+__global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int T = MeshDims<N>::T;
+    const int rz = N == 3 ? B.rz : 1;
+    const DetectLayout L = detect_layout<N>(F.nx, B.ry, B.rz);
+    int32_t *Ft = reinterpret_cast<int32_t *>(smem);
+    uint8_t *Wt = smem + L.off_words;
+    uint32_t *bm = reinterpret_cast<uint32_t *>(smem + L.off_bm);
+    int *sv = reinterpret_cast<int *>(smem + L.off_sv);
+    uint32_t *flags = reinterpret_cast<uint32_t *>(smem + L.off_flags);
+    long long *red = reinterpret_cast<long long *>(smem + L.off_red);
+    __shared__ long long s_base;
+
+    int u = blockIdx.x;
+    const int tci = u % B.ntc;
+    u /= B.ntc;
+    const int yb = u % B.nyb;
+    const int zb = u / B.nyb;
+
+    TileGeom g;
+    g.nx = F.nx; g.ny = F.ny; g.nz = F.nz;
+    g.y0 = yb * B.ry;
+    g.z0 = N == 3 ? zb * B.rz : 0;
+    g.PY = B.ry + 3; g.PZ = N == 3 ? B.rz + 3 : 1;
+    g.WY = B.ry + 1; g.WZ = N == 3 ? B.rz + 1 : 1;
+    g.tile = L.tile; g.wtile = L.wtile;
+
+    const int t_begin = tci * B.tc;
+    const int t_end = min(F.nt, t_begin + B.tc);
+    unsigned *status = &W.ctr->status;
+
+    load_tile<N>(F, g, t_begin, Ft, status);
+    __syncthreads();
+    make_words<N>(g, Ft, Wt);
+    int cur = 0;
+    for (int t = t_begin; t < t_end; ++t) {
+        const bool has_next = t + 1 < F.nt;
+        const int nxt = cur ^ 1;
+        const int32_t *T0 = Ft + cur * L.tile;
+        const int32_t *T1 = Ft + nxt * L.tile;
+        if (has_next) {
+            load_tile<N>(F, g, t + 1, Ft + nxt * L.tile, status);
+            __syncthreads();
+            make_words<N>(g, T1, Wt + nxt * L.wtile);
+        }
+        for (int i = threadIdx.x; i < rz * L.plane_words; i += NT) bm[i] = 0u;
+        __syncthreads();
+
+        // ---- exact cube cull ------------------------------------------------
+        bool any = false;
+        for (int i = threadIdx.x; i < rz * B.ry * g.nx; i += NT) {
+            const int x = i % g.nx;
+            const int r = i / g.nx;
+            const int ly = r % B.ry;
+            const int lz = r / B.ry;
+            const int y = g.y0 + ly, z = g.z0 + lz;
+            if (y >= g.ny || z >= g.nz) continue;
+            const int ex = x + 1 < g.nx, ey = y + 1 < g.ny, ez = (N == 3) && (z + 1 < g.nz);
+            uint32_t m = 0xffu;
+            for (int ds = 0; ds <= (int)has_next; ++ds) {
+                const uint8_t *wb = Wt + (cur ^ ds) * L.wtile;
+                for (int dz = 0; dz <= ez; ++dz)
+                    for (int dy = 0; dy <= ey; ++dy) {
+                        const uint8_t *wr = wb + ((lz + dz) * g.WY + ly + dy) * g.nx + x;
+                        m &= wr[0];
+                        if (ex) m &= wr[1];
+                    }
+            }
+            if (m == 0u) {
+                const int idx = ly * g.nx + x;
+                atomicOr(&bm[lz * L.plane_words + (idx >> 5)], 1u << (idx & 31));
+                any = true;
+            }
+        }
+        const int any_all = __syncthreads_or(any);
+
+        // ---- survivors: exact predicate, ordered compaction per segment -----
+        for (int lz = 0; lz < rz; ++lz) {
+            const int z = g.z0 + lz;
+            if (z >= g.nz) break;
+            const long long seg = ((long long)t * g.nz + z) * B.nyb + yb;
+            if (!any_all) {
+                if (threadIdx.x == 0) { W.seg_cnt[seg] = 0; W.seg_stage[seg] = 0; }
+                continue;
+            }
+            // survivor list in vertex order
+            int nsv = 0;
+            for (int b0 = 0; b0 < L.plane_words; b0 += NT) {
+                const int i = b0 + threadIdx.x;
+                uint32_t bits = i < L.plane_words ? bm[lz * L.plane_words + i] : 0u;
+                long long tot;
+                long long pos = nsv + block_excl_scan<long long>(__popc(bits), red, tot);
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    sv[pos++] = i * 32 + b;
+                }
+                nsv += (int)tot;
+            }
+            const int ncand = nsv * T;
+            const int nfw = (ncand + 31) / 32;
+            for (int i = threadIdx.x; i < nfw; i += NT) flags[i] = 0u;
+            __syncthreads();
+            for (int c = threadIdx.x; c < ncand; c += NT) {
+                const int v = sv[c / T];
+                const int tt = c % T;
+                const int ly = v / g.nx, x = v % g.nx;
+                if (eval_face<N>(g, T0, T1, has_next, x, g.y0 + ly, z, ly, lz, tt))
+                    atomicOr(&flags[c >> 5], 1u << (c & 31));
+            }
+            __syncthreads();
+            long long mine = 0;
+            for (int i = threadIdx.x; i < nfw; i += NT) mine += __popc(flags[i]);
+            long long count;
+            block_excl_scan<long long>(mine, red, count);
+            if (threadIdx.x == 0) {
+                const long long base = count ? (long long)atomicAdd(&W.ctr->staged, (unsigned long long)count) : 0;
+                W.seg_cnt[seg] = (int)count;
+                W.seg_stage[seg] = base;
+                s_base = base;
+                if (base + count > W.cap) atomicOr(status, ST_OVERFLOW);
+            }
+            __syncthreads();
+            const long long base = s_base;
+            long long run = 0;
+            for (int b0 = 0; b0 < nfw; b0 += NT) {
+                const int i = b0 + threadIdx.x;
+                uint32_t bits = i < nfw ? flags[i] : 0u;
+                long long tot;
+                long long pos = base + run + block_excl_scan<long long>(__popc(bits), red, tot);
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int c = i * 32 + b;
+                    const int v = sv[c / T];
+                    const int ly = v / g.nx, x = v % g.nx;
+                    const long long gid = (((long long)t * g.nz + z) * g.ny + g.y0 + ly) * g.nx + x;
+                    if (pos < W.cap) W.staging[pos] = gid * T + (c % T);
+                    ++pos;
+                }
+                run += tot;
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        cur = nxt;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Scan of per-segment counts (one CTA)
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_scan(Workspace W) {
+    __shared__ long long red[NT / 32 + 1];
+    constexpr int PER = 16;
+    long long run = 0;
+    for (long long b0 = 0; b0 < W.nseg; b0 += (long long)NT * PER) {
+        const long long i0 = b0 + (long long)threadIdx.x * PER;
+        long long loc[PER];
+        long long s = 0;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const long long i = i0 + j;
+            loc[j] = i < W.nseg ? (long long)W.seg_cnt[i] : 0;
+            s += loc[j];
+        }
+        long long tot;
+        long long ex = run + block_excl_scan<long long>(s, red, tot);
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const long long i = i0 + j;
+            if (i < W.nseg) W.seg_off[i] = ex;
+            ex += loc[j];
+        }
+        run += tot;
+    }
+    if (threadIdx.x == 0) W.ctr->punctures = run;
+}
+
+// ----------------------------------------------------------------------------
+// Global-memory gradient / Hessian (sparse stages)
+// ----------------------------------------------------------------------------
+struct Pt { int c[4]; };   // x, y, z, t (z = 0 in 2D)
+
+__device__ __forceinline__ int qload(const Field &F, int x, int y, int z, int t) {
+    const long long idx = (((long long)t * F.nz + z) * F.ny + y) * F.nx + x;
+    const float v = __ldg(F.f + idx) * F.scale;
+    return fabsf(v) <= RANGE_LIMIT ? __float2int_rn(v) : 0;
+}
+
+__device__ __forceinline__ int ext_of(const Field &F, int a) { return a == 0 ? F.nx : a == 1 ? F.ny : F.nz; }
+
+// gradient component a (spatial axis 0 = x, 1 = y, 2 = z) at point p
+__device__ int grad_global(const Field &F, Pt p, int a) {
+    const int n = ext_of(F, a);
+    Pt lo = p, hi = p;
+    if (p.c[a] == 0) { hi.c[a] = 1; return 2 * (qload(F, hi.c[0], hi.c[1], hi.c[2], hi.c[3]) - qload(F, p.c[0], p.c[1], p.c[2], p.c[3])); }
+    if (p.c[a] == n - 1) { lo.c[a] = n - 2; return 2 * (qload(F, p.c[0], p.c[1], p.c[2], p.c[3]) - qload(F, lo.c[0], lo.c[1], lo.c[2], lo.c[3])); }
+    lo.c[a] -= 1;
+    hi.c[a] += 1;
+    return qload(F, hi.c[0], hi.c[1], hi.c[2], hi.c[3]) - qload(F, lo.c[0], lo.c[1], lo.c[2], lo.c[3]);
+}
+
+// Hessian entry H_ab = difference of G_a along axis b (same boundary rule)
+__device__ long long hess_global(const Field &F, Pt p, int a, int b) {
+    const int n = ext_of(F, b);
+    Pt lo = p, hi = p;
+    if (p.c[b] == 0) { hi.c[b] = 1; return 2LL * ((long long)grad_global(F, hi, a) - grad_global(F, p, a)); }
+    if (p.c[b] == n - 1) { lo.c[b] = n - 2; return 2LL * ((long long)grad_global(F, p, a) - grad_global(F, lo, a)); }
+    lo.c[b] -= 1;
+    hi.c[b] += 1;
+    return (long long)grad_global(F, hi, a) - grad_global(F, lo, a);
+}
+
+__device__ __forceinline__ float i128_to_float(__int128 v) {
+    const bool neg = v < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    const float r = __fmaf_rn((float)hi, 18446744073709551616.0f, (float)lo);
+    return neg ? -r : r;
+}
+
+template <int N>
+__device__ __forceinline__ Pt decode_face(const Field &F, long long fid, int &tt) {
+    constexpr int T = MeshDims<N>::T;
+    long long g = fid / T;
+    tt = (int)(fid - g * T);
+    Pt p;
+    p.c[0] = (int)(g % F.nx); g /= F.nx;
+    p.c[1] = (int)(g % F.ny); g /= F.ny;
+    p.c[2] = (int)(g % F.nz); g /= F.nz;
+    p.c[3] = (int)g;
+    return p;
+}
+
+// vertex k of a simplex: base + bits of mask m (axis N of m is time)
+template <int N>
+__device__ __forceinline__ Pt add_mask(Pt p, int m) {
+    p.c[0] += m & 1;
+    p.c[1] += (m >> 1) & 1;
+    if (N == 3) p.c[2] += (m >> 2) & 1;
+    p.c[3] += (m >> N) & 1;
+    return p;
+}
+
+template <int N, int W>
+__device__ int morse_from_S(const BigInt<W> (&S)[N][N]) {
+    BigInt<W> e[N];
+    if (N == 2) {
+        e[0] = big_add(S[0][0], S[1][1]);
+        e[1] = big_sub(big_mul(S[0][0], S[1][1]), big_mul(S[0][1], S[1][0]));
+    } else {
+        e[0] = big_add(big_add(S[0][0], S[1][1]), S[N - 1][N - 1]);
+        BigInt<W> m01 = big_sub(big_mul(S[0][0], S[1][1]), big_mul(S[0][1], S[1][0]));
+        BigInt<W> m02 = big_sub(big_mul(S[0][0], S[N - 1][N - 1]), big_mul(S[0][N - 1], S[N - 1][0]));
+        BigInt<W> m12 = big_sub(big_mul(S[1][1], S[N - 1][N - 1]), big_mul(S[1][N - 1], S[N - 1][1]));
+        e[1] = big_add(big_add(m01, m02), m12);
+        // det by expansion along row 0
+        BigInt<W> c0 = m12;
+        BigInt<W> c1 = big_sub(big_mul(S[1][0], S[N - 1][N - 1]), big_mul(S[1][N - 1], S[N - 1][0]));
+        BigInt<W> c2 = big_sub(big_mul(S[1][0], S[N - 1][1]), big_mul(S[1][1], S[N - 1][0]));
+        e[N - 1] = big_add(big_sub(big_mul(S[0][0], c0), big_mul(S[0][1], c1)), big_mul(S[0][N - 1], c2));
+    }
+    if (big_sign(e[N - 1]) == 0) return -1;
+    int prev = 1, changes = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const int s = big_sign(e[i]);
+        if (s != 0) {
+            if (s != prev) ++changes;
+            prev = s;
+        }
+    }
+    return changes;
+}
+
+template <int N>
+__device__ void locate_classify(const Field &F, long long fid, float4 &off, int8_t &morse) {
+    constexpr int BW = N == 2 ? 8 : 16;
+    int tt;
+    const Pt base = decode_face<N>(F, fid, tt);
+    const uint8_t *ch = mesh<N>().face[tt];
+    Pt v[N + 1];
+    int32_t V[N + 1][N];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        v[k] = k == 0 ? base : add_mask<N>(base, ch[k - 1]);
+#pragma unroll
+        for (int a = 0; a < N; ++a) V[k][a] = grad_global(F, v[k], a);
+    }
+    __int128 D[N + 1];
+    __int128 Dsum = 0;
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        int32_t M[N][N];
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j <= N; ++j) {
+            if (j == k) continue;
+#pragma unroll
+            for (int r = 0; r < N; ++r) M[c][r] = V[j][r];
+            ++c;
+        }
+        const __int128 d = det_exact(M);
+        D[k] = ((N + k) & 1) ? -d : d;
+        Dsum += D[k];
+    }
+    float mu[N + 1];
+    if (Dsum == 0) {
+#pragma unroll
+        for (int k = 0; k <= N; ++k) mu[k] = 1.0f / (N + 1);
+    } else {
+        const float fd = i128_to_float(Dsum);
+#pragma unroll
+        for (int k = 0; k <= N; ++k) mu[k] = i128_to_float(D[k]) / fd;
+    }
+    float o[N + 1];
+#pragma unroll
+    for (int a = 0; a <= N; ++a) o[a] = 0.0f;
+#pragma unroll
+    for (int k = 1; k <= N; ++k)
+#pragma unroll
+        for (int a = 0; a <= N; ++a)
+            if ((ch[k - 1] >> a) & 1) o[a] += mu[k];
+    off = make_float4(o[0], o[1], N == 3 ? o[2] : 0.0f, o[N]);
+
+    // S = sign(D) sum_k D_k (H_k + H_k^T), exact
+    const int sg = sgn128(Dsum);
+    BigInt<BW> S[N][N];
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = 0; b < N; ++b) S[a][b] = big_from<BW>(0);
+    for (int k = 0; k <= N; ++k) {
+        long long H[N][N];
+        for (int a = 0; a < N; ++a)
+            for (int b = 0; b < N; ++b) H[a][b] = hess_global(F, v[k], a, b);
+        const __int128 w = sg < 0 ? -D[k] : D[k];
+        for (int a = 0; a < N; ++a)
+            for (int b = 0; b < N; ++b)
+                S[a][b] = big_add(S[a][b], big_from<BW>(w * (__int128)(H[a][b] + H[b][a])));
+    }
+    morse = (int8_t)morse_from_S<N, BW>(S);
+}
+
+template <int N>
+__global__ void __launch_bounds__(NT) k_finalize(Field F, Blocking B, Workspace W) {
+    const unsigned long long staged_all = W.ctr->staged;
+    const long long staged = staged_all < (unsigned long long)W.cap ? (long long)staged_all : W.cap;
+    if (W.ctr->status & ST_OVERFLOW) return;
+    constexpr int T = MeshDims<N>::T;
+    for (long long s = blockIdx.x * (long long)NT + threadIdx.x; s < staged; s += (long long)gridDim.x * NT) {
+        const long long fid = W.staging[s];
+        const long long seg = segment_of(fid / T, F, B);
+        const long long i = W.seg_off[seg] + (s - W.seg_stage[seg]);
+        W.face[i] = fid;
+        W.parent[i] = (int)i;
+        float4 o;
+        int8_t m;
+        locate_classify<N>(F, fid, o, m);
+        W.off[i] = o;
+        W.morse[i] = m;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Linking
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int uf_find(int *parent, int x, unsigned *status) {
+    for (int it = 0; it < UF_LIMIT; ++it) {
+        const int p = *(volatile int *)&parent[x];
+        if (p == x) return x;
+        const int gp = *(volatile int *)&parent[p];
+        if (gp != p) *(volatile int *)&parent[x] = gp;   // path halving (points to an ancestor)
+        x = gp;
+    }
+    atomicOr(status, ST_TIMEOUT);
+    return x;
+}
+
+__device__ __forceinline__ void uf_unite(int *parent, int a, int b, unsigned *status) {
+    for (int it = 0; it < UF_LIMIT; ++it) {
+        a = uf_find(parent, a, status);
+        b = uf_find(parent, b, status);
+        if (a == b) return;
+        if (a < b) { const int t = a; a = b; b = t; }
+        // hook the larger root under the smaller: roots stay component minima
+        const int old = atomicCAS(&parent[a], a, b);
+        if (old == a) return;
+        a = old;
+    }
+    atomicOr(status, ST_TIMEOUT);
+}
+
+__device__ __forceinline__ long long find_face(const long long *face, long long P, long long key) {
+    long long lo = 0, hi = P;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        const long long v = face[mid];
+        if (v < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < P && face[lo] == key) ? lo : -1;
+}
+
+template <int N>
+__device__ __forceinline__ long long face_id_of(const Field &F, Pt b, const int (&m)[N]) {
+    constexpr int T = MeshDims<N>::T;
+    const int tt = mesh<N>().lookup[chain_key<N>(m)];
+    const long long g = (((long long)b.c[3] * F.nz + b.c[2]) * F.ny + b.c[1]) * F.nx + b.c[0];
+    return g * T + tt;
+}
+
+template <int N>
+__global__ void __launch_bounds__(NT) k_link(Field F, Workspace W) {
+    constexpr int D = N + 1;
+    constexpr int FULL = (1 << D) - 1;
+    if (W.ctr->status & ST_OVERFLOW) return;
+    const long long P = W.ctr->punctures;
+    unsigned *status = &W.ctr->status;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        const long long fid = W.face[i];
+        int tt;
+        const Pt base = decode_face<N>(F, fid, tt);
+        int m[N];
+        for (int k = 0; k < N; ++k) m[k] = mesh<N>().face[tt][k];
+        // cofaces: cells (base, full chain of D masks) containing the face
+        Pt cb[2];
+        int cm[2][D];
+        int ncell = 0;
+        if (m[N - 1] == FULL) {
+            int prev = 0;
+            for (int j = 0; j < N; ++j) {
+                const int step = m[j] ^ prev;
+                if (__popc(step) == 2) {
+                    for (int a = 0; a < D; ++a) {
+                        if (!((step >> a) & 1)) continue;
+                        for (int q = 0; q < j; ++q) cm[ncell][q] = m[q];
+                        cm[ncell][j] = prev | (1 << a);
+                        for (int q = j; q < N; ++q) cm[ncell][q + 1] = m[q];
+                        cb[ncell] = base;
+                        ++ncell;
+                    }
+                    break;
+                }
+                prev = m[j];
+            }
+        } else {
+            const int a = __ffs(FULL ^ m[N - 1]) - 1;
+            const int ca = a == N ? 3 : a;           // coordinate slot of axis a
+            const int ext = a == N ? F.nt : (a == 0 ? F.nx : a == 1 ? F.ny : F.nz);
+            if (base.c[ca] >= 1) {
+                cb[ncell] = base;
+                cb[ncell].c[ca] -= 1;
+                cm[ncell][0] = 1 << a;
+                for (int q = 0; q < N; ++q) cm[ncell][q + 1] = m[q] | (1 << a);
+                ++ncell;
+            }
+            if (base.c[ca] + 1 < ext) {
+                cb[ncell] = base;
+                for (int q = 0; q < N; ++q) cm[ncell][q] = m[q];
+                cm[ncell][N] = FULL;
+                ++ncell;
+            }
+        }
+        for (int c = 0; c < ncell; ++c) {
+            int hits = 0;
+            long long partner = -1;
+            for (int k = 0; k <= D; ++k) {
+                Pt sb = cb[c];
+                int sm[N];
+                if (k == 0) {
+                    sb = add_mask<N>(cb[c], cm[c][0]);
+                    for (int q = 0; q < N; ++q) sm[q] = cm[c][q + 1] ^ cm[c][0];
+                } else if (k == D) {
+                    for (int q = 0; q < N; ++q) sm[q] = cm[c][q];
+                } else {
+                    int w = 0;
+                    for (int q = 0; q < D; ++q)
+                        if (q != k - 1) sm[w++] = cm[c][q];
+                }
+                const long long sid = face_id_of<N>(F, sb, sm);
+                if (sid == fid) continue;
+                const long long j = find_face(W.face, P, sid);
+                if (j >= 0) { ++hits; partner = j; }
+            }
+            if (hits != 1) {
+                atomicOr(status, ST_PAIRING);
+                continue;
+            }
+            uf_unite(W.parent, (int)i, (int)partner, status);
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(NT) k_label(Field F, Workspace W) {
+    if (W.ctr->status & ST_OVERFLOW) return;
+    const long long P = W.ctr->punctures;
+    unsigned *status = &W.ctr->status;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        const int r = uf_find(W.parent, (int)i, status);
+        const long long fid = W.face[i];
+        const long long lab = W.face[r];
+        W.label[i] = lab;
+        int tt;
+        const Pt b = decode_face<N>(F, fid, tt);
+        ftk_cp rec;
+        rec.face_id = fid;
+        rec.label = lab;
+        rec.base[0] = b.c[0]; rec.base[1] = b.c[1]; rec.base[2] = b.c[2]; rec.base[3] = b.c[3];
+        const float4 o = W.off[i];
+        rec.off[0] = o.x; rec.off[1] = o.y; rec.off[2] = o.z; rec.off[3] = o.w;
+        rec.morse_index = W.morse[i];
+        rec.ordinal = (mesh<N>().face[tt][N - 1] & MeshDims<N>::TBIT) ? 0 : 1;
+        rec.ndim = (uint8_t)N;
+        for (int q = 0; q < 5; ++q) rec.reserved[q] = 0;
+        W.packed[i] = rec;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Host-side launch helpers
+// ----------------------------------------------------------------------------
+size_t detect_smem_bytes(int ndim, const Field &F, const Blocking &B) {
+    const DetectLayout L = ndim == 2 ? detect_layout<2>(F.nx, B.ry, B.rz) : detect_layout<3>(F.nx, B.ry, B.rz);
+    return (size_t)L.total;
+}
+
+static int sparse_grid() {
+    static int g = 0;
+    if (!g) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g = (sms > 0 ? sms : 148) * 4;
+    }
+    return g;
+}
+
+template <int N>
+static cudaError_t launch_all(const Field &F, const Blocking &B, const Workspace &W, cudaStream_t s,
+                              cudaEvent_t *ev) {
+    const size_t smem = detect_smem_bytes(N, F, B);
+    static size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_detect<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    const long long units = (long long)B.ntc * B.nyb * B.nzb;
+    const int sg = sparse_grid();
+    if (ev) cudaEventRecord(ev[0], s);
+    k_detect<N><<<(unsigned)units, NT, smem, s>>>(F, B, W);
+    if (ev) cudaEventRecord(ev[1], s);
+    k_scan<<<1, NT, 0, s>>>(W);
+    if (ev) cudaEventRecord(ev[2], s);
+    k_finalize<N><<<sg, NT, 0, s>>>(F, B, W);
+    if (ev) cudaEventRecord(ev[3], s);
+    k_link<N><<<sg, NT, 0, s>>>(F, W);
+    if (ev) cudaEventRecord(ev[4], s);
+    k_label<N><<<sg, NT, 0, s>>>(F, W);
+    if (ev) cudaEventRecord(ev[5], s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pipeline(int ndim, const Field &F, const Blocking &B, const Workspace &W,
+                            cudaStream_t s, cudaEvent_t *ev) {
+    cudaError_t e = cudaMemsetAsync(W.ctr, 0, sizeof(RunCounters), s);
+    if (e != cudaSuccess) return e;
+    return ndim == 2 ? launch_all<2>(F, B, W, s, ev) : launch_all<3>(F, B, W, s, ev);
+}
+
+}  // namespace ftk

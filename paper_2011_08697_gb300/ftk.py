@@ -1,0 +1,263 @@
+"""Thin Python binding of the C ABI in ``include/ftk.h`` (argument marshalling
+only: every step of the tracking pipeline runs in the CUDA library).
+
+Functions keep the C names.  Field arguments may be CUDA torch tensors,
+CPU torch tensors or numpy arrays (float32, C-contiguous, (nt, ny, nx) or
+(nt, nz, ny, nx)); results come back as numpy structured arrays with the
+layout of ``ftk_cp``.  The library must have been built
+(``paper_2011_08697_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CP_DTYPE = np.dtype([
+    ("face_id", "<i8"), ("label", "<i8"), ("base", "<i4", (4,)), ("off", "<f4", (4,)),
+    ("morse_index", "i1"), ("ordinal", "u1"), ("ndim", "u1"), ("reserved", "u1", (5,)),
+])
+assert CP_DTYPE.itemsize == 56
+
+FTK_OK = 0
+FTK_FLAG_STAGE_TIMES = 1
+STATUS_NAMES = {0: "FTK_OK", 1: "FTK_ERR_ARG", 2: "FTK_ERR_RANGE", 3: "FTK_ERR_NOMEM",
+                4: "FTK_ERR_CUDA", 5: "FTK_ERR_TIMEOUT", 6: "FTK_ERR_BUSY",
+                7: "FTK_ERR_INVARIANT", 8: "FTK_ERR_STATE"}
+
+
+class FtkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ftk_params(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("spacing", ctypes.c_double * 3),
+                ("t0", ctypes.c_double), ("dt", ctypes.c_double),
+                ("quant_shift", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("max_punctures", ctypes.c_int64)]
+
+
+class ftk_device_view(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64), ("face_id", ctypes.c_void_p), ("label", ctypes.c_void_p),
+                ("off", ctypes.c_void_p), ("morse", ctypes.c_void_p)]
+
+
+_lib = None
+
+# every symbol the header declares (checked by the CPU test-suite)
+EXPORTS = [
+    "ftk_params_default", "ftk_status_string", "ftk_last_error", "ftk_version",
+    "ftk_track_cp2d", "ftk_track_cp3d", "ftk_result_count", "ftk_result_data",
+    "ftk_result_free", "ftk_plan_create", "ftk_plan_execute", "ftk_plan_count",
+    "ftk_plan_download", "ftk_plan_device_view", "ftk_plan_stage_times", "ftk_plan_destroy",
+]
+
+
+def lib():
+    """Load libftk_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2011_08697_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "ftk_params_default": (None, [ctypes.POINTER(ftk_params)]),
+        "ftk_status_string": (ctypes.c_char_p, [i32]),
+        "ftk_last_error": (ctypes.c_char_p, []),
+        "ftk_version": (ctypes.c_char_p, []),
+        "ftk_track_cp2d": (i32, [vp, i64, i64, i64, ctypes.POINTER(ftk_params), pp, vp]),
+        "ftk_track_cp3d": (i32, [vp, i64, i64, i64, i64, ctypes.POINTER(ftk_params), pp, vp]),
+        "ftk_result_count": (ctypes.c_size_t, [vp]),
+        "ftk_result_data": (vp, [vp]),
+        "ftk_result_free": (None, [vp]),
+        "ftk_plan_create": (i32, [i32, i64, i64, i64, i64, ctypes.POINTER(ftk_params), pp]),
+        "ftk_plan_execute": (i32, [vp, vp, vp]),
+        "ftk_plan_count": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "ftk_plan_download": (i32, [vp, pp]),
+        "ftk_plan_device_view": (i32, [vp, ctypes.POINTER(ftk_device_view)]),
+        "ftk_plan_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
+        "ftk_plan_destroy": (i32, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != FTK_OK:
+        raise FtkError(status, lib().ftk_last_error().decode())
+
+
+def make_params(quant_shift: int = 20, flags: int = 0, max_punctures: int = 0, **kw) -> ftk_params:
+    p = ftk_params()
+    lib().ftk_params_default(ctypes.byref(p))
+    p.quant_shift = quant_shift
+    p.flags = flags
+    p.max_punctures = max_punctures
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _field_ptr(f):
+    """(pointer, keep-alive, shape) for a torch tensor or numpy array."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(f, torch.Tensor):
+        if f.dtype != torch.float32 or not f.is_contiguous():
+            raise ValueError("field must be a contiguous float32 tensor")
+        return ctypes.c_void_p(f.data_ptr()), f, tuple(f.shape)
+    a = np.ascontiguousarray(f, dtype=np.float32)
+    return ctypes.c_void_p(a.ctypes.data), a, a.shape
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _take_result(rp) -> np.ndarray:
+    L = lib()
+    try:
+        n = L.ftk_result_count(rp)
+        data = L.ftk_result_data(rp)
+        out = np.empty(n, dtype=CP_DTYPE)
+        if n:
+            ctypes.memmove(out.ctypes.data, data, n * CP_DTYPE.itemsize)
+        return out
+    finally:
+        L.ftk_result_free(rp)
+
+
+def ftk_track_cp2d(f, params: ftk_params | None = None, stream=None) -> np.ndarray:
+    ptr, keep, shape = _field_ptr(f)
+    if len(shape) != 3:
+        raise ValueError("2D field must have shape (nt, ny, nx)")
+    nt, ny, nx = shape
+    out = ctypes.c_void_p()
+    p = params if params is not None else make_params()
+    _check(lib().ftk_track_cp2d(ptr, nx, ny, nt, ctypes.byref(p), ctypes.byref(out), _stream_ptr(stream)))
+    del keep
+    return _take_result(out)
+
+
+def ftk_track_cp3d(f, params: ftk_params | None = None, stream=None) -> np.ndarray:
+    ptr, keep, shape = _field_ptr(f)
+    if len(shape) != 4:
+        raise ValueError("3D field must have shape (nt, nz, ny, nx)")
+    nt, nz, ny, nx = shape
+    out = ctypes.c_void_p()
+    p = params if params is not None else make_params()
+    _check(lib().ftk_track_cp3d(ptr, nx, ny, nz, nt, ctypes.byref(p), ctypes.byref(out), _stream_ptr(stream)))
+    del keep
+    return _take_result(out)
+
+
+class Plan:
+    """Device workspace for repeated tracking of fields of one shape
+    (``ftk_plan_*``)."""
+
+    def __init__(self, shape, params: ftk_params | None = None):
+        shape = tuple(int(s) for s in shape)
+        if len(shape) == 3:
+            nt, ny, nx = shape
+            nz, ndim = 1, 2
+        elif len(shape) == 4:
+            nt, nz, ny, nx = shape
+            ndim = 3
+        else:
+            raise ValueError("shape must be (nt, ny, nx) or (nt, nz, ny, nx)")
+        self.shape = shape
+        self.ndim = ndim
+        self._p = params if params is not None else make_params()
+        h = ctypes.c_void_p()
+        _check(lib().ftk_plan_create(ndim, nx, ny, nz, nt, ctypes.byref(self._p), ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+
+    def execute(self, f, stream=None):
+        ptr, keep, shape = _field_ptr(f)
+        if tuple(shape) != self.shape:
+            raise ValueError(f"field shape {shape} != plan shape {self.shape}")
+        self._keep = keep
+        _check(lib().ftk_plan_execute(self._h, ptr, _stream_ptr(stream)))
+
+    def count(self) -> int:
+        c = ctypes.c_int64()
+        _check(lib().ftk_plan_count(self._h, ctypes.byref(c)))
+        return c.value
+
+    def download(self) -> np.ndarray:
+        out = ctypes.c_void_p()
+        _check(lib().ftk_plan_download(self._h, ctypes.byref(out)))
+        return _take_result(out)
+
+    def device_view(self) -> ftk_device_view:
+        v = ftk_device_view()
+        _check(lib().ftk_plan_device_view(self._h, ctypes.byref(v)))
+        return v
+
+    def stage_times(self):
+        ms = (ctypes.c_float * 8)()
+        n = ctypes.c_int()
+        _check(lib().ftk_plan_stage_times(self._h, ms, 8, ctypes.byref(n)))
+        return list(ms[: n.value])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ftk_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# C-ABI names for the plan calls
+def ftk_plan_create(shape, params=None) -> Plan:
+    return Plan(shape, params)
+
+
+def ftk_plan_execute(plan: Plan, f, stream=None):
+    plan.execute(f, stream)
+
+
+def ftk_plan_count(plan: Plan) -> int:
+    return plan.count()
+
+
+def ftk_plan_download(plan: Plan) -> np.ndarray:
+    return plan.download()
+
+
+def ftk_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def ftk_version() -> str:
+    return lib().ftk_version().decode()
