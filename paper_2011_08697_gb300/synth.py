@@ -43,18 +43,23 @@ __all__ = [
 
 
 def spiral_woven(n: int, nt: int, sigma: float = 0.0, seed: int = 0,
-                 lo: float = -4.0, hi: float = 4.0, ny: int | None = None) -> np.ndarray:
+                 lo: float = -4.0, hi: float = 4.0, ny: int | None = None,
+                 k_stop: int | None = None) -> np.ndarray:
     """Spiral woven field sampled on an ``ny x n`` grid over ``nt`` steps.
 
     x_i = lo + (hi-lo) i/(n-1) (inclusive linspace), t_k = k/(nt-1).
     Noise N(0, sigma^2) is drawn slice by slice from ``default_rng(seed)``.
+    ``k_stop`` returns only the first k_stop slices (identical to the leading
+    slices of the full field).
     """
     ny = n if ny is None else ny
     x = np.linspace(lo, hi, n)
     y = np.linspace(lo, hi, ny)
     ts = np.linspace(0.0, 1.0, nt) if nt > 1 else np.zeros(1)
     rng = np.random.default_rng(seed)
-    out = np.empty((nt, ny, n), dtype=np.float32)
+    if k_stop is not None:
+        ts = ts[:k_stop]
+    out = np.empty((len(ts), ny, n), dtype=np.float32)
     X = x[None, :]
     Y = y[:, None]
     for k, t in enumerate(ts):
