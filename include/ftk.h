@@ -143,6 +143,43 @@ ftk_status ftk_plan_device_view(ftk_plan *plan, ftk_device_view *view);
 ftk_status ftk_plan_stage_times(ftk_plan *plan, float *ms, int cap, int *n);
 ftk_status ftk_plan_destroy(ftk_plan *plan);
 
+/* ---------------------------------------------------------------------
+ * Tracking without device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code that
+ * runs inside a host application which has already reserved the device's
+ * memory for its own pool (an in situ coupling inside a simulation), code
+ * that must not trigger the implicit device synchronisation that
+ * cudaMalloc/cudaFree may cause, or loops that cannot afford allocation
+ * latency.  It runs the same 2D pipeline as ftk_track_cp2d, but every
+ * scratch array lives in one file-scope device array of
+ * FTK_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU loading the library
+ * holds until the process exits.
+ *
+ *   f_dev    device pointer, nt x ny x nx float32 (host pointers are rejected)
+ *   out_dev  device buffer of out_cap ftk_cp records; receives the punctured
+ *            faces sorted by face_id (same records as ftk_track_cp2d)
+ *   count    host pointer; receives the number of punctured faces, also when
+ *            the call fails with FTK_ERR_NOMEM because they did not fit
+ *
+ * Limits: at most FTK_NOALLOC_MAX_SEGMENTS segments (nt * ceil(ny / rows per
+ * tile)) and FTK_NOALLOC_MAX_PUNCTURES punctured faces per call; larger
+ * grids are rejected with FTK_ERR_ARG, more punctures (or more than out_cap)
+ * with FTK_ERR_NOMEM.  The call allocates nothing (no cudaMalloc, cudaFree
+ * or allocating library routine); it synchronises cuda_stream before it
+ * returns.  The first call on each device looks up the scratch array's
+ * device address (with that device current); make that first call before
+ * any stream capture.  All calls share the one scratch array and it keeps
+ * the previous call's contents (the pipeline clears what must start at
+ * zero), so calls that overlap on the GPU -- from several host threads or
+ * streams at once -- race and must be serialised by the caller.
+ * ------------------------------------------------------------------- */
+#define FTK_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define FTK_NOALLOC_MAX_SEGMENTS 262144
+#define FTK_NOALLOC_MAX_PUNCTURES 1310720
+ftk_status ftk_track_cp2d_noalloc(const float *f_dev, int64_t nx, int64_t ny, int64_t nt,
+                                  const ftk_params *p, ftk_cp *out_dev, int64_t out_cap,
+                                  int64_t *count, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,6 +48,8 @@ bool is_device_pointer(const void *p) {
 
 }  // namespace
 
+void ftk::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 struct ftk_result {
     ftk_cp *data;
     size_t count;

@@ -62,4 +62,7 @@ size_t detect_smem_bytes(int ndim, const Field &F, const Blocking &B);
 cudaError_t launch_pipeline(int ndim, const Field &F, const Blocking &B, const Workspace &W,
                             cudaStream_t s, cudaEvent_t *ev /* 6 events or null */);
 
+// sets the thread-local message returned by ftk_last_error()
+void set_last_error(const char *msg);
+
 }  // namespace ftk

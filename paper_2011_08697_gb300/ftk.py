@@ -55,6 +55,7 @@ EXPORTS = [
     "ftk_track_cp2d", "ftk_track_cp3d", "ftk_result_count", "ftk_result_data",
     "ftk_result_free", "ftk_plan_create", "ftk_plan_execute", "ftk_plan_count",
     "ftk_plan_download", "ftk_plan_device_view", "ftk_plan_stage_times", "ftk_plan_destroy",
+    "ftk_track_cp2d_noalloc",
 ]
 
 
@@ -86,6 +87,8 @@ def lib():
         "ftk_plan_device_view": (i32, [vp, ctypes.POINTER(ftk_device_view)]),
         "ftk_plan_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
         "ftk_plan_destroy": (i32, [vp]),
+        "ftk_track_cp2d_noalloc": (i32, [vp, i64, i64, i64, ctypes.POINTER(ftk_params), vp, i64,
+                                         ctypes.POINTER(ctypes.c_int64), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
