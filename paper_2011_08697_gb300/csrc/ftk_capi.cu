@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -57,6 +58,7 @@ struct ftk_result {
 
 struct ftk_plan {
     int ndim;
+    int variant;               // detect kernel (VAR_*)
     int device;
     Field F;
     Blocking B;
@@ -67,6 +69,7 @@ struct ftk_plan {
     RunCounters *h_ctr;        // pinned mirror of the device counters
     cudaStream_t stream;
     const float *last_f;
+    const float *last_dev;     // device copy the last run read
     bool last_host;
     bool executed;
     bool timing;
@@ -89,7 +92,27 @@ void free_workspace(Workspace &W) {
     cudaFree(W.morse);
     cudaFree(W.label);
     cudaFree(W.packed);
+    cudaFree(W.surv);
+    cudaFree(W.surv_mask);
+    cudaFree(W.surv_off);
+    cudaFree(W.seg_scnt);
+    cudaFree(W.seg_sstage);
     std::memset(&W, 0, sizeof(W));
+}
+
+ftk_status alloc_survivors(Workspace &W, long long scap) {
+    cudaFree(W.surv); W.surv = nullptr;
+    cudaFree(W.surv_mask); W.surv_mask = nullptr;
+    cudaFree(W.surv_off); W.surv_off = nullptr;
+    W.scap = 0;
+    if (cudaMalloc(&W.surv, scap * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&W.surv_mask, scap * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&W.surv_off, scap * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FTK_ERR_NOMEM, "device allocation of the survivor arrays failed");
+    }
+    W.scap = scap;
+    return FTK_OK;
 }
 
 ftk_status alloc_capacity(Workspace &W, long long cap) {
@@ -115,9 +138,47 @@ ftk_status alloc_capacity(Workspace &W, long long cap) {
     return FTK_OK;
 }
 
-ftk_status choose_blocking(int ndim, const Field &F, Blocking &B) {
+int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 148;
+}
+
+// time chunks: split each spatial block's time range so that the units fill
+// whole waves of resident CTAs as closely as possible
+void choose_time_chunks(const Field &F, Blocking &B, long long spatial, long long wave) {
+    long long best_ntc = 1;
+    double best = -1.0;
+    for (long long k = 1; k <= 6; ++k) {
+        long long ntc = std::max<long long>(1, (k * wave) / std::max<long long>(1, spatial));
+        ntc = std::min<long long>(ntc, F.nt);
+        const int tc = (int)((F.nt + ntc - 1) / ntc);
+        ntc = (F.nt + tc - 1) / tc;
+        const long long units = ntc * spatial;
+        const double waves = (double)units / (double)wave;
+        const double fill = waves / std::ceil(waves);        // occupancy of the last wave
+        const double over = 1.0 / tc;                         // re-read slice per chunk
+        const double score = fill - over;
+        if (score > best) { best = score; best_ntc = ntc; }
+    }
+    B.tc = (int)((F.nt + best_ntc - 1) / best_ntc);
+    B.ntc = (F.nt + B.tc - 1) / B.tc;
+}
+
+ftk_status choose_blocking(int ndim, const Field &F, Blocking &B, int &variant) {
     static const int cand2[] = {16, 8, 4, 2, 1};
     static const int cand3[][2] = {{8, 4}, {8, 2}, {4, 4}, {4, 2}, {2, 2}, {2, 1}, {1, 1}};
+    const int sms = sm_count();
+    if (ndim == 2 && F.nx % 4 == 0 && F.nx <= STREAM2_MAX_NX) {
+        variant = VAR_STREAM2;
+        B.ry = STREAM2_ROWS; B.rz = 1;
+        B.nyb = (F.ny + B.ry - 1) / B.ry;
+        B.nzb = 1;
+        choose_time_chunks(F, B, B.nyb, (long long)sms * stream2_ctas_per_sm(F.nx));
+        return FTK_OK;
+    }
+    variant = VAR_TILE;
     bool ok = false;
     if (ndim == 2) {
         for (int ry : cand2) {
@@ -135,9 +196,6 @@ ftk_status choose_blocking(int ndim, const Field &F, Blocking &B) {
     B.nzb = ndim == 3 ? (F.nz + B.rz - 1) / B.rz : 1;
     // enough units to fill the GPU: split time into chunks if the spatial
     // blocks alone are too few
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long spatial = (long long)B.nyb * B.nzb;
     const long long want = 4LL * sms;
     long long chunks = spatial >= want ? 1 : (want + spatial - 1) / spatial;
@@ -168,9 +226,9 @@ ftk_status status_of(unsigned st) {
     return FTK_OK;
 }
 
-ftk_status launch(ftk_plan *pl, const float *dev_f, cudaStream_t s) {
+ftk_status launch(ftk_plan *pl, const float *dev_f, cudaStream_t s, int variant) {
     pl->F.f = dev_f;
-    cudaError_t e = launch_pipeline(pl->ndim, pl->F, pl->B, pl->W, s, pl->timing ? pl->ev : nullptr);
+    cudaError_t e = launch_pipeline(pl->ndim, variant, pl->F, pl->B, pl->W, s, pl->timing ? pl->ev : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "pipeline launch");
     pl->stream = s;
     pl->executed = true;
@@ -180,24 +238,36 @@ ftk_status launch(ftk_plan *pl, const float *dev_f, cudaStream_t s) {
 // synchronise, grow and re-run on overflow, check device status
 ftk_status settle(ftk_plan *pl) {
     if (!pl->executed) return fail(FTK_ERR_STATE, "plan has not been executed");
-    for (int attempt = 0; attempt < 4; ++attempt) {
+    int variant = pl->variant;
+    for (int attempt = 0; attempt < 6; ++attempt) {
         ftk_status s = read_counters(pl);
         if (s != FTK_OK) return s;
         const unsigned st = pl->h_ctr->status;
         if (st & ST_RANGE) return status_of(st);
-        if (!(st & ST_OVERFLOW)) {
+        if (st & ST_WIDE) {
+            // a sample beyond the fast rounding range: redo with exact rounding
+            variant = VAR_STREAM2_EXACT;
+            s = launch(pl, pl->last_dev, pl->stream, variant);
+            if (s != FTK_OK) return s;
+            continue;
+        }
+        if (!(st & (ST_OVERFLOW | ST_SOVERFLOW))) {
             if (pl->timing) {
                 pl->nstage = 5;
                 for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&pl->stage_ms[i], pl->ev[i], pl->ev[i + 1]);
             }
             return status_of(st);
         }
-        const long long need = (long long)pl->h_ctr->staged;
-        long long cap = std::max<long long>(need + need / 4 + 1024, 2 * pl->W.cap);
-        s = alloc_capacity(pl->W, cap);
-        if (s != FTK_OK) return s;
-        const float *src = pl->last_host ? pl->d_input : pl->last_f;
-        s = launch(pl, src, pl->stream);
+        if (st & ST_SOVERFLOW) {
+            const long long need = (long long)pl->h_ctr->survivors;
+            s = alloc_survivors(pl->W, std::max<long long>(need + need / 4 + 1024, 2 * pl->W.scap));
+            if (s != FTK_OK) return s;
+        } else {
+            const long long need = (long long)pl->h_ctr->staged;
+            s = alloc_capacity(pl->W, std::max<long long>(need + need / 4 + 1024, 2 * pl->W.cap));
+            if (s != FTK_OK) return s;
+        }
+        s = launch(pl, pl->last_dev, pl->stream, variant);
         if (s != FTK_OK) return s;
     }
     return fail(FTK_ERR_NOMEM, "puncture capacity did not converge");
@@ -281,10 +351,11 @@ ftk_status ftk_plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t
     cudaGetDevice(&pl->device);
     pl->F.nx = (int)nx; pl->F.ny = (int)ny; pl->F.nz = (int)nz; pl->F.nt = (int)nt;
     pl->F.scale = (float)std::ldexp(1.0, pl->p.quant_shift);
+    field_divisors(pl->F);
     pl->nverts = (long long)nx * ny * nz * nt;
-    s = choose_blocking(ndim, pl->F, pl->B);
+    s = choose_blocking(ndim, pl->F, pl->B, pl->variant);
     if (s != FTK_OK) { delete pl; return s; }
-    pl->W.nseg = (long long)nt * nz * pl->B.nyb;
+    pl->W.nseg = (long long)nt * nz * pl->B.nyb;   // segments (t, z, y-block)
     pl->timing = (pl->p.flags & 1u) != 0;
 
     Workspace &W = pl->W;
@@ -303,6 +374,15 @@ ftk_status ftk_plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t
                         ? pl->p.max_punctures
                         : std::max<long long>(1 << 16, std::min<long long>(pl->nverts / 32, 1LL << 26));
     s = alloc_capacity(W, cap);
+    if (s == FTK_OK && pl->variant != VAR_TILE) {
+        if (cudaMalloc(&W.seg_scnt, W.nseg * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&W.seg_sstage, W.nseg * sizeof(long long)) != cudaSuccess) {
+            cudaGetLastError();
+            s = fail(FTK_ERR_NOMEM, "device allocation failed");
+        } else {
+            s = alloc_survivors(W, std::max<long long>(1 << 16, std::min<long long>(pl->nverts / 32, 1LL << 26)));
+        }
+    }
     if (s != FTK_OK) {
         free_workspace(W);
         cudaFreeHost(pl->h_ctr);
@@ -319,8 +399,10 @@ ftk_status ftk_plan_execute(ftk_plan *pl, const float *f, void *cuda_stream) {
     if (!pl || !f) return fail(FTK_ERR_ARG, "plan and field must be non-NULL");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const bool host = !is_device_pointer(f);
+    // the streaming kernel copies rows with TMA: they must start on 16 bytes
+    const bool misaligned = pl->variant != VAR_TILE && ((uintptr_t)f & 15u) != 0;
     const float *src = f;
-    if (host) {
+    if (host || misaligned) {
         const size_t bytes = (size_t)pl->nverts * sizeof(float);
         if (!pl->d_input) {
             if (cudaMalloc(&pl->d_input, bytes) != cudaSuccess) {
@@ -328,12 +410,13 @@ ftk_status ftk_plan_execute(ftk_plan *pl, const float *f, void *cuda_stream) {
                 return fail(FTK_ERR_NOMEM, "device input buffer allocation failed");
             }
         }
-        FTK_CUDA(cudaMemcpyAsync(pl->d_input, f, bytes, cudaMemcpyHostToDevice, s));
+        FTK_CUDA(cudaMemcpyAsync(pl->d_input, f, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
         src = pl->d_input;
     }
     pl->last_f = f;
+    pl->last_dev = src;
     pl->last_host = host;
-    return launch(pl, src, s);
+    return launch(pl, src, s, pl->variant);
 }
 
 ftk_status ftk_plan_count(ftk_plan *pl, int64_t *count) {

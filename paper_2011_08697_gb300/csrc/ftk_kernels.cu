@@ -5,9 +5,10 @@
 //              march through the time slices; per slice load the tile,
 //              quantise F = rint(f 2^S), integer central-difference gradient,
 //              2N sign bits per vertex; per spacetime cube AND the sign bits
-//              of its corners -- a component that keeps one strict sign on
-//              every corner rules out every face owned by the cube, exactly,
-//              because the symbolic perturbation is infinitesimal.  Surviving
+//              of its corners -- a component that is < 0 on every corner, or
+//              >= 0 on every corner, rules out every face owned by the cube,
+//              exactly: the symbolic perturbation is infinitesimal and adds a
+//              positive term to a zero component.  Surviving
 //              cubes (rare) run the exact SoS predicate on each of their
 //              faces; punctured faces are compacted in face-id order per
 //              segment (t, z, y-block).
@@ -67,13 +68,15 @@ __device__ __noinline__ int sos_fallback(const int32_t (&M)[N][N]) {
 // increasing global-id order.
 template <int N>
 __device__ bool face_punctured(const int32_t (&V)[N + 1][N]) {
-    // a component with one strict sign on every vertex excludes the origin
+    // a component that is < 0 on every vertex, or >= 0 on every vertex,
+    // excludes the origin: SoS perturbs a zero entry by a positive
+    // infinitesimal, so zero counts as positive
 #pragma unroll
     for (int r = 0; r < N; ++r) {
         bool allp = true, alln = true;
 #pragma unroll
         for (int k = 0; k <= N; ++k) {
-            allp &= V[k][r] > 0;
+            allp &= V[k][r] >= 0;
             alln &= V[k][r] < 0;
         }
         if (allp || alln) return false;
@@ -200,7 +203,7 @@ __device__ void make_words(const TileGeom &g, const int32_t *T, uint8_t *Wd) {
         grad_tile<N>(T, g, x, y, z, wy + 1, N == 3 ? wz + 1 : 0, G);
         uint32_t w = 0;
 #pragma unroll
-        for (int c = 0; c < N; ++c) w |= ((uint32_t)(G[c] < 0) << (2 * c)) | ((uint32_t)(G[c] > 0) << (2 * c + 1));
+        for (int c = 0; c < N; ++c) w |= ((uint32_t)(G[c] < 0) << (2 * c)) | ((uint32_t)(G[c] >= 0) << (2 * c + 1));
         Wd[i] = (uint8_t)w;
     }
 }
@@ -406,9 +409,10 @@ __global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W)
 // ----------------------------------------------------------------------------
 // Scan of per-segment counts (one CTA)
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_scan(Workspace W) {
+__global__ void __launch_bounds__(NT) k_scan(Workspace W, int stream_mode) {
     __shared__ long long red[NT / 32 + 1];
     constexpr int PER = 16;
+    if (stream_mode && (W.ctr->status & ST_SOVERFLOW)) return;
     long long run = 0;
     for (long long b0 = 0; b0 < W.nseg; b0 += (long long)NT * PER) {
         const long long i0 = b0 + (long long)threadIdx.x * PER;
@@ -430,7 +434,14 @@ __global__ void __launch_bounds__(NT) k_scan(Workspace W) {
         }
         run += tot;
     }
-    if (threadIdx.x == 0) W.ctr->punctures = run;
+    if (threadIdx.x == 0) {
+        W.ctr->punctures = run;
+        if (stream_mode) {
+            // the streaming variant writes punctures straight to their sorted slots
+            W.ctr->staged = (unsigned long long)run;
+            if (run > W.cap) atomicOr(&W.ctr->status, ST_OVERFLOW);
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------
@@ -476,17 +487,33 @@ __device__ __forceinline__ float i128_to_float(__int128 v) {
     return neg ? -r : r;
 }
 
-template <int N>
-__device__ __forceinline__ Pt decode_face(const Field &F, long long fid, int &tt) {
-    constexpr int T = MeshDims<N>::T;
-    long long g = fid / T;
-    tt = (int)(fid - g * T);
+// coordinates (x, y, z, t) of vertex id g
+__device__ __forceinline__ Pt decode_vertex(const Field &F, long long g) {
     Pt p;
+    if (F.small) {
+        const unsigned u = (unsigned)g;
+        const unsigned r1 = fdiv(u, F.dx);
+        p.c[0] = (int)(u - r1 * (unsigned)F.nx);
+        const unsigned r2 = fdiv(r1, F.dy);
+        p.c[1] = (int)(r1 - r2 * (unsigned)F.ny);
+        const unsigned r3 = fdiv(r2, F.dz);
+        p.c[2] = (int)(r2 - r3 * (unsigned)F.nz);
+        p.c[3] = (int)r3;
+        return p;
+    }
     p.c[0] = (int)(g % F.nx); g /= F.nx;
     p.c[1] = (int)(g % F.ny); g /= F.ny;
     p.c[2] = (int)(g % F.nz); g /= F.nz;
     p.c[3] = (int)g;
     return p;
+}
+
+template <int N>
+__device__ __forceinline__ Pt decode_face(const Field &F, long long fid, int &tt) {
+    constexpr int T = MeshDims<N>::T;
+    const long long g = fid / T;
+    tt = (int)(fid - g * T);
+    return decode_vertex(F, g);
 }
 
 // vertex k of a simplex: base + bits of mask m (axis N of m is time)
@@ -528,6 +555,34 @@ __device__ int morse_from_S(const BigInt<W> (&S)[N][N]) {
         }
     }
     return changes;
+}
+
+// |a| * |b| as a 256-bit magnitude (hi, lo)
+__device__ __forceinline__ void mul_u128(unsigned __int128 a, unsigned __int128 b, unsigned __int128 &hi,
+                                         unsigned __int128 &lo) {
+    const unsigned long long a0 = (unsigned long long)a, a1 = (unsigned long long)(a >> 64);
+    const unsigned long long b0 = (unsigned long long)b, b1 = (unsigned long long)(b >> 64);
+    const unsigned __int128 p00 = (unsigned __int128)a0 * b0;
+    const unsigned __int128 p01 = (unsigned __int128)a0 * b1;
+    const unsigned __int128 p10 = (unsigned __int128)a1 * b0;
+    const unsigned __int128 p11 = (unsigned __int128)a1 * b1;
+    const unsigned __int128 mid = (p00 >> 64) + (unsigned long long)p01 + (unsigned long long)p10;
+    lo = (mid << 64) | (unsigned long long)p00;
+    hi = p11 + (p01 >> 64) + (p10 >> 64) + (mid >> 64);
+}
+
+// sign(a*b - c*d) for signed 128-bit operands, exact
+__device__ int cmp_prod128(__int128 a, __int128 b, __int128 c, __int128 d) {
+    const int s1 = sgn128(a) * sgn128(b), s2 = sgn128(c) * sgn128(d);
+    if (s1 != s2) return s1 > s2 ? 1 : -1;   // also covers zero products
+    if (s1 == 0) return 0;
+    unsigned __int128 h1, l1, h2, l2;
+    mul_u128(a < 0 ? (unsigned __int128)(-a) : (unsigned __int128)a,
+             b < 0 ? (unsigned __int128)(-b) : (unsigned __int128)b, h1, l1);
+    mul_u128(c < 0 ? (unsigned __int128)(-c) : (unsigned __int128)c,
+             d < 0 ? (unsigned __int128)(-d) : (unsigned __int128)d, h2, l2);
+    const int mag = h1 != h2 ? (h1 > h2 ? 1 : -1) : (l1 != l2 ? (l1 > l2 ? 1 : -1) : 0);
+    return s1 > 0 ? mag : -mag;   // both products positive, or both negative
 }
 
 template <int N>
@@ -582,6 +637,21 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
 
     // S = sign(D) sum_k D_k (H_k + H_k^T), exact
     const int sg = sgn128(Dsum);
+    if (N == 2) {
+        // |D_k| < 2^62 and |H + H^T| < 2^34: entries of S fit in int128;
+        // det S = S00 S11 - S01^2 is compared exactly in 256 bits
+        __int128 S00 = 0, S01 = 0, S11 = 0;
+        for (int k = 0; k <= N; ++k) {
+            const __int128 w = sg < 0 ? -D[k] : D[k];
+            S00 += w * (__int128)(2 * hess_global(F, v[k], 0, 0));
+            S11 += w * (__int128)(2 * hess_global(F, v[k], 1, 1));
+            S01 += w * (__int128)(hess_global(F, v[k], 0, 1) + hess_global(F, v[k], 1, 0));
+        }
+        const int d = cmp_prod128(S00, S11, S01, S01);   // sign(S00 S11 - S01 S01)
+        const __int128 tr = S00 + S11;
+        morse = (int8_t)(d < 0 ? 1 : d > 0 ? (tr < 0 ? 2 : 0) : -1);
+        return;
+    }
     BigInt<BW> S[N][N];
 #pragma unroll
     for (int a = 0; a < N; ++a)
@@ -667,11 +737,27 @@ __device__ __forceinline__ long long face_id_of(const Field &F, Pt b, const int 
     return g * T + tt;
 }
 
+// index of face `key` (base vertex b) in the sorted array, searching only
+// its own segment
+__device__ __forceinline__ long long find_in_segment(const Field &F, const Blocking &B, const Workspace &W,
+                                                     const Pt &b, long long key) {
+    const long long seg = segment_of_coords(b.c[1], b.c[2], b.c[3], F, B);
+    const long long lo0 = W.seg_off[seg];
+    const long long hi0 = lo0 + W.seg_cnt[seg];
+    long long lo = lo0, hi = hi0;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (W.face[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < hi0 && W.face[lo] == key) ? lo : -1;
+}
+
 template <int N>
-__global__ void __launch_bounds__(NT) k_link(Field F, Workspace W) {
+__global__ void __launch_bounds__(NT) k_link(Field F, Blocking B, Workspace W) {
     constexpr int D = N + 1;
     constexpr int FULL = (1 << D) - 1;
-    if (W.ctr->status & ST_OVERFLOW) return;
+    if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
     const long long P = W.ctr->punctures;
     unsigned *status = &W.ctr->status;
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
@@ -737,21 +823,22 @@ __global__ void __launch_bounds__(NT) k_link(Field F, Workspace W) {
                 }
                 const long long sid = face_id_of<N>(F, sb, sm);
                 if (sid == fid) continue;
-                const long long j = find_face(W.face, P, sid);
+                const long long j = find_in_segment(F, B, W, sb, sid);
                 if (j >= 0) { ++hits; partner = j; }
             }
             if (hits != 1) {
                 atomicOr(status, ST_PAIRING);
                 continue;
             }
-            uf_unite(W.parent, (int)i, (int)partner, status);
+            // both ends see the pair; one union suffices
+            if (partner > i) uf_unite(W.parent, (int)i, (int)partner, status);
         }
     }
 }
 
 template <int N>
 __global__ void __launch_bounds__(NT) k_label(Field F, Workspace W) {
-    if (W.ctr->status & ST_OVERFLOW) return;
+    if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
     const long long P = W.ctr->punctures;
     unsigned *status = &W.ctr->status;
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
@@ -776,6 +863,505 @@ __global__ void __launch_bounds__(NT) k_label(Field F, Workspace W) {
 }
 
 // ----------------------------------------------------------------------------
+// Streaming 2D detect kernel (rows of nx % 4 == 0 floats, 16-byte aligned).
+//
+// One CTA per unit = (block of RY2 cube rows, time chunk), three warp roles:
+//  * producer warp: streams the unit's rows -- slice after slice, the clamped
+//    rows y0-1 .. y0+RY2+1 -- into a ring of NS2 shared-memory row slots with
+//    1D bulk TMA copies (cp.async.bulk; an mbarrier per slot counts the
+//    bytes, a second one counts the consumer warps that released the slot);
+//  * consumer warps: a thread owns CX = 8 columns; it reads each row once
+//    (two float4 plus three clamped neighbours), quantises, forms the integer
+//    gradient of the previous row and packs the 18 sign bits of (G_x, G_y) at
+//    9 columns with funnel shifts.  The exact cube cull of its 8 cubes is
+//    then bit-parallel: AND/OR of x pairs, y pairs (previous row) and time
+//    pairs (one 32-bit word per cube row kept in a register across slices).
+//    Grid edges need no branches in the row code: clamped rows/columns make
+//    every one-sided difference a doubled central difference;
+//  * compactor warp: at the end of each slab it turns the slab's survivor
+//    bitmap (double-buffered; mbarrier handshake with the consumers) into an
+//    ordered list of surviving cubes in global memory.
+// No CTA-wide barrier runs inside the main loop.
+// ----------------------------------------------------------------------------
+constexpr int RY2 = 16;       // cube rows per unit
+constexpr int NS2 = 16;       // TMA ring slots (rows)
+constexpr int CX = 8;         // columns per consumer thread
+constexpr long long WAIT_CYCLES = 4000000000LL;   // bound of every mbarrier wait (~2 s)
+constexpr uint32_t MAGIC_BITS = 0x4B400000u;      // bit pattern of 1.5 * 2^23
+constexpr float MAGIC_F = 12582912.0f;            // 1.5 * 2^23
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait on a phase; false if it did not complete within WAIT_CYCLES
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_row(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// quantised sample in offset encoding: MAGIC_BITS + rint(v 2^S) (mod 2^32);
+// differences of two encodings are exact integer differences
+template <bool EXACT>
+__device__ __forceinline__ uint32_t qbits(float v, float scale, uint32_t &bad) {
+    if (EXACT) {
+        const float w = v * scale;
+        if (!(fabsf(w) <= RANGE_LIMIT)) bad |= 1u;
+        return (uint32_t)(fabsf(w) <= RANGE_LIMIT ? __float2int_rn(w) : 0) + MAGIC_BITS;
+    }
+    // v * 2^S + 1.5 * 2^23 rounds to the nearest integer (ties to even) in
+    // the mantissa whenever |v * 2^S| <= 2^22; bits - MAGIC_BITS = rint(v 2^S)
+    return __float_as_uint(__fmaf_rn(v, scale, MAGIC_F));
+}
+
+__host__ __device__ inline int stream2_consumers(int nx) { return ((nx + CX - 1) / CX + 31) / 32 * 32; }
+
+struct Stream2Layout {
+    int ring, bars, bm, bmw, total;
+};
+__host__ __device__ inline Stream2Layout stream2_layout(int nx) {
+    Stream2Layout L;
+    L.ring = 0;
+    L.bars = L.ring + NS2 * nx * 4;
+    L.bmw = (RY2 * nx + 31) / 32;
+    L.bm = round_up16(L.bars + (2 * NS2 + 4) * 8);
+    L.total = round_up16(L.bm + 2 * L.bmw * 4);
+    return L;
+}
+
+// Word of one G row's pairs: bits 0-7 / 16-23 = G_x / G_y "both corners of the
+// x pair negative" (AND), bits 8-15 / 24-31 = "some corner negative" (OR).
+// Input: sign bits of G_x at bits 0-8 and of G_y at bits 16-24.
+__device__ __forceinline__ uint32_t pair_word(uint32_t w) {
+    const uint32_t s = w >> 1;
+    return ((w & s) & 0x00FF00FFu) | (((w | s) & 0x00FF00FFu) << 8);
+}
+// AND on the all-negative bits, OR on the some-negative bits
+__device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b) {
+    return ((a & b) & 0x00FF00FFu) | ((a | b) & 0xFF00FF00u);
+}
+// cubes (bit k) where both components have corners of both signs
+__device__ __forceinline__ uint32_t survivors8(uint32_t c) {
+    const uint32_t mixed = (c >> 8) & ~c & 0x00FF00FFu;
+    return mixed & (mixed >> 16) & 0xFFu;
+}
+
+template <bool EXACT, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking B, Workspace W) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nx = F.nx, ny = F.ny, nt = F.nt;
+    const int NC = (int)blockDim.x - 64;
+    const int CW = NC >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Stream2Layout L = stream2_layout(nx);
+    float *ring = reinterpret_cast<float *>(smem + L.ring);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bars);
+    uint64_t *empty = full + NS2;
+    uint64_t *done = empty + NS2;    // [2] slab bits complete (consumer warps arrive)
+    uint64_t *freed = done + 2;      // [2] bitmap compacted and cleared (compactor arrives)
+    uint32_t *bm = reinterpret_cast<uint32_t *>(smem + L.bm);   // [2][bmw]
+    unsigned *status = &W.ctr->status;
+
+    const int tci = blockIdx.x % B.ntc;
+    const int yb = blockIdx.x / B.ntc;
+    const int y0 = yb * RY2;
+    const int t0 = tci * B.tc;
+    const int t_end = min(nt, t0 + B.tc);
+    const int s_last = min(t_end, nt - 1);
+    const int nsl = s_last - t0 + 1;      // slices streamed
+    const int nslab = t_end - t0;         // slabs (base slices) owned
+    constexpr int RS = RY2 + 3;           // rows streamed per slice
+    const int J = nsl * RS;
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NS2; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], CW);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&done[b], CW);
+            mbar_init(&freed[b], 1);
+        }
+        mbar_fence_init();
+    }
+    for (int i = threadIdx.x; i < 2 * L.bmw; i += blockDim.x) bm[i] = 0u;
+    __syncthreads();
+
+    if (warp == CW) {
+        // ---------------- producer ----------------------------------------
+        if (lane == 0) {
+            int issued = 0;
+            bool ok = true;
+            for (int j = 0; j < J; ++j) {
+                const int slot = j % NS2;
+                if (j >= NS2 && !mbar_wait(&empty[slot], ((j / NS2) + 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                const int s = t0 + j / RS;
+                const int y = min(max(y0 - 1 + j % RS, 0), ny - 1);
+                mbar_arrive_expect_tx(&full[slot], (uint32_t)nx * 4u);
+                tma_row(ring + (size_t)slot * nx, F.f + ((long long)s * ny + y) * nx, (uint32_t)nx * 4u, &full[slot]);
+                issued = j + 1;
+            }
+            if (!ok) {
+                atomicOr(status, ST_TIMEOUT);
+                // never leave a copy in flight into a CTA that is exiting
+                for (int j = max(0, issued - NS2); j < issued; ++j) mbar_wait(&full[j % NS2], (j / NS2) & 1);
+            }
+        }
+        return;
+    }
+    if (warp == CW + 1) {
+        // ---------------- compactor ---------------------------------------
+        const int per = (L.bmw + 31) / 32;
+        const int w0 = min(L.bmw, lane * per), w1 = min(L.bmw, w0 + per);
+        for (int q = 0; q < nslab; ++q) {
+            const int b = q & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&done[b], (q >> 1) & 1))) {
+                if (lane == 0) atomicOr(status, ST_TIMEOUT);
+                return;
+            }
+            uint32_t *words = bm + b * L.bmw;
+            int cnt = 0;
+            for (int w = w0; w < w1; ++w) cnt += __popc(words[w]);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int t = t0 + q;
+            const long long seg = (long long)t * B.nyb + yb;
+            long long base = 0;
+            if (lane == 0) {
+                base = total ? (long long)atomicAdd(&W.ctr->survivors, (unsigned long long)total) : 0;
+                W.seg_scnt[seg] = total;
+                W.seg_sstage[seg] = base;
+                if (base + total > W.scap) atomicOr(status, ST_SOVERFLOW);
+            }
+            base = __shfl_sync(0xffffffffu, base, 0);
+            long long pos = base + incl - cnt;
+            for (int w = w0; w < w1; ++w) {
+                uint32_t bits = words[w];
+                words[w] = 0u;
+                while (bits) {
+                    const int bit = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int idx = w * 32 + bit;
+                    const long long g = ((long long)t * ny + y0 + idx / nx) * nx + idx % nx;
+                    if (pos < W.scap) W.surv[pos] = g;
+                    ++pos;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&freed[b]);
+        }
+        return;
+    }
+
+    // ---------------- consumers ---------------------------------------------
+    const int x0 = (int)threadIdx.x * CX;
+    const bool act = x0 < nx;
+    const int ncol = act ? min(CX, nx - x0) : 0;           // 8, or 4 on the last thread
+    const uint32_t vmask = ncol == 8 ? 0xFFu : ncol == 4 ? 0x0Fu : 0u;
+    const int xa = act ? x0 : 0;                           // safe address for idle threads
+    const int xb = ncol == 8 ? x0 + 4 : xa;                // second float4 (duplicate when absent)
+    const int xl = max(xa - 1, 0);
+    const int xr1 = min(xa + CX, nx - 1);
+    const int xr2 = min(xa + CX + 1, nx - 1);
+    const bool dbl0 = x0 == 0;                             // one-sided difference at x = 0
+    const bool dbl7 = ncol == 8 && x0 + 8 == nx;           // ... at x = nx-1 (column 7)
+    const bool dbl3 = ncol == 4;                           // ... at x = nx-1 (column 3)
+    const float scale = F.scale;
+    uint32_t bad = 0, dummy = 0;
+    uint32_t st[RY2];
+#pragma unroll
+    for (int i = 0; i < RY2; ++i) st[i] = 0;
+    uint32_t fa[11], fb[11], fc[11];
+#pragma unroll
+    for (int k = 0; k < 11; ++k) fa[k] = fb[k] = fc[k] = MAGIC_BITS;
+    uint32_t pprev = 0;
+    int j = 0;
+    bool ok = true;
+
+    for (int sl = 0; sl < nsl && ok; ++sl) {
+        // slice sl > 0 completes slab q = sl-1, whose bits go to buffer q & 1:
+        // wait until the compactor has released that buffer (slab q-2)
+        const int q = sl - 1;
+        uint32_t *bq = bm + (q & 1) * L.bmw;
+        if (sl > 0 && q >= 2 && !mbar_wait(&freed[q & 1], ((q >> 1) - 1) & 1)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+#pragma unroll
+        for (int vi = 0; vi < RS; ++vi) {
+            const int slot = j % NS2;
+            if (ok && !mbar_wait(&full[slot], (j / NS2) & 1)) ok = false;
+            ok = __all_sync(0xffffffffu, ok);   // keep the warp converged
+            if (ok) {
+                const float *r = ring + (size_t)slot * nx;
+                const float4 c0 = *reinterpret_cast<const float4 *>(r + xa);
+                const float4 c1 = *reinterpret_cast<const float4 *>(r + xb);
+                fc[1] = qbits<EXACT>(c0.x, scale, bad);
+                fc[2] = qbits<EXACT>(c0.y, scale, bad);
+                fc[3] = qbits<EXACT>(c0.z, scale, bad);
+                fc[4] = qbits<EXACT>(c0.w, scale, bad);
+                fc[5] = qbits<EXACT>(c1.x, scale, bad);
+                fc[6] = qbits<EXACT>(c1.y, scale, bad);
+                fc[7] = qbits<EXACT>(c1.z, scale, bad);
+                fc[8] = qbits<EXACT>(c1.w, scale, bad);
+                if (ncol == 4) {
+                    // columns x0+4.. do not exist: clamp to column nx-1
+                    fc[5] = fc[6] = fc[7] = fc[8] = fc[4];
+                }
+                fc[0] = qbits<EXACT>(r[xl], scale, dummy);
+                fc[9] = qbits<EXACT>(r[xr1], scale, dummy);
+                fc[10] = qbits<EXACT>(r[xr2], scale, dummy);
+                if (!EXACT) {
+                    // every own sample must lie in the fast rounding range
+                    const uint32_t a = fc[1] & fc[2] & fc[3] & fc[4] & fc[5] & fc[6] & fc[7] & fc[8];
+                    const uint32_t o = fc[1] | fc[2] | fc[3] | fc[4] | fc[5] | fc[6] | fc[7] | fc[8];
+                    bad |= act ? ((a ^ MAGIC_BITS) | (o ^ MAGIC_BITS)) & 0xFF800000u : 0u;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            }
+            ++j;
+            // G row u = y0 - 2 + vi (rows u-1, u, u+1 are fa, fb, fc, clamped)
+            const int u = y0 - 2 + vi;
+            if (vi >= 2 && u <= ny - 1) {
+                uint32_t gx[9], gy[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    gx[k] = fb[k + 2] - fb[k];
+                    gy[k] = fc[k + 1] - fa[k + 1];
+                }
+                if (u == 0 || u == ny - 1) {
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) gy[k] <<= 1;
+                }
+                gx[0] = dbl0 ? gx[0] << 1 : gx[0];
+                gx[7] = dbl7 ? gx[7] << 1 : gx[7];
+                gx[3] = dbl3 ? gx[3] << 1 : gx[3];
+                if (dbl7) { gx[8] = gx[7]; gy[8] = gy[7]; }      // no column x0+8: duplicate
+                if (dbl3) { gx[4] = gx[3]; gy[4] = gy[3]; }      // no column x0+4
+                // bit 31 of each (wrapped) difference is the sign of G
+                uint32_t w = 0;
+#pragma unroll
+                for (int k = 8; k >= 0; --k) w = __funnelshift_l(gy[k], w, 1);
+                w <<= 7;
+#pragma unroll
+                for (int k = 8; k >= 0; --k) w = __funnelshift_l(gx[k], w, 1);
+                const uint32_t p = pair_word(w);
+                // cube row c = u-1 (G rows u-1, u); at the top edge cube row u alone
+                if (vi >= 3) {
+                    const int i = vi >= 3 ? vi - 3 : 0;
+                    const uint32_t sq = combine(pprev, p);
+                    if (sl > 0) {
+                        const uint32_t sv8 = survivors8(combine(sq, st[i])) & vmask;
+                        if (sv8) {
+                            const int idx = i * nx + x0;
+                            atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
+                            if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
+                        }
+                    }
+                    st[i] = sq;
+                }
+                if (u == ny - 1 && vi >= 2 && vi - 2 < RY2) {
+                    const int i = vi >= 2 ? vi - 2 : 0;
+                    if (sl > 0) {
+                        const uint32_t sv8 = survivors8(combine(p, st[i])) & vmask;
+                        if (sv8) {
+                            const int idx = i * nx + x0;
+                            atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
+                            if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
+                        }
+                    }
+                    st[i] = p;
+                }
+                pprev = p;
+            }
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                fa[k] = fb[k];
+                fb[k] = fc[k];
+            }
+        }
+        if (sl > 0) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&done[q & 1]);
+        }
+    }
+    if (ok && t_end == nt) {
+        // base slice nt-1 has no later slice: its cubes use that slice alone
+        const int q = nslab - 1;
+        uint32_t *bq = bm + (q & 1) * L.bmw;
+        if (q >= 2 && !mbar_wait(&freed[q & 1], ((q >> 1) - 1) & 1)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        if (ok) {
+#pragma unroll
+            for (int i = 0; i < RY2; ++i) {
+                if (y0 + i < ny) {
+                    const uint32_t sv8 = survivors8(st[i]) & vmask;
+                    if (sv8) {
+                        const int idx = i * nx + x0;
+                        atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
+                        if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&done[q & 1]);
+        }
+    }
+    if (!ok) atomicOr(status, ST_TIMEOUT);
+    if (bad & (EXACT ? 1u : 0xFF800000u)) atomicOr(status, EXACT ? ST_RANGE : ST_WIDE);
+}
+
+// ----------------------------------------------------------------------------
+// Surviving cubes of the streaming variant: exact evaluation, ordered output
+// ----------------------------------------------------------------------------
+// bit tt of the result set iff face type tt based at vertex g is punctured
+template <int N>
+__device__ unsigned long long eval_cube(const Field &F, long long g) {
+    constexpr int D = N + 1;
+    constexpr int NCRN = 1 << D;
+    constexpr int T = MeshDims<N>::T;
+    const Pt b = decode_vertex(F, g);
+    int inside = 0;   // bit a: axis a can step +1
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const int slot = a == N ? 3 : a;
+        const int ext = a == N ? F.nt : ext_of(F, a);
+        if (b.c[slot] + 1 < ext) inside |= 1 << a;
+    }
+    int32_t Gc[NCRN][N];
+#pragma unroll
+    for (int c = 0; c < NCRN; ++c) {
+        if (c & ~inside) {
+#pragma unroll
+            for (int r = 0; r < N; ++r) Gc[c][r] = 0;
+            continue;
+        }
+        const Pt p = add_mask<N>(b, c);
+#pragma unroll
+        for (int r = 0; r < N; ++r) Gc[c][r] = grad_global(F, p, r);
+    }
+    unsigned long long m = 0;
+    for (int tt = 0; tt < T; ++tt) {
+        const uint8_t *ch = mesh<N>().face[tt];
+        if (ch[N - 1] & ~inside) continue;   // the face leaves the grid
+        int32_t V[N + 1][N];
+#pragma unroll
+        for (int k = 0; k <= N; ++k) {
+            const int c = k == 0 ? 0 : ch[k - 1];
+#pragma unroll
+            for (int r = 0; r < N; ++r) V[k][r] = Gc[c][r];
+        }
+        if (face_punctured<N>(V)) m |= 1ull << tt;
+    }
+    return m;
+}
+
+// one CTA per segment (grid-stride): evaluate its survivors, local scan of
+// their puncture counts, segment total
+template <int N>
+__global__ void __launch_bounds__(NT) k_survive(Field F, Workspace W) {
+    __shared__ long long red[NT / 32 + 1];
+    if (W.ctr->status & ST_SOVERFLOW) return;
+    for (long long seg = blockIdx.x; seg < W.nseg; seg += gridDim.x) {
+        const int n = W.seg_scnt[seg];
+        if (n == 0) {
+            if (threadIdx.x == 0) W.seg_cnt[seg] = 0;
+            continue;
+        }
+        const long long base = W.seg_sstage[seg];
+        long long run = 0;
+        for (int b0 = 0; b0 < n; b0 += NT) {
+            const int q = b0 + threadIdx.x;
+            unsigned long long m = 0;
+            if (q < n) {
+                m = eval_cube<N>(F, W.surv[base + q]);
+                W.surv_mask[base + q] = m;
+            }
+            long long tot;
+            const long long ex = block_excl_scan<long long>(__popcll(m), red, tot);
+            if (q < n) W.surv_off[base + q] = (int)(run + ex);
+            run += tot;
+        }
+        if (threadIdx.x == 0) W.seg_cnt[seg] = (int)run;
+    }
+}
+
+// per surviving cube: write its punctured faces at their sorted positions
+template <int N>
+__global__ void __launch_bounds__(NT) k_emit(Field F, Blocking B, Workspace W) {
+    constexpr int T = MeshDims<N>::T;
+    if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
+    const unsigned long long ns = W.ctr->survivors;
+    for (long long s = blockIdx.x * (long long)NT + threadIdx.x; s < (long long)ns; s += (long long)gridDim.x * NT) {
+        unsigned long long m = W.surv_mask[s];
+        if (!m) continue;
+        const long long g = W.surv[s];
+        long long i = W.seg_off[segment_of(g, F, B)] + W.surv_off[s];
+        while (m) {
+            const int tt = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            W.face[i] = g * T + tt;
+            W.parent[i] = (int)i;
+            ++i;
+        }
+    }
+}
+
+// per puncture: location and Morse type
+template <int N>
+__global__ void __launch_bounds__(NT) k_locate(Field F, Workspace W) {
+    if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
+    const long long P = W.ctr->punctures;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        float4 o;
+        int8_t mo;
+        locate_classify<N>(F, W.face[i], o, mo);
+        W.off[i] = o;
+        W.morse[i] = mo;
+    }
+}
+
+// ----------------------------------------------------------------------------
 // Host-side launch helpers
 // ----------------------------------------------------------------------------
 size_t detect_smem_bytes(int ndim, const Field &F, const Blocking &B) {
@@ -794,37 +1380,80 @@ static int sparse_grid() {
     return g;
 }
 
+size_t stream2_smem_bytes(int nx) { return (size_t)stream2_layout(nx).total; }
+int stream2_threads(int nx) { return stream2_consumers(nx) + 64; }
+
+// rows up to 1024 floats: 192 threads, three CTAs per SM; wider rows: up to 320
+template <bool EXACT>
+static void *stream2_kernel(int nx) {
+    if (nx <= 1024) return (void *)k_detect2_stream<EXACT, 192, 3>;
+    return (void *)k_detect2_stream<EXACT, 320, 1>;
+}
+
+int stream2_ctas_per_sm(int nx) {
+    int n = 0;
+    const size_t smem = stream2_smem_bytes(nx);
+    const void *k = stream2_kernel<false>(nx);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, stream2_threads(nx), smem);
+    return n > 0 ? n : 1;
+}
+
 template <int N>
-static cudaError_t launch_all(const Field &F, const Blocking &B, const Workspace &W, cudaStream_t s,
+static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, const Workspace &W, cudaStream_t s,
                               cudaEvent_t *ev) {
-    const size_t smem = detect_smem_bytes(N, F, B);
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_detect<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
-    const long long units = (long long)B.ntc * B.nyb * B.nzb;
     const int sg = sparse_grid();
     if (ev) cudaEventRecord(ev[0], s);
-    k_detect<N><<<(unsigned)units, NT, smem, s>>>(F, B, W);
+    if (N == 2 && variant != VAR_TILE) {
+        const size_t smem = stream2_smem_bytes(F.nx);
+        const void *k = variant == VAR_STREAM2_EXACT ? stream2_kernel<true>(F.nx) : stream2_kernel<false>(F.nx);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const unsigned units = (unsigned)((long long)B.ntc * B.nyb);
+        Field Fa = F;
+        Blocking Ba = B;
+        Workspace Wa = W;
+        void *args[] = {&Fa, &Ba, &Wa};
+        e = cudaLaunchKernel(k, dim3(units), dim3(stream2_threads(F.nx)), args, smem, s);
+        if (e != cudaSuccess) return e;
+    } else {
+        const size_t smem = detect_smem_bytes(N, F, B);
+        static size_t configured = 0;
+        if (smem > configured) {
+            cudaError_t e = cudaFuncSetAttribute(k_detect<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            configured = smem;
+        }
+        const long long units = (long long)B.ntc * B.nyb * B.nzb;
+        k_detect<N><<<(unsigned)units, NT, smem, s>>>(F, B, W);
+    }
     if (ev) cudaEventRecord(ev[1], s);
-    k_scan<<<1, NT, 0, s>>>(W);
+    const bool stream = N == 2 && variant != VAR_TILE;
+    if (stream) {
+        const long long ng = W.nseg < 65535LL * 8 ? W.nseg : 65535LL * 8;
+        k_survive<N><<<(unsigned)(ng > 0 ? ng : 1), NT, 0, s>>>(F, W);
+    }
+    k_scan<<<1, NT, 0, s>>>(W, stream ? 1 : 0);
     if (ev) cudaEventRecord(ev[2], s);
-    k_finalize<N><<<sg, NT, 0, s>>>(F, B, W);
+    if (stream) {
+        k_emit<N><<<sg, NT, 0, s>>>(F, B, W);
+        k_locate<N><<<sg, NT, 0, s>>>(F, W);
+    } else {
+        k_finalize<N><<<sg, NT, 0, s>>>(F, B, W);
+    }
     if (ev) cudaEventRecord(ev[3], s);
-    k_link<N><<<sg, NT, 0, s>>>(F, W);
+    k_link<N><<<sg, NT, 0, s>>>(F, B, W);
     if (ev) cudaEventRecord(ev[4], s);
     k_label<N><<<sg, NT, 0, s>>>(F, W);
     if (ev) cudaEventRecord(ev[5], s);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pipeline(int ndim, const Field &F, const Blocking &B, const Workspace &W,
+cudaError_t launch_pipeline(int ndim, int variant, const Field &F, const Blocking &B, const Workspace &W,
                             cudaStream_t s, cudaEvent_t *ev) {
     cudaError_t e = cudaMemsetAsync(W.ctr, 0, sizeof(RunCounters), s);
     if (e != cudaSuccess) return e;
-    return ndim == 2 ? launch_all<2>(F, B, W, s, ev) : launch_all<3>(F, B, W, s, ev);
+    return ndim == 2 ? launch_all<2>(variant, F, B, W, s, ev) : launch_all<3>(variant, F, B, W, s, ev);
 }
 
 }  // namespace ftk

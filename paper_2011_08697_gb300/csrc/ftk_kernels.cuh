@@ -12,21 +12,56 @@ enum : unsigned {
     ST_OVERFLOW = 2u,   // staging capacity exceeded (count is still exact)
     ST_PAIRING = 4u,    // a cell with a punctured-side count other than 0 or 2
     ST_TIMEOUT = 8u,    // bounded device loop gave up
+    ST_WIDE = 16u,      // a value outside the fast rounding range: rerun exactly
+    ST_SOVERFLOW = 32u, // survivor capacity exceeded (count is still exact)
 };
 
 // Device-resident counters of one pipeline run (one memset clears them).
 struct RunCounters {
     unsigned status;
     unsigned pad;
-    unsigned long long staged;   // punctures written (or attempted) to staging
-    long long punctures;         // final count P (set by the scan kernel)
+    unsigned long long staged;     // punctures written (or attempted) to staging
+    long long punctures;           // final count P (set by the scan kernel)
+    unsigned long long survivors;  // spacetime cubes that survived the sign cull
 };
+
+// Division by a fixed divisor d for numerators n < 2^31: with
+// l = ceil(log2 d) and m = ceil(2^(31+l) / d), floor(n / d) = (n m) >> (31+l),
+// because n m / 2^(31+l) exceeds n / d by less than n / 2^(31+l) < 2^-l <= 1/d,
+// which cannot carry the fractional part (at most (d-1)/d) past an integer.
+struct FastDiv {
+    unsigned long long m;
+    int shift;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    const unsigned long long num = 1ull << (31 + l);
+    f.m = (num + d - 1) / d;
+    f.shift = 31 + l;
+    return f;
+}
+__host__ __device__ inline unsigned fdiv(unsigned n, const FastDiv &f) {
+    return (unsigned)(((unsigned long long)n * f.m) >> f.shift);
+}
 
 struct Field {
     const float *f;      // C-contiguous f[t][z][y][x]
     int nx, ny, nz, nt;  // nz = 1 in 2D
     float scale;         // 2^quant_shift
+    int small;           // nx*ny*nz*nt < 2^31: vertex ids decode with FastDiv
+    FastDiv dx, dy, dz;  // division by nx, ny, nz
 };
+
+// fills the FastDiv fields of a Field whose extents are set
+inline void field_divisors(Field &F) {
+    F.dx = make_fastdiv((unsigned)F.nx);
+    F.dy = make_fastdiv((unsigned)F.ny);
+    F.dz = make_fastdiv((unsigned)F.nz);
+    const double nv = (double)F.nx * F.ny * F.nz * F.nt;
+    F.small = nv < 2147483648.0 ? 1 : 0;
+}
 
 struct Blocking {
     int ry, rz;          // rows / planes of base vertices per unit
@@ -48,18 +83,46 @@ struct Workspace {
     ftk_cp *packed;          // [cap] host-layout records
     long long cap;
     long long nseg;
+    // streaming variant: surviving cubes, evaluated after the dense pass
+    long long *surv;                // [scap] vertex id of each surviving cube, per-segment runs
+    unsigned long long *surv_mask;  // [scap] punctured face types of the cube
+    int *surv_off;                  // [scap] first puncture of the cube within its segment
+    int *seg_scnt;                  // [nseg] survivors per segment
+    long long *seg_sstage;          // [nseg] start of the segment's run in surv
+    long long scap;
 };
 
 // segment = (t, z, y-block): a contiguous run of face ids
+__host__ __device__ inline long long segment_of_coords(int y, int z, int t, const Field &F, const Blocking &B) {
+    return ((long long)t * F.nz + z) * B.nyb + y / B.ry;
+}
 __host__ __device__ inline long long segment_of(long long g, const Field &F, const Blocking &B) {
+    if (F.small) {
+        const unsigned row = fdiv((unsigned)g, F.dx);            // (t*nz + z)*ny + y
+        const unsigned tz = fdiv(row, F.dy);
+        const unsigned y = row - tz * (unsigned)F.ny;
+        return (long long)tz * B.nyb + y / B.ry;
+    }
     const long long row = g / F.nx;             // (t*nz + z)*ny + y
     const long long y = row % F.ny;
     const long long tz = row / F.ny;            // t*nz + z
     return tz * B.nyb + y / B.ry;
 }
 
+// detect-kernel variants
+enum : int {
+    VAR_TILE = 0,           // smem-tile kernel: any 2D/3D shape
+    VAR_STREAM2 = 1,        // streaming 2D kernel (nx % 4 == 0, 16-byte aligned rows)
+    VAR_STREAM2_EXACT = 2,  // same, exact rounding for |f 2^S| > 2^22
+};
+constexpr int STREAM2_ROWS = 16;      // cube rows per unit of the streaming kernel
+constexpr int STREAM2_MAX_NX = 2048;  // widest row the streaming kernel takes
+
 size_t detect_smem_bytes(int ndim, const Field &F, const Blocking &B);
-cudaError_t launch_pipeline(int ndim, const Field &F, const Blocking &B, const Workspace &W,
+size_t stream2_smem_bytes(int nx);
+int stream2_threads(int nx);
+int stream2_ctas_per_sm(int nx);
+cudaError_t launch_pipeline(int ndim, int variant, const Field &F, const Blocking &B, const Workspace &W,
                             cudaStream_t s, cudaEvent_t *ev /* 6 events or null */);
 
 // sets the thread-local message returned by ftk_last_error()

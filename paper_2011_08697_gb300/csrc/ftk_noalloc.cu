@@ -91,6 +91,7 @@ extern "C" ftk_status ftk_track_cp2d_noalloc(const float *f_dev, int64_t nx, int
     F.f = f_dev;
     F.nx = (int)nx; F.ny = (int)ny; F.nz = 1; F.nt = (int)nt;
     F.scale = (float)std::ldexp(1.0, prm.quant_shift);
+    field_divisors(F);
 
     Blocking B;
     static const int cand[] = {16, 8, 4, 2, 1};
@@ -146,7 +147,7 @@ extern "C" ftk_status ftk_track_cp2d_noalloc(const float *f_dev, int64_t nx, int
     W.nseg = nseg;
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    cudaError_t e = launch_pipeline(2, F, B, W, st, nullptr);
+    cudaError_t e = launch_pipeline(2, VAR_TILE, F, B, W, st, nullptr);
     if (e != cudaSuccess) return cuda_err(e, "pipeline launch");
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_err(e, "cudaStreamSynchronize");

@@ -49,6 +49,17 @@ CASES = [
     ("tiny3d_2x2x2x2", lambda: synth.random_levels((2, 2, 2, 2), seed=11), 20),
     ("thin2d_2x50x7", lambda: synth.random_levels((7, 50, 2), seed=12), 20),
     ("zero_field", lambda: np.zeros((3, 8, 9), np.float32), 20),
+    # shapes taking the streaming 2D kernel (nx % 4 == 0)
+    ("stream_levels_36x23x5", lambda: synth.random_levels((5, 23, 36), seed=13), 20),
+    ("stream_levels_4x40x3", lambda: synth.random_levels((3, 40, 4), seed=14), 20),
+    ("stream_levels5_8x17x2", lambda: synth.random_levels((2, 17, 8), levels=(-1, -.5, 0, .5, 1), seed=15), 20),
+    ("stream_zero_12x10x3", lambda: np.zeros((3, 10, 12), np.float32), 20),
+    ("stream_nt1_64x48", lambda: synth.spiral_woven(64, 1, ny=48), 20),
+    ("stream_wide_values", lambda: (synth.spiral_woven(64, 6, sigma=0.01, seed=5, ny=48) * 10.0), 20),
+    ("stream_blobs_256x100x40", lambda: synth.gaussian_blobs((256, 100), 40, nblobs=30, seed=16,
+                                                              sigma_range=(2.0, 9.0)), 20),
+    ("stream_levels_20x37x7", lambda: synth.random_levels((7, 37, 20), levels=(-1, -.5, 0, .5, 1), seed=17), 20),
+    ("stream_noisy_128x33x12", lambda: synth.spiral_woven(128, 12, sigma=0.05, seed=6, ny=33), 20),
 ]
 
 
@@ -68,6 +79,13 @@ def test_host_pointer_and_capacity_growth(F):
     compare_full(_gpu(F, f, max_punctures=16), ref)
     f3 = synth.random_levels((4, 7, 9, 11), seed=4)
     compare_full(_gpu(F, f3, host=True, max_punctures=8), cp.track(f3))
+    # a device pointer that is not 16-byte aligned (rows are copied by TMA)
+    f2 = synth.random_levels((5, 23, 36), seed=13)
+    buf = torch.empty(f2.size + 1, dtype=torch.float32, device="cuda")
+    x = buf[1:].view(f2.shape)
+    x.copy_(torch.from_numpy(f2))
+    assert x.data_ptr() % 16 != 0
+    compare_full(F.ftk_track_cp2d(x, F.make_params()), cp.track(f2))
 
 
 def test_plan_reuse_and_device_view(F):
