@@ -60,7 +60,8 @@ typedef enum {
     FTK_ERR_STATE = 8       /* call not valid in the object's current state */
 } ftk_status;
 
-#define FTK_FLAG_STAGE_TIMES 1u
+#define FTK_FLAG_STAGE_TIMES 1u   /* record per-stage device times (plans) */
+#define FTK_FLAG_AUTOTUNE 2u      /* choose each shape's time chunking by measurement */
 
 /* Tracking parameters.  ftk_params_default() fills the defaults. */
 typedef struct {
@@ -68,8 +69,7 @@ typedef struct {
     double   spacing[3];     /* physical grid spacing (x, y, z) */
     double   t0, dt;         /* physical time of slice 0 and slice spacing */
     int32_t  quant_shift;    /* fixed-point scale 2^quant_shift; default 20 */
-    uint32_t flags;          /* bit 0 (FTK_FLAG_STAGE_TIMES): record per-stage device
-                                times; other bits reserved, must be 0 */
+    uint32_t flags;          /* FTK_FLAG_* bits; other bits reserved, must be 0 */
     int64_t  max_punctures;  /* initial device capacity; 0 = automatic (grows on demand) */
 } ftk_params;
 
@@ -99,6 +99,8 @@ typedef struct {
 typedef struct ftk_result ftk_result;
 typedef struct ftk_plan ftk_plan;
 typedef struct ftk_stream ftk_stream;
+typedef struct ftk_batch ftk_batch;
+typedef struct ftk_server ftk_server;
 
 void        ftk_params_default(ftk_params *p);
 const char *ftk_status_string(ftk_status s);
@@ -142,6 +144,54 @@ ftk_status ftk_plan_device_view(ftk_plan *plan, ftk_device_view *view);
  * detect, scan, finalize, link, label; n = number of entries written. */
 ftk_status ftk_plan_stage_times(ftk_plan *plan, float *ms, int cap, int *n);
 ftk_status ftk_plan_destroy(ftk_plan *plan);
+
+/* ---------------------------------------------------------------------
+ * Batches: many independent 2D fields of uneven size and length (the paper's
+ * method applied field by field; the batching itself has no counterpart in
+ * the paper).  dims[i] = {nx, ny, nt} of field i.  ftk_batch_execute takes
+ * device pointers; the first execute runs uncaptured and synchronously
+ * (capacities settle, and with FTK_FLAG_AUTOTUNE every shape's time
+ * chunking is chosen by measurement and cached per shape); later executes
+ * replay one CUDA graph holding every field's pipeline, spread over a pool of
+ * streams, and return without synchronising.  ftk_batch_counts /
+ * ftk_batch_download synchronise, check all fields with one counter copy and
+ * re-run any field whose punctures outgrew its capacity.
+ * ------------------------------------------------------------------- */
+ftk_status ftk_batch_create(int nfields, const int64_t (*dims)[3], const ftk_params *p, ftk_batch **batch);
+ftk_status ftk_batch_execute(ftk_batch *batch, const float *const *f_dev, void *cuda_stream);
+ftk_status ftk_batch_counts(ftk_batch *batch, int64_t *counts /* [nfields] */);
+ftk_status ftk_batch_download(ftk_batch *batch, ftk_result **outs /* [nfields] */);
+ftk_status ftk_batch_destroy(ftk_batch *batch);
+/* One-shot batch: outs[i] receives field i's punctured faces, sorted by face_id. */
+ftk_status ftk_track_cp2d_batch(int nfields, const float *const *f_dev, const int64_t (*dims)[3],
+                                const ftk_params *p, ftk_result **outs, void *cuda_stream);
+
+/* ---------------------------------------------------------------------
+ * In-situ streams (paper Sec. 8, push_field_data(); Sec. 3.2, traversal
+ * of ordinal then interval elements with a sliding window of two slices).
+ * A stream keeps the previous slice and a union-find over every puncture so
+ * far resident on the device.  Push k (slice k, host or device pointer of
+ * nz*ny*nx floats) returns the delta: the punctured ordinal faces of slice k
+ * and interval faces of slab [k-1, k], face ids and base t global to the
+ * stream, labels provisional (smallest face id connected so far).  Close
+ * returns every puncture with its final label (the whole-field result,
+ * sorted by face_id) and releases the stream; final may be NULL.  A stream
+ * owns its CUDA stream; one handle must not be used by two threads at once,
+ * but different streams may push concurrently from different threads and
+ * their work overlaps on the device.
+ * ------------------------------------------------------------------- */
+ftk_status ftk_stream_open(int ndim, int64_t nx, int64_t ny, int64_t nz, const ftk_params *p, ftk_stream **s);
+ftk_status ftk_stream_push(ftk_stream *s, const float *slice, ftk_result **delta);
+ftk_status ftk_stream_close(ftk_stream *s, ftk_result **final);
+
+/* Serving: streams opened in a server are admitted only while the sum of
+ * their device-memory footprints stays within budget_bytes; otherwise
+ * ftk_stream_open_in returns FTK_ERR_BUSY (retry after a stream closes). */
+ftk_status ftk_server_create(uint64_t budget_bytes, ftk_server **server);
+ftk_status ftk_server_used(ftk_server *server, uint64_t *used_bytes);
+ftk_status ftk_server_destroy(ftk_server *server);   /* FTK_ERR_STATE while streams are open */
+ftk_status ftk_stream_open_in(ftk_server *server, int ndim, int64_t nx, int64_t ny, int64_t nz,
+                              const ftk_params *p, ftk_stream **s);
 
 /* ---------------------------------------------------------------------
  * Tracking without device allocation.  The paper has no counterpart: this

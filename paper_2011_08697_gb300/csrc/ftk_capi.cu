@@ -9,26 +9,33 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
+#include <vector>
 
 #include "../../include/ftk.h"
 #include "ftk_kernels.cuh"
+#include "ftk_internal.h"
 
 using namespace ftk;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
 
-ftk_status fail(ftk_status s, const std::string &msg) {
+ftk_status ftk::fail(ftk_status s, const std::string &msg) {
     g_err = msg;
     return s;
 }
 
-ftk_status cuda_fail(cudaError_t e, const char *what) {
+ftk_status ftk::cuda_fail(cudaError_t e, const char *what) {
     g_err = std::string(what) + ": " + cudaGetErrorString(e);
     return FTK_ERR_CUDA;
 }
+
+namespace {
 
 #define FTK_CUDA(call)                                   \
     do {                                                 \
@@ -38,7 +45,9 @@ ftk_status cuda_fail(cudaError_t e, const char *what) {
 
 constexpr size_t kSmemBudget = 110 * 1024;   // two detect CTAs per SM
 
-bool is_device_pointer(const void *p) {
+}  // namespace
+
+bool ftk::is_device_pointer(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
@@ -47,36 +56,7 @@ bool is_device_pointer(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-}  // namespace
-
 void ftk::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
-
-struct ftk_result {
-    ftk_cp *data;
-    size_t count;
-};
-
-struct ftk_plan {
-    int ndim;
-    int variant;               // detect kernel (VAR_*)
-    int device;
-    Field F;
-    Blocking B;
-    ftk_params p;
-    long long nverts;
-    Workspace W;
-    float *d_input;
-    RunCounters *h_ctr;        // pinned mirror of the device counters
-    cudaStream_t stream;
-    const float *last_f;
-    const float *last_dev;     // device copy the last run read
-    bool last_host;
-    bool executed;
-    bool timing;
-    cudaEvent_t ev[6];
-    float stage_ms[5];
-    int nstage;
-};
 
 namespace {
 
@@ -208,7 +188,7 @@ ftk_status choose_blocking(int ndim, const Field &F, Blocking &B, int &variant) 
 ftk_status check_params(const ftk_params *p) {
     if (p && (p->quant_shift < 0 || p->quant_shift > 40))
         return fail(FTK_ERR_ARG, "quant_shift must lie in [0, 40]");
-    if (p && p->flags & ~1u) return fail(FTK_ERR_ARG, "unknown flag bits");
+    if (p && p->flags & ~(FTK_FLAG_STAGE_TIMES | FTK_FLAG_AUTOTUNE)) return fail(FTK_ERR_ARG, "unknown flag bits");
     if (p && p->max_punctures < 0) return fail(FTK_ERR_ARG, "max_punctures must be >= 0");
     return FTK_OK;
 }
@@ -229,19 +209,23 @@ ftk_status status_of(unsigned st) {
 ftk_status launch(ftk_plan *pl, const float *dev_f, cudaStream_t s, int variant) {
     pl->F.f = dev_f;
     cudaError_t e = launch_pipeline(pl->ndim, variant, pl->F, pl->B, pl->W, s, pl->timing ? pl->ev : nullptr);
-    if (e != cudaSuccess) return cuda_fail(e, "pipeline launch");
+    if (e != cudaSuccess) return cuda_fail(e, (std::string("pipeline launch (") + last_launch_stage() + ")").c_str());
     pl->stream = s;
     pl->executed = true;
     return FTK_OK;
 }
 
-// synchronise, grow and re-run on overflow, check device status
-ftk_status settle(ftk_plan *pl) {
+// grow and re-run on overflow (synchronously), check device status; the
+// counters of the last run are in pl->h_ctr when have_counters is set
+ftk_status settle_from(ftk_plan *pl, bool have_counters) {
     if (!pl->executed) return fail(FTK_ERR_STATE, "plan has not been executed");
     int variant = pl->variant;
     for (int attempt = 0; attempt < 6; ++attempt) {
-        ftk_status s = read_counters(pl);
-        if (s != FTK_OK) return s;
+        ftk_status s = FTK_OK;
+        if (!have_counters || attempt > 0) {
+            s = read_counters(pl);
+            if (s != FTK_OK) return s;
+        }
         const unsigned st = pl->h_ctr->status;
         if (st & ST_RANGE) return status_of(st);
         if (st & ST_WIDE) {
@@ -273,6 +257,8 @@ ftk_status settle(ftk_plan *pl) {
     return fail(FTK_ERR_NOMEM, "puncture capacity did not converge");
 }
 
+ftk_status settle(ftk_plan *pl) { return settle_from(pl, false); }
+
 ftk_status make_result(ftk_plan *pl, ftk_result **out) {
     const long long P = pl->h_ctr->punctures;
     ftk_result *r = new (std::nothrow) ftk_result;
@@ -295,7 +281,90 @@ ftk_status make_result(ftk_plan *pl, ftk_result **out) {
     return FTK_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: measured time chunking per (shape, variant, SM count)
+// ---------------------------------------------------------------------------
+struct TuneKey {
+    int ndim, nx, ny, nz, nt, variant, sms;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(ndim, nx, ny, nz, nt, variant, sms) < std::tie(o.ndim, o.nx, o.ny, o.nz, o.nt, o.variant, o.sms);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned_ntc;
+
+TuneKey tune_key(const ftk_plan *pl) {
+    return TuneKey{pl->ndim, pl->F.nx, pl->F.ny, pl->F.nz, pl->F.nt, pl->variant, sm_count()};
+}
+
+void set_chunks(ftk_plan *pl, int ntc) {
+    pl->B.tc = (pl->F.nt + ntc - 1) / ntc;
+    pl->B.ntc = (pl->F.nt + pl->B.tc - 1) / pl->B.tc;
+}
+
+void apply_tuned(ftk_plan *pl) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned_ntc.find(tune_key(pl));
+    if (it != g_tuned_ntc.end()) set_chunks(pl, it->second);
+}
+
 }  // namespace
+
+ftk_status ftk::plan_launch(ftk_plan *pl, const float *f, cudaStream_t s) {
+    pl->last_f = f;
+    pl->last_dev = f;
+    pl->last_host = false;
+    return launch(pl, f, s, pl->variant);
+}
+
+ftk_status ftk::plan_check(ftk_plan *pl) { return settle_from(pl, true); }
+
+ftk_status ftk::plan_result(ftk_plan *pl, ftk_result **out) { return make_result(pl, out); }
+
+ftk_status ftk::plan_autotune(ftk_plan *pl, const float *f, cudaStream_t s) {
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned_ntc.find(tune_key(pl));
+        if (it != g_tuned_ntc.end()) {
+            set_chunks(pl, it->second);
+            return FTK_OK;
+        }
+    }
+    // candidates: the heuristic choice and powers of two around it
+    const int heur = pl->B.ntc;
+    std::vector<int> cand = {heur};
+    for (int c = 1; c <= pl->F.nt; c *= 2)
+        if (c != heur && c <= 4 * heur + 4 && 4 * c + 4 >= heur) cand.push_back(c);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_ntc = heur;
+    for (int c : cand) {
+        set_chunks(pl, c);
+        float tot = 0.0f;
+        for (int rep = 0; rep < 3; ++rep) {
+            ftk_status st = launch(pl, f, s, pl->variant);      // first run warms up
+            if (st != FTK_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+            if (rep == 0) continue;
+            cudaEventRecord(e0, s);
+            st = launch(pl, f, s, pl->variant);
+            cudaEventRecord(e1, s);
+            if (st != FTK_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tot += ms;
+        }
+        if (tot < best) { best = tot; best_ntc = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_chunks(pl, best_ntc);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned_ntc[tune_key(pl)] = best_ntc;
+    return FTK_OK;
+}
 
 extern "C" {
 
@@ -326,8 +395,10 @@ const char *ftk_last_error(void) { return g_err.c_str(); }
 
 const char *ftk_version(void) { return "ftk-gb300 0.1 sm_103a"; }
 
-ftk_status ftk_plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt,
-                           const ftk_params *p, ftk_plan **plan) {
+}  // extern "C"
+
+ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, const ftk_params *p,
+                            RunCounters *ctr, ftk_plan **plan) {
     if (plan) *plan = nullptr;
     if (!plan) return fail(FTK_ERR_ARG, "plan is NULL");
     if (ndim != 2 && ndim != 3) return fail(FTK_ERR_ARG, "ndim must be 2 or 3");
@@ -359,12 +430,15 @@ ftk_status ftk_plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t
     pl->timing = (pl->p.flags & 1u) != 0;
 
     Workspace &W = pl->W;
-    if (cudaMalloc(&W.ctr, sizeof(RunCounters)) != cudaSuccess ||
+    pl->external_ctr = ctr != nullptr;
+    if (ctr) W.ctr = ctr;
+    if ((!ctr && cudaMalloc(&W.ctr, sizeof(RunCounters)) != cudaSuccess) ||
         cudaMalloc(&W.seg_cnt, W.nseg * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&W.seg_stage, W.nseg * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&W.seg_off, W.nseg * sizeof(long long)) != cudaSuccess ||
         cudaMallocHost(&pl->h_ctr, sizeof(RunCounters)) != cudaSuccess) {
         cudaGetLastError();
+        if (pl->external_ctr) W.ctr = nullptr;
         free_workspace(W);
         if (pl->h_ctr) cudaFreeHost(pl->h_ctr);
         delete pl;
@@ -384,15 +458,24 @@ ftk_status ftk_plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t
         }
     }
     if (s != FTK_OK) {
+        if (pl->external_ctr) W.ctr = nullptr;
         free_workspace(W);
         cudaFreeHost(pl->h_ctr);
         delete pl;
         return s;
     }
+    apply_tuned(pl);
     if (pl->timing)
         for (int i = 0; i < 6; ++i) cudaEventCreate(&pl->ev[i]);
     *plan = pl;
     return FTK_OK;
+}
+
+extern "C" {
+
+ftk_status ftk_plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt,
+                           const ftk_params *p, ftk_plan **plan) {
+    return plan_create(ndim, nx, ny, nz, nt, p, nullptr, plan);
 }
 
 ftk_status ftk_plan_execute(ftk_plan *pl, const float *f, void *cuda_stream) {
@@ -458,6 +541,7 @@ ftk_status ftk_plan_stage_times(ftk_plan *pl, float *ms, int cap, int *n) {
 ftk_status ftk_plan_destroy(ftk_plan *pl) {
     if (!pl) return FTK_OK;
     if (pl->executed) cudaStreamSynchronize(pl->stream);
+    if (pl->external_ctr) pl->W.ctr = nullptr;
     free_workspace(pl->W);
     cudaFree(pl->d_input);
     if (pl->h_ctr) cudaFreeHost(pl->h_ctr);

@@ -22,6 +22,8 @@
 //   k_label    label = smallest face id of the component; pack records.
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include "ftk_device.cuh"
 #include "ftk_kernels.cuh"
 
@@ -1394,21 +1396,194 @@ int stream2_ctas_per_sm(int nx) {
     int n = 0;
     const size_t smem = stream2_smem_bytes(nx);
     const void *k = stream2_kernel<false>(nx);
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < smem)
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, stream2_threads(nx), smem);
     return n > 0 ? n : 1;
 }
+
+// ----------------------------------------------------------------------------
+// In-situ streaming: merging one push (a 2-slice or 1-slice run) into the
+// stream's global union-find over every puncture seen so far.
+//
+// The run's punctures get global slots gi = n_base + i.  Ordinal faces of the
+// run's first slice were already reported by the previous push: they are
+// "shadows", linked to their earlier slot through the previous push's sorted
+// list of last-slice ordinal faces.  Component minima (face ids) are kept at
+// union-find roots; a delta label is the minimum over every face known so far
+// that is connected to the face.
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ bool run_is_shadow(const StreamMerge &M, long long fid_local) {
+    if (M.first) return false;
+    const long long g = fid_local / M.T;
+    const int tt = (int)(fid_local - g * M.T);
+    return g < M.slice_verts && !(M.tbit & (M.T == 12 ? mesh<2>().face[tt][1] : mesh<3>().face[tt][2]));
+}
+
+// slot of a face in a sorted array (or -1)
+__device__ __forceinline__ long long bsearch_ll(const long long *a, long long n, long long key) {
+    long long lo = 0, hi = n;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < n && a[lo] == key) ? lo : -1;
+}
+
+__global__ void __launch_bounds__(NT) k_stream_place(StreamMerge M) {
+    const long long P = M.ctr->punctures;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        const long long gi = M.n_base + i;
+        const long long fl = M.face[i];
+        const long long fg = fl + M.shift_g * M.T;
+        const bool sh = run_is_shadow(M, fl);
+        M.gfid[gi] = fg;
+        M.gparent[gi] = (int)gi;
+        M.gmin[gi] = sh ? LLONG_MAX : fg;
+        M.gshadow[gi] = sh ? 1 : 0;
+        ftk_cp r = M.packed[i];
+        r.face_id = fg;
+        r.base[3] += M.shift_t;
+        M.grec[gi] = r;
+        int lp = -1, orr = -1;
+        if (sh) {
+            const long long j = bsearch_ll(M.ord_fid, M.n_ord, fg);
+            if (j < 0) atomicOr(M.status, ST_PAIRING);   // must have been reported before
+            else {
+                lp = M.ord_gi[j];
+                orr = uf_find(M.gparent, lp, M.status);
+            }
+        }
+        M.link_prev[i] = lp;
+        M.old_root[i] = orr;
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_stream_unite(StreamMerge M) {
+    const long long P = M.ctr->punctures;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        const long long gi = M.n_base + i;
+        // the run's component: its root is the slot of the run label
+        const long long r = bsearch_ll(M.face, P, M.label[i]);
+        if (r < 0) { atomicOr(M.status, ST_PAIRING); continue; }
+        if (r != i) uf_unite(M.gparent, (int)gi, (int)(M.n_base + r), M.status);
+        if (M.link_prev[i] >= 0) uf_unite(M.gparent, (int)gi, M.link_prev[i], M.status);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_stream_minima(StreamMerge M) {
+    const long long P = M.ctr->punctures;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        const long long gi = M.n_base + i;
+        const int root = uf_find(M.gparent, (int)gi, M.status);
+        if (M.link_prev[i] >= 0) atomicMin(&M.gmin[root], M.gmin[M.old_root[i]]);
+        else atomicMin(&M.gmin[root], M.gfid[gi]);
+    }
+}
+
+// ordered compaction of the delta (non-shadow) records with their
+// provisional labels, and of the last-slice ordinal faces (one CTA)
+__global__ void __launch_bounds__(NT) k_stream_delta(StreamMerge M) {
+    __shared__ long long red[NT / 32 + 1];
+    const long long P = M.ctr->punctures;
+    long long run_d = 0, run_o = 0;
+    for (long long b0 = 0; b0 < P; b0 += NT) {
+        const long long i = b0 + threadIdx.x;
+        int keep = 0, last = 0;
+        long long gi = 0;
+        if (i < P) {
+            gi = M.n_base + i;
+            keep = M.gshadow[gi] ? 0 : 1;
+            last = M.first ? 1 : (M.face[i] / M.T >= M.slice_verts ? 1 : 0);
+        }
+        long long td, to;
+        const long long pd = run_d + block_excl_scan<long long>(keep, red, td);
+        const long long po = run_o + block_excl_scan<long long>(last, red, to);
+        if (keep) {
+            ftk_cp r = M.grec[gi];
+            r.label = M.gmin[uf_find(M.gparent, (int)gi, M.status)];
+            M.delta[pd] = r;
+        }
+        if (last) {
+            M.ord_fid_next[po] = M.gfid[gi];
+            M.ord_gi_next[po] = (int)gi;
+        }
+        run_d += td;
+        run_o += to;
+    }
+    if (threadIdx.x == 0) {
+        *M.delta_count = run_d;
+        *M.ord_count_next = run_o;
+    }
+}
+
+// final labels of every non-shadow slot, compacted in slot order (one CTA)
+__global__ void __launch_bounds__(NT) k_stream_final(long long n, const int *gshadow, int *gparent, const long long *gmin,
+                                                     const ftk_cp *grec, ftk_cp *out, long long *count,
+                                                     unsigned *status) {
+    __shared__ long long red[NT / 32 + 1];
+    long long run = 0;
+    for (long long b0 = 0; b0 < n; b0 += NT) {
+        const long long i = b0 + threadIdx.x;
+        const int keep = i < n && !gshadow[i];
+        long long t;
+        const long long p = run + block_excl_scan<long long>(keep, red, t);
+        if (keep) {
+            ftk_cp r = grec[i];
+            r.label = gmin[uf_find(gparent, (int)i, status)];
+            out[p] = r;
+        }
+        run += t;
+    }
+    if (threadIdx.x == 0) *count = run;
+}
+
+cudaError_t launch_stream_merge(const StreamMerge &M, cudaStream_t s) {
+    const int sg = sparse_grid();
+    k_stream_place<<<sg, NT, 0, s>>>(M);
+    k_stream_unite<<<sg, NT, 0, s>>>(M);
+    k_stream_minima<<<sg, NT, 0, s>>>(M);
+    k_stream_delta<<<1, NT, 0, s>>>(M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_final(long long n, const int *gshadow, int *gparent, const long long *gmin,
+                                const ftk_cp *grec, ftk_cp *out, long long *count, unsigned *status,
+                                cudaStream_t s) {
+    k_stream_final<<<1, NT, 0, s>>>(n, gshadow, gparent, gmin, grec, out, count, status);
+    return cudaGetLastError();
+}
+
+thread_local const char *g_launch_stage = "";
+const char *last_launch_stage() { return g_launch_stage; }
 
 template <int N>
 static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, const Workspace &W, cudaStream_t s,
                               cudaEvent_t *ev) {
     const int sg = sparse_grid();
     if (ev) cudaEventRecord(ev[0], s);
+    // kernel attributes are set outside stream capture (a first, uncaptured
+    // launch of the same shape always precedes a captured one)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
     if (N == 2 && variant != VAR_TILE) {
         const size_t smem = stream2_smem_bytes(F.nx);
         const void *k = variant == VAR_STREAM2_EXACT ? stream2_kernel<true>(F.nx) : stream2_kernel<false>(F.nx);
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        // the attribute only ever grows: a graph may replay a wider field's
+        // launch after a narrower one was configured
+        static size_t configured[4] = {0, 0, 0, 0};
+        const int slot = (variant == VAR_STREAM2_EXACT ? 2 : 0) + (F.nx <= 1024 ? 0 : 1);
+        cudaError_t e = cudaSuccess;
+        if (smem > configured[slot]) {
+            if (capturing) return cudaErrorInvalidValue;   // configured by the first, uncaptured launch
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            configured[slot] = smem;
+        }
         const unsigned units = (unsigned)((long long)B.ntc * B.nyb);
         Field Fa = F;
         Blocking Ba = B;
@@ -1419,7 +1594,7 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
     } else {
         const size_t smem = detect_smem_bytes(N, F, B);
         static size_t configured = 0;
-        if (smem > configured) {
+        if (smem > configured && !capturing) {
             cudaError_t e = cudaFuncSetAttribute(k_detect<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             configured = smem;
@@ -1432,6 +1607,10 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
     if (stream) {
         const long long ng = W.nseg < 65535LL * 8 ? W.nseg : 65535LL * 8;
         k_survive<N><<<(unsigned)(ng > 0 ? ng : 1), NT, 0, s>>>(F, W);
+    }
+    {
+        cudaError_t e2 = cudaGetLastError();
+        if (e2 != cudaSuccess) { g_launch_stage = "detect/survive"; return e2; }
     }
     k_scan<<<1, NT, 0, s>>>(W, stream ? 1 : 0);
     if (ev) cudaEventRecord(ev[2], s);
@@ -1446,13 +1625,17 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
     if (ev) cudaEventRecord(ev[4], s);
     k_label<N><<<sg, NT, 0, s>>>(F, W);
     if (ev) cudaEventRecord(ev[5], s);
-    return cudaGetLastError();
+    cudaError_t e3 = cudaGetLastError();
+    if (e3 != cudaSuccess) g_launch_stage = "scan..label";
+    return e3;
 }
 
 cudaError_t launch_pipeline(int ndim, int variant, const Field &F, const Blocking &B, const Workspace &W,
                             cudaStream_t s, cudaEvent_t *ev) {
+    g_launch_stage = "memset";
     cudaError_t e = cudaMemsetAsync(W.ctr, 0, sizeof(RunCounters), s);
     if (e != cudaSuccess) return e;
+    g_launch_stage = "launch";
     return ndim == 2 ? launch_all<2>(variant, F, B, W, s, ev) : launch_all<3>(variant, F, B, W, s, ev);
 }
 

@@ -125,6 +125,46 @@ int stream2_ctas_per_sm(int nx);
 cudaError_t launch_pipeline(int ndim, int variant, const Field &F, const Blocking &B, const Workspace &W,
                             cudaStream_t s, cudaEvent_t *ev /* 6 events or null */);
 
+struct StreamMerge {
+    // run (plan workspace, sorted by local face id)
+    const long long *face;      // [P] local face ids
+    const long long *label;     // [P] local labels (smallest local face id of the run's component)
+    const ftk_cp *packed;       // [P] records of the run
+    const RunCounters *ctr;     // run counters (P)
+    long long shift_g;          // global vertex id of the run's first vertex
+    int shift_t;                // global slice index of the run's first slice
+    int first;                  // 1 for the stream's first push (no shadows)
+    long long slice_verts;      // vertices per slice
+    int T;                      // face types
+    int tbit;                   // time bit of a chain
+    // stream state
+    long long n_base;           // global slots in use before this push
+    long long *gfid;            // [acap] global face id per slot
+    int *gparent;               // [acap]
+    long long *gmin;            // [acap] component minimum (valid at roots)
+    int *gshadow;               // [acap] 1 if the slot repeats an earlier slot
+    ftk_cp *grec;               // [acap] global records
+    const long long *ord_fid;   // [n_ord] previous push's last-slice ordinal faces (global ids, sorted)
+    const int *ord_gi;          // [n_ord] their slots
+    int n_ord;
+    int *link_prev;             // [P] earlier slot of a shadow, -1 otherwise
+    int *old_root;              // [P] root of that earlier slot before this push's unions
+    ftk_cp *delta;              // [P] compacted delta records (out)
+    long long *delta_count;     // (out)
+    long long *ord_fid_next;    // [P] this push's last-slice ordinal faces (out)
+    int *ord_gi_next;           // [P]
+    long long *ord_count_next;  // (out)
+    unsigned *status;
+};
+
+cudaError_t launch_stream_merge(const StreamMerge &M, cudaStream_t s);
+cudaError_t launch_stream_final(long long n, const int *gshadow, int *gparent, const long long *gmin,
+                                const ftk_cp *grec, ftk_cp *out, long long *count, unsigned *status,
+                                cudaStream_t s);
+
+// name of the step whose CUDA call failed in the last launch_pipeline
+const char *last_launch_stage();
+
 // sets the thread-local message returned by ftk_last_error()
 void set_last_error(const char *msg);
 

@@ -24,6 +24,7 @@ assert CP_DTYPE.itemsize == 56
 
 FTK_OK = 0
 FTK_FLAG_STAGE_TIMES = 1
+FTK_FLAG_AUTOTUNE = 2
 STATUS_NAMES = {0: "FTK_OK", 1: "FTK_ERR_ARG", 2: "FTK_ERR_RANGE", 3: "FTK_ERR_NOMEM",
                 4: "FTK_ERR_CUDA", 5: "FTK_ERR_TIMEOUT", 6: "FTK_ERR_BUSY",
                 7: "FTK_ERR_INVARIANT", 8: "FTK_ERR_STATE"}
@@ -56,6 +57,10 @@ EXPORTS = [
     "ftk_result_free", "ftk_plan_create", "ftk_plan_execute", "ftk_plan_count",
     "ftk_plan_download", "ftk_plan_device_view", "ftk_plan_stage_times", "ftk_plan_destroy",
     "ftk_track_cp2d_noalloc",
+    "ftk_batch_create", "ftk_batch_execute", "ftk_batch_counts", "ftk_batch_download",
+    "ftk_batch_destroy", "ftk_track_cp2d_batch",
+    "ftk_stream_open", "ftk_stream_push", "ftk_stream_close", "ftk_server_create",
+    "ftk_server_used", "ftk_server_destroy", "ftk_stream_open_in",
 ]
 
 
@@ -89,6 +94,19 @@ def lib():
         "ftk_plan_destroy": (i32, [vp]),
         "ftk_track_cp2d_noalloc": (i32, [vp, i64, i64, i64, ctypes.POINTER(ftk_params), vp, i64,
                                          ctypes.POINTER(ctypes.c_int64), vp]),
+        "ftk_batch_create": (i32, [i32, vp, ctypes.POINTER(ftk_params), pp]),
+        "ftk_batch_execute": (i32, [vp, vp, vp]),
+        "ftk_batch_counts": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "ftk_batch_download": (i32, [vp, vp]),
+        "ftk_batch_destroy": (i32, [vp]),
+        "ftk_track_cp2d_batch": (i32, [i32, vp, vp, ctypes.POINTER(ftk_params), vp, vp]),
+        "ftk_stream_open": (i32, [i32, i64, i64, i64, ctypes.POINTER(ftk_params), pp]),
+        "ftk_stream_push": (i32, [vp, vp, pp]),
+        "ftk_stream_close": (i32, [vp, pp]),
+        "ftk_server_create": (i32, [ctypes.c_uint64, pp]),
+        "ftk_server_used": (i32, [vp, ctypes.POINTER(ctypes.c_uint64)]),
+        "ftk_server_destroy": (i32, [vp]),
+        "ftk_stream_open_in": (i32, [vp, i32, i64, i64, i64, ctypes.POINTER(ftk_params), pp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -264,3 +282,151 @@ def ftk_plan_destroy(plan: Plan):
 
 def ftk_version() -> str:
     return lib().ftk_version().decode()
+
+
+def _dims_array(shapes):
+    """int64 [n][3] = (nx, ny, nt) from (nt, ny, nx) shapes."""
+    return np.ascontiguousarray([[s[2], s[1], s[0]] for s in shapes], dtype=np.int64)
+
+
+class Batch:
+    """Many independent 2D fields tracked together (``ftk_batch_*``): one
+    CUDA graph launch per execute after the first."""
+
+    def __init__(self, shapes, params: ftk_params | None = None):
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        for s in self.shapes:
+            if len(s) != 3:
+                raise ValueError("batched fields are 2D: (nt, ny, nx)")
+        self.n = len(self.shapes)
+        self._dims = _dims_array(self.shapes)
+        self._p = params if params is not None else make_params()
+        h = ctypes.c_void_p()
+        _check(lib().ftk_batch_create(self.n, self._dims.ctypes.data, ctypes.byref(self._p), ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+
+    def execute(self, fields, stream=None):
+        if len(fields) != self.n:
+            raise ValueError("one field per batch entry")
+        ptrs = (ctypes.c_void_p * self.n)()
+        keep = []
+        for i, f in enumerate(fields):
+            p, k, shape = _field_ptr(f)
+            if tuple(shape) != self.shapes[i]:
+                raise ValueError(f"field {i}: shape {shape} != {self.shapes[i]}")
+            ptrs[i] = p.value
+            keep.append(k)
+        self._keep = (keep, ptrs)
+        _check(lib().ftk_batch_execute(self._h, ptrs, _stream_ptr(stream)))
+
+    def counts(self):
+        out = np.zeros(self.n, dtype=np.int64)
+        _check(lib().ftk_batch_counts(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return out
+
+    def download(self):
+        outs = (ctypes.c_void_p * self.n)()
+        _check(lib().ftk_batch_download(self._h, outs))
+        return [_take_result(ctypes.c_void_p(outs[i])) for i in range(self.n)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ftk_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def ftk_track_cp2d_batch(fields, params: ftk_params | None = None, stream=None):
+    """One-shot batch of 2D device fields; returns one result array per field."""
+    n = len(fields)
+    ptrs = (ctypes.c_void_p * n)()
+    keep = []
+    shapes = []
+    for i, f in enumerate(fields):
+        p, k, shape = _field_ptr(f)
+        ptrs[i] = p.value
+        keep.append(k)
+        shapes.append(shape)
+    dims = _dims_array(shapes)
+    outs = (ctypes.c_void_p * n)()
+    prm = params if params is not None else make_params()
+    _check(lib().ftk_track_cp2d_batch(n, ptrs, dims.ctypes.data, ctypes.byref(prm), outs, _stream_ptr(stream)))
+    return [_take_result(ctypes.c_void_p(outs[i])) for i in range(n)]
+
+
+class Server:
+    """Admission of streams by device-memory footprint (``ftk_server_*``)."""
+
+    def __init__(self, budget_bytes: int):
+        h = ctypes.c_void_p()
+        _check(lib().ftk_server_create(int(budget_bytes), ctypes.byref(h)))
+        self._h = h
+
+    def used(self) -> int:
+        u = ctypes.c_uint64()
+        _check(lib().ftk_server_used(self._h, ctypes.byref(u)))
+        return u.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().ftk_server_destroy(self._h))
+            self._h = None
+
+
+class Stream:
+    """In-situ stream (``ftk_stream_*``): push one slice at a time."""
+
+    def __init__(self, spatial_shape, params: ftk_params | None = None, server: Server | None = None):
+        shp = tuple(int(v) for v in spatial_shape)
+        if len(shp) == 2:
+            ny, nx = shp
+            nz, ndim = 1, 2
+        elif len(shp) == 3:
+            nz, ny, nx = shp
+            ndim = 3
+        else:
+            raise ValueError("spatial shape must be (ny, nx) or (nz, ny, nx)")
+        self.shape = shp
+        self._p = params if params is not None else make_params()
+        h = ctypes.c_void_p()
+        if server is None:
+            _check(lib().ftk_stream_open(ndim, nx, ny, nz, ctypes.byref(self._p), ctypes.byref(h)))
+        else:
+            _check(lib().ftk_stream_open_in(server._h, ndim, nx, ny, nz, ctypes.byref(self._p), ctypes.byref(h)))
+        self._h = h
+
+    def push(self, slice_) -> np.ndarray:
+        ptr, keep, shape = _field_ptr(slice_)
+        if tuple(shape) != self.shape:
+            raise ValueError(f"slice shape {shape} != {self.shape}")
+        out = ctypes.c_void_p()
+        _check(lib().ftk_stream_push(self._h, ptr, ctypes.byref(out)))
+        del keep
+        return _take_result(out)
+
+    def close(self, want_final: bool = True):
+        if not getattr(self, "_h", None):
+            return None
+        out = ctypes.c_void_p()
+        st = lib().ftk_stream_close(self._h, ctypes.byref(out) if want_final else None)
+        self._h = None
+        _check(st)
+        return _take_result(out) if want_final else None
+
+    def __del__(self):
+        try:
+            self.close(False)
+        except Exception:
+            pass
