@@ -8,6 +8,13 @@ the paper's data):
   spiral2d (default): spiral woven, 1024 x 1024 grid over [-4,4]^2, 64 steps
                       in t in [0,1], + i.i.d. N(0, 1e-3^2), seed = rank
   blobs3d           : 128^3 grid x 16 steps, 32 moving Gaussian blobs
+  batch2d           : 256 independent 2D blob fields, N log-uniform 64..512,
+                      8..32 steps each; one graph-captured batch per step,
+                      against a loop of the plain per-field path
+  serve2d           : 32 in-situ streams (N log-uniform 256..2048) fed one
+                      slice at a time by Poisson arrivals (200 slices/s in
+                      total); per-slice latency, then saturated throughput
+                      against the plain path run slab by slab
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 a bounded sample of the same workload instead.
@@ -33,11 +40,15 @@ METRIC = "spacetime simplices tested/s"
 WORKLOADS = {
     "spiral2d": dict(name="spiral_woven_1024x1024x64_noise1e-3", ndim=2, dims=(1024, 1024), nt=64),
     "blobs3d": dict(name="gaussian_blobs_128x128x128x16_32blobs", ndim=3, dims=(128, 128, 128), nt=16),
+    "batch2d": dict(name="batch_256_blob_fields_N64-512_nt8-32", ndim=2, count=256),
+    "serve2d": dict(name="serve_32_streams_N256-2048_poisson200", ndim=2, count=32, rate=200.0),
 }
 # bounded CPU-oracle sample per workload: (spatial dims, slices)
 ORACLE_SAMPLE = {
     "spiral2d": ((1024, 1024), 2),
     "blobs3d": ((48, 48, 48), 2),
+    "batch2d": ((128, 128), 8),
+    "serve2d": ((512, 512), 2),
 }
 
 
@@ -83,6 +94,12 @@ def sample_field(wl: str, seed: int):
     if wl == "spiral2d":
         return synth.spiral_woven(dims[0], WORKLOADS[wl]["nt"], sigma=1e-3, seed=seed,
                                   ny=dims[1], k_stop=s)
+    if wl in ("batch2d", "serve2d"):
+        # one field of the batch / stream law at a bounded size
+        n = dims[0]
+        bs = synth.blob_set((n, n), 36, seed=70_000 + seed,
+                            sigma_range=(4.0 * n / 128.0, 12.0 * n / 128.0), vmax=1.0)
+        return np.stack([synth.blob_slice(bs, k) for k in range(s)])
     return make_field(wl, seed, dims=dims, nt=s)
 
 
@@ -193,18 +210,420 @@ def reference_arm(args):
         times.append(dt)
     tot = sum(times)
     value = faces * args.steps / tot
+    metric, unit = METRIC, "simplices/s"
+    if wl == "serve2d":
+        # one bounded sample = one two-slice slab = one pushed timestep
+        value, metric, unit = args.steps / tot, "timesteps/s", "timesteps/s"
     sample = f"{wl}: {'x'.join(map(str, dims))} grid x {s} slices ({faces} faces) per step"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "simplices/s",
+        "impl": "reference", "metric": metric, "value": value, "unit": unit,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i64", "data": "synthetic",
         "config": {"workload": WORKLOADS[wl]["name"], "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "simplices/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
                          "sample": sample},
-        "e2e": {"value": value, "unit": "simplices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def _dist_setup():
+    """(dist or None, rank, world, local rank); gloo carries only the
+    barrier and the max-over-ranks of the timings."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return dist, rank, world, local
+
+
+def _max_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
+
+
+def _same_result(a, b) -> bool:
+    if len(a) != len(b):
+        return False
+    if not len(a):
+        return True
+    return bool(np.array_equal(a["face_id"], b["face_id"]) and np.array_equal(a["label"], b["label"])
+                and np.array_equal(a["morse_index"], b["morse_index"])
+                and float(np.max(np.abs(a["off"] - b["off"]))) <= 1e-6)
+
+
+def _oracle_check(res, f) -> bool:
+    """Whole-field oracle comparison of one small field (bit-exact faces,
+    types and labels; offsets within 1e-5 of a cell)."""
+    from oracle import cp
+    ref = cp.track(f)
+    if not np.array_equal(res["face_id"], ref["face_id"]):
+        return False
+    return bool(np.array_equal(res["morse_index"], ref["morse"]) and np.array_equal(res["label"], ref["label"])
+                and (len(ref["face_id"]) == 0 or float(np.max(np.abs(res["off"] - ref["off"]))) <= 1e-5))
+
+
+def _cpu_baseline(wl):
+    fs, dt, _ = run_oracle_sample(wl, seed=0)
+    dims, sl = ORACLE_SAMPLE[wl]
+    return {"value": fs / dt, "unit": "simplices/s", "cores": 1, "kind": "oracle",
+            "sample": f"{'x'.join(map(str, dims))} grid x {sl} slices ({fs} faces), same generator law"}
+
+
+def batch_arm(args):
+    """256 independent fields per step: one graph replay of the batch vs a
+    loop of the plain per-field path (plan execute + count per field)."""
+    import torch
+    from paper_2011_08697_gb300 import build as _b, ftk, synth
+
+    dist, rank, world, local = _dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _b.build()
+    ftk.lib()
+    W = WORKLOADS["batch2d"]
+    specs = synth.batch_fields(W["count"], seed0=rank * W["count"], materialise=False)
+    xs = [synth.blob_slices_torch(bs, 0, nt, dev) for (n, _, nt, _, bs) in specs]
+    shapes = [tuple(x.shape) for x in xs]
+    faces = sum(face_count((n, n), nt) for (n, _, nt, _, _) in specs)
+    nverts = sum(x.numel() for x in xs)
+    steps_per_batch = sum(nt for (_, _, nt, _, _) in specs)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    batch = ftk.Batch(shapes, ftk.make_params(flags=ftk.FTK_FLAG_AUTOTUNE))
+    plans = [ftk.Plan(sh) for sh in shapes]
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        batch.execute(xs, stream)                 # uncaptured, autotuned
+        tune_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            batch.execute(xs, stream)
+            batch.counts()
+        for _ in range(max(1, args.warmup // 2)):
+            for p, x in zip(plans, xs):
+                p.execute(x, stream)
+                p.count()
+    # exactness: batched == plain on every field; the two smallest fields
+    # against the oracle
+    got_b = batch.download()
+    got_p = [p.download() for p in plans]
+    same = all(_same_result(a, b) for a, b in zip(got_b, got_p))
+    small = sorted(range(len(specs)), key=lambda i: xs[i].numel())[:2]
+    oracle_ok = all(_oracle_check(got_b[i], xs[i].cpu().numpy()) for i in small) if rank == 0 else None
+    P = int(sum(len(r) for r in got_b))
+
+    def timed(fn, k):
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        with torch.cuda.stream(stream):
+            for i in range(k):
+                flush.zero_()
+                st[i].record(stream)
+                fn()
+                en[i].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in zip(st, en)]
+
+    def run_batch():
+        batch.execute(xs, stream)
+        batch.counts()
+
+    def run_plain():
+        for p, x in zip(plans, xs):
+            p.execute(x, stream)
+            p.count()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        b_ms = timed(run_batch, args.steps)
+    barrier()
+    plain_steps = max(3, min(args.steps, 10))
+    p_ms = timed(run_plain, plain_steps)
+    tot_b = _max_over_ranks(dist, sum(b_ms))
+    tot_p = _max_over_ranks(dist, sum(p_ms))
+    value = faces * world * args.steps / (tot_b / 1e3)
+    plain_value = faces * world * plain_steps / (tot_p / 1e3)
+
+    # e2e: pinned host fields copied in, batch, results copied out
+    hosts = [x.cpu().pin_memory() for x in xs]
+    dbuf = [torch.empty_like(x) for x in xs]
+    with torch.cuda.stream(stream):
+        for h, d in zip(hosts, dbuf):
+            d.copy_(h, non_blocking=True)
+        batch.execute(dbuf, stream)
+        batch.download()
+        torch.cuda.synchronize()
+        e2e_steps = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for h, d in zip(hosts, dbuf):
+                d.copy_(h, non_blocking=True)
+            batch.execute(dbuf, stream)
+            outs = batch.download()
+        e2e_s = _max_over_ranks(dist, time.perf_counter() - t0)
+    e2e_val = faces * world * e2e_steps / e2e_s
+    kernels = batch.kernels()
+    peak, peak_kind = measured_peak_hbm()
+    graph_ms = statistics.mean(b_ms)
+    achieved = 4.0 * nverts / (graph_ms / 1e3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "simplices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_b / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": W["name"], "fields": len(specs), "faces_per_step": faces,
+                       "vertices_per_step": nverts, "timesteps_per_step": steps_per_batch,
+                       "l2": "256 MB buffer written between steps (L2 flushed); inputs 1.5 GB > L2",
+                       "step": "one CUDA-graph replay of all fields + one counter read-back and check",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "timesteps_per_s": steps_per_batch * world * args.steps / (tot_b / 1e3),
+            "p50_step_ms": statistics.median(b_ms), "p99_step_ms": _pct(b_ms, 0.99),
+            "plain_loop": {"value": plain_value, "unit": "simplices/s", "ms_per_step": tot_p / plain_steps,
+                           "steps": plain_steps,
+                           "form": "per field: plan execute + count (synchronising), one stream"},
+            "batched_over_plain": value / plain_value,
+            "autotune_s": tune_s, "punctures": P,
+            "bit_exact": {"batched_equals_plain": same, "oracle_two_smallest_fields": oracle_ok},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "whole batch graph",
+                         "peak_kind": peak_kind, "algorithmic_bytes_per_launch": 4.0 * nverts,
+                         "launch_ms": graph_ms},
+            "cpu_baseline": _cpu_baseline("batch2d"),
+            "e2e": {"value": e2e_val, "unit": "simplices/s", "h2d_bytes_per_step": int(4 * nverts),
+                    "d2h_bytes_per_step": int(P * 56)},
+            "gpu_launches": int(kernels * args.steps),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for p in plans:
+        p.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def serve_arm(args):
+    """In-situ serving: 32 streams, slices arriving as a Poisson process;
+    per-slice latency at that load, then saturated throughput against the
+    plain path run on the same slabs one at a time."""
+    import queue
+    import threading
+
+    import torch
+    from paper_2011_08697_gb300 import build as _b, ftk, synth
+
+    dist, rank, world, local = _dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _b.build()
+    ftk.lib()
+    W = WORKLOADS["serve2d"]
+    ns = W["count"]
+    specs = synth.stream_specs(ns, seed0=rank * ns)
+    events = synth.poisson_arrivals(ns, W["rate"], args.duration, seed=rank)
+    arrivals = [0] * ns
+    for _, s_ in events:
+        arrivals[s_] += 1
+    n_sat = args.sat_pushes
+    slices = [synth.blob_slices_torch(bs, 0, arrivals[i] + n_sat, dev) for i, (n, bs) in enumerate(specs)]
+    torch.cuda.synchronize()
+    new_faces = [face_count((n, n), 2) - face_count((n, n), 1) for n, _ in specs]
+
+    budget = int(args.serve_budget_gb * (1 << 30))
+    server = ftk.Server(budget)
+    streams = [ftk.Stream((n, n), server=server) for n, _ in specs]
+    footprint_open = server.used()
+    lat_poisson = [[] for _ in range(ns)]
+    lat_sat = [[] for _ in range(ns)]
+    done_sat = [0.0] * ns
+    qs = [queue.Queue() for _ in range(ns)]
+    start_sat = threading.Barrier(ns + 1)
+    errors = []
+
+    def worker(i):
+        try:
+            torch.cuda.set_device(local)
+            st = streams[i]
+            k = 0
+            while True:
+                item = qs[i].get()
+                if item is None:
+                    break
+                st.push(slices[i][k])
+                lat_poisson[i].append(time.perf_counter() - item)
+                k += 1
+            start_sat.wait()
+            for j in range(n_sat):
+                t0 = time.perf_counter()
+                st.push(slices[i][k])
+                lat_sat[i].append(time.perf_counter() - t0)
+                k += 1
+            done_sat[i] = time.perf_counter()
+        except Exception as e:      # reported after the join
+            errors.append(repr(e))
+            try:
+                start_sat.abort()
+            except Exception:
+                pass
+
+    threads = [threading.Thread(target=worker, args=(i,), daemon=True) for i in range(ns)]
+    for t in threads:
+        t.start()
+    if dist is not None:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for (ta, s_) in events:
+            target = t0 + ta
+            now = time.perf_counter()
+            if target > now:
+                time.sleep(target - now)
+            qs[s_].put(target)
+        for q in qs:
+            q.put(None)
+        poisson_wall = time.perf_counter() - t0
+        try:
+            start_sat.wait()
+        except threading.BrokenBarrierError:
+            pass
+        t_sat = time.perf_counter()
+        for t in threads:
+            t.join()
+        sat_wall = max(done_sat) - t_sat if not errors else float("nan")
+    if errors:
+        raise RuntimeError("stream worker failed: " + errors[0])
+    total_arrivals = len(events)
+    lp = [x * 1e3 for L in lat_poisson for x in L]
+    ls = [x * 1e3 for L in lat_sat for x in L]
+    sat_faces = sum(new_faces[i] * n_sat for i in range(ns))
+    sat_wall = _max_over_ranks(dist, sat_wall)
+    served_steps_s = ns * n_sat * world / sat_wall
+    served_faces_s = sat_faces * world / sat_wall
+
+    # plain path on the same slabs, one at a time, one host thread
+    plans = {}
+    for n, _ in specs:
+        if n not in plans:
+            plans[n] = ftk.Plan((2, n, n))
+    pstream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(pstream):
+        for i, (n, _) in enumerate(specs):       # warm-up: every shape once
+            plans[n].execute(slices[i][0:2], pstream)
+            plans[n].download()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in range(n_sat):
+            for i, (n, _) in enumerate(specs):
+                k = arrivals[i] + j
+                plans[n].execute(slices[i][k - 1:k + 1], pstream)
+                plans[n].download()
+        plain_wall = _max_over_ranks(dist, time.perf_counter() - t0)
+    plain_steps_s = ns * n_sat * world / plain_wall
+
+    # e2e: the same streams fed from pinned host slices (copies inside push)
+    n_e2e = min(4, n_sat)
+    hosts = [slices[i][arrivals[i]:arrivals[i] + n_e2e].cpu().pin_memory() for i in range(ns)]
+    e2e_streams = [ftk.Stream((n, n)) for n, _ in specs]
+    e2e_bar = threading.Barrier(ns + 1)
+    e2e_done = [0.0] * ns
+
+    def e2e_worker(i):
+        torch.cuda.set_device(local)
+        e2e_bar.wait()
+        for j in range(n_e2e):
+            e2e_streams[i].push(hosts[i][j])
+        e2e_done[i] = time.perf_counter()
+
+    th = [threading.Thread(target=e2e_worker, args=(i,), daemon=True) for i in range(ns)]
+    for t in th:
+        t.start()
+    e2e_bar.wait()
+    t0 = time.perf_counter()
+    for t in th:
+        t.join()
+    e2e_wall = _max_over_ranks(dist, max(e2e_done) - t0)
+    for s_ in e2e_streams:
+        s_.close(False)
+
+    # exactness: the four smallest streams' final results equal the plain
+    # path on the whole pushed field; one small stream slab vs the oracle
+    order = sorted(range(ns), key=lambda i: specs[i][0])
+    same = True
+    for i in order[:4]:
+        fin = streams[i].close()
+        whole = ftk.ftk_track_cp2d(slices[i][: arrivals[i] + n_sat].contiguous())
+        same = same and _same_result(fin, whole)
+    for i in order[4:]:
+        streams[i].close(False)
+    used_after = server.used()
+    server.close()
+    oracle_ok = None
+    if rank == 0:
+        i = order[0]
+        f3 = slices[i][:3].cpu().numpy()
+        st = ftk.Stream(f3.shape[1:])
+        for k in range(3):
+            st.push(f3[k])
+        oracle_ok = _oracle_check(st.close(), f3)
+    launches_per_push = 8 + 4      # the two-slice pipeline + the stream merge
+    if rank == 0:
+        line = {
+            "metric": "timesteps/s", "value": served_steps_s, "unit": "timesteps/s", "n_gpus": world,
+            "steps": ns * n_sat, "warmup": 0, "ms_per_step": 1e3 * sat_wall / (ns * n_sat),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": W["name"], "streams": ns, "grid_N": [n for n, _ in specs],
+                       "poisson_rate_steps_s": W["rate"], "poisson_duration_s": args.duration,
+                       "saturated_pushes_per_stream": n_sat,
+                       "timing": "host wall clock per push (arrival to delta on the host)",
+                       "l2": "slices of 32 streams (~130 MB per round) rotate through L2; no flush",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "poisson": {"arrivals": total_arrivals, "wall_s": poisson_wall,
+                        "throughput_steps_s": total_arrivals / poisson_wall,
+                        "p50_step_ms": _pct(lp, 0.5), "p99_step_ms": _pct(lp, 0.99),
+                        "max_step_ms": max(lp) if lp else None},
+            "saturated": {"steps_s": served_steps_s, "simplices_s": served_faces_s,
+                          "p50_step_ms": _pct(ls, 0.5), "p99_step_ms": _pct(ls, 0.99)},
+            "plain_loop": {"value": plain_steps_s, "unit": "timesteps/s",
+                           "form": "per slab: 2-slice plan execute + download, one host thread"},
+            "served_over_plain": served_steps_s / plain_steps_s,
+            "admission": {"budget_bytes": budget, "footprint_bytes_at_open": footprint_open,
+                          "footprint_bytes_at_end": used_after, "admitted": ns},
+            "bit_exact": {"stream_final_equals_plain_whole_field": same, "oracle_3_slices": oracle_ok},
+            "cpu_baseline": _cpu_baseline("serve2d"),
+            "e2e": {"value": ns * n_e2e * world / e2e_wall, "unit": "timesteps/s",
+                    "h2d_bytes_per_step": int(4 * statistics.mean(n * n for n, _ in specs)),
+                    "d2h_bytes_per_step": None},
+            "gpu_launches": int(launches_per_push * ns * n_sat),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    for p in plans.values():
+        p.close()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def gpu_arm(args):
@@ -287,6 +706,10 @@ def gpu_arm(args):
             det.append(st[0])
             stages.append(st)
     det_ms = statistics.mean(det)
+    desc = plan.describe()
+    streaming = desc["detect_variant"] != 0
+    stage_names = (["detect", "survive+scan", "emit+locate", "link", "label"] if streaming
+                   else ["detect", "scan", "finalize", "link", "label"])
     alg_bytes = 4.0 * nverts
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (det_ms / 1e3) / 1e9
@@ -342,16 +765,16 @@ def gpu_arm(args):
             "p50_step_ms": statistics.median(step_ms), "p99_step_ms": p99,
             "punctures": int(P), "trajectories": int(len(np.unique(res["label"]))),
             "bit_exact_sample": exact,
-            "stages_ms": {k: statistics.mean(s[i] for s in stages)
-                          for i, k in enumerate(["detect", "scan", "finalize", "link", "label"])},
+            "stages_ms": {k: statistics.mean(s[i] for s in stages) for i, k in enumerate(stage_names)},
+            "plan": desc,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(wl),
-                         "kernel": "k_detect", "peak_kind": peak_kind,
+                         "kernel": "k_detect2_stream" if streaming else "k_detect", "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": det_ms},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "simplices/s",
                     "h2d_bytes_per_step": int(nverts * 4), "d2h_bytes_per_step": int(P * 56 + 24)},
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": int(desc["kernels_per_execute"]) * args.steps,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
@@ -369,11 +792,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="spiral2d")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve2d: Poisson phase seconds")
+    ap.add_argument("--sat-pushes", type=int, default=24, help="serve2d: saturated pushes per stream")
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="serve2d: admission budget")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "batch2d":
+        batch_arm(args)
+    elif args.workload == "serve2d":
+        serve_arm(args)
     else:
         gpu_arm(args)
 

@@ -145,6 +145,19 @@ ftk_status ftk_plan_device_view(ftk_plan *plan, ftk_device_view *view);
 ftk_status ftk_plan_stage_times(ftk_plan *plan, float *ms, int cap, int *n);
 ftk_status ftk_plan_destroy(ftk_plan *plan);
 
+/* Launch configuration a plan chose (for reports and benchmarks). */
+typedef struct {
+    int32_t detect_variant;       /* 0 = tiled detect, 1 = streaming 2D detect,
+                                     2 = streaming 2D detect with exact rounding */
+    int32_t kernels_per_execute;  /* kernel launches one execute queues
+                                     (an overflow or exact-rounding re-run adds more) */
+    int32_t rows_per_unit;        /* grid rows (y) of base vertices per detect unit */
+    int32_t slices_per_unit;      /* time slices of base vertices per detect unit */
+    int64_t detect_units;         /* CTAs of the detect launch */
+    int64_t capacity;             /* current puncture capacity */
+} ftk_plan_desc;
+ftk_status ftk_plan_describe(ftk_plan *plan, ftk_plan_desc *desc);
+
 /* ---------------------------------------------------------------------
  * Batches: many independent 2D fields of uneven size and length (the paper's
  * method applied field by field; the batching itself has no counterpart in
@@ -162,6 +175,8 @@ ftk_status ftk_batch_execute(ftk_batch *batch, const float *const *f_dev, void *
 ftk_status ftk_batch_counts(ftk_batch *batch, int64_t *counts /* [nfields] */);
 ftk_status ftk_batch_download(ftk_batch *batch, ftk_result **outs /* [nfields] */);
 ftk_status ftk_batch_destroy(ftk_batch *batch);
+/* Kernel launches one execute queues over all fields (re-runs excluded). */
+ftk_status ftk_batch_kernels(ftk_batch *batch, int64_t *kernels_per_execute);
 /* One-shot batch: outs[i] receives field i's punctured faces, sorted by face_id. */
 ftk_status ftk_track_cp2d_batch(int nfields, const float *const *f_dev, const int64_t (*dims)[3],
                                 const ftk_params *p, ftk_result **outs, void *cuda_stream);

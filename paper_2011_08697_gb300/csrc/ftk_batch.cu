@@ -258,6 +258,19 @@ ftk_status ftk_batch_download(ftk_batch *b, ftk_result **outs) {
     return FTK_OK;
 }
 
+ftk_status ftk_batch_kernels(ftk_batch *b, int64_t *k) {
+    if (!b || !k) return fail(FTK_ERR_ARG, "NULL argument");
+    int64_t total = 0;
+    for (ftk_plan *pl : b->plans) {
+        ftk_plan_desc d;
+        ftk_status st = ftk_plan_describe(pl, &d);
+        if (st != FTK_OK) return st;
+        total += d.kernels_per_execute;
+    }
+    *k = total;
+    return FTK_OK;
+}
+
 ftk_status ftk_batch_destroy(ftk_batch *b) {
     if (!b) return FTK_OK;
     if (b->last) cudaStreamSynchronize(b->last);

@@ -158,6 +158,16 @@ ftk_status choose_blocking(int ndim, const Field &F, Blocking &B, int &variant) 
         choose_time_chunks(F, B, B.nyb, (long long)sms * stream2_ctas_per_sm(F.nx));
         return FTK_OK;
     }
+    if (ndim == 3 && F.nx % 4 == 0 && F.nx <= STREAM3_MAX_NX) {
+        variant = VAR_STREAM3;
+        // plane chunks of (ry + 3) rows of about 10 KB or less; 8 cube planes
+        B.ry = std::max(1, std::min(15, std::min(F.ny, 10240 / (F.nx * 4) - 3)));
+        B.rz = std::min(8, F.nz);
+        B.nyb = (F.ny + B.ry - 1) / B.ry;
+        B.nzb = (F.nz + B.rz - 1) / B.rz;
+        choose_time_chunks(F, B, (long long)B.nyb * B.nzb, (long long)sms * stream3_ctas_per_sm(F.nx, B));
+        return FTK_OK;
+    }
     variant = VAR_TILE;
     bool ok = false;
     if (ndim == 2) {
@@ -230,7 +240,7 @@ ftk_status settle_from(ftk_plan *pl, bool have_counters) {
         if (st & ST_RANGE) return status_of(st);
         if (st & ST_WIDE) {
             // a sample beyond the fast rounding range: redo with exact rounding
-            variant = VAR_STREAM2_EXACT;
+            variant = exact_variant(pl->variant);
             s = launch(pl, pl->last_dev, pl->stream, variant);
             if (s != FTK_OK) return s;
             continue;
@@ -535,6 +545,18 @@ ftk_status ftk_plan_stage_times(ftk_plan *pl, float *ms, int cap, int *n) {
     if (!pl->timing) return fail(FTK_ERR_STATE, "plan created without the stage-timing flag");
     *n = std::min(cap, pl->nstage);
     for (int i = 0; i < *n; ++i) ms[i] = pl->stage_ms[i];
+    return FTK_OK;
+}
+
+ftk_status ftk_plan_describe(ftk_plan *pl, ftk_plan_desc *d) {
+    if (!pl || !d) return fail(FTK_ERR_ARG, "NULL argument");
+    std::memset(d, 0, sizeof(*d));
+    d->detect_variant = pl->variant;
+    d->kernels_per_execute = pl->variant != VAR_TILE ? 8 : 5;
+    d->rows_per_unit = pl->B.ry;
+    d->slices_per_unit = pl->B.tc;
+    d->detect_units = (int64_t)pl->B.ntc * pl->B.nyb * pl->B.nzb;
+    d->capacity = pl->W.cap;
     return FTK_OK;
 }
 

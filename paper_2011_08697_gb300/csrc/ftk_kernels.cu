@@ -26,6 +26,7 @@
 
 #include "ftk_device.cuh"
 #include "ftk_kernels.cuh"
+#include "ftk_tma.cuh"
 
 namespace ftk {
 
@@ -888,53 +889,6 @@ __global__ void __launch_bounds__(NT) k_label(Field F, Workspace W) {
 constexpr int RY2 = 16;       // cube rows per unit
 constexpr int NS2 = 16;       // TMA ring slots (rows)
 constexpr int CX = 8;         // columns per consumer thread
-constexpr long long WAIT_CYCLES = 4000000000LL;   // bound of every mbarrier wait (~2 s)
-constexpr uint32_t MAGIC_BITS = 0x4B400000u;      // bit pattern of 1.5 * 2^23
-constexpr float MAGIC_F = 12582912.0f;            // 1.5 * 2^23
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait on a phase; false if it did not complete within WAIT_CYCLES
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
-    return true;
-}
-__device__ __forceinline__ void tma_row(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
 // quantised sample in offset encoding: MAGIC_BITS + rint(v 2^S) (mod 2^32);
 // differences of two encodings are exact integer differences
 template <bool EXACT>
@@ -952,7 +906,7 @@ __device__ __forceinline__ uint32_t qbits(float v, float scale, uint32_t &bad) {
 __host__ __device__ inline int stream2_consumers(int nx) { return ((nx + CX - 1) / CX + 31) / 32 * 32; }
 
 struct Stream2Layout {
-    int ring, bars, bm, bmw, total;
+    int ring, bars, bm, bmw, cnt, total;
 };
 __host__ __device__ inline Stream2Layout stream2_layout(int nx) {
     Stream2Layout L;
@@ -960,7 +914,8 @@ __host__ __device__ inline Stream2Layout stream2_layout(int nx) {
     L.bars = L.ring + NS2 * nx * 4;
     L.bmw = (RY2 * nx + 31) / 32;
     L.bm = round_up16(L.bars + (2 * NS2 + 4) * 8);
-    L.total = round_up16(L.bm + 2 * L.bmw * 4);
+    L.cnt = L.bm + 2 * L.bmw * 4;     // [2] survivors per slab buffer
+    L.total = round_up16(L.cnt + 2 * 4);
     return L;
 }
 
@@ -995,6 +950,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     uint64_t *done = empty + NS2;    // [2] slab bits complete (consumer warps arrive)
     uint64_t *freed = done + 2;      // [2] bitmap compacted and cleared (compactor arrives)
     uint32_t *bm = reinterpret_cast<uint32_t *>(smem + L.bm);   // [2][bmw]
+    int *scnt = reinterpret_cast<int *>(smem + L.cnt);          // [2]
     unsigned *status = &W.ctr->status;
 
     const int tci = blockIdx.x % B.ntc;
@@ -1020,6 +976,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
         mbar_fence_init();
     }
     for (int i = threadIdx.x; i < 2 * L.bmw; i += blockDim.x) bm[i] = 0u;
+    if (threadIdx.x < 2) scnt[threadIdx.x] = 0;
     __syncthreads();
 
     if (warp == CW) {
@@ -1049,24 +1006,15 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     }
     if (warp == CW + 1) {
         // ---------------- compactor ---------------------------------------
-        const int per = (L.bmw + 31) / 32;
-        const int w0 = min(L.bmw, lane * per), w1 = min(L.bmw, w0 + per);
+        // words are dealt to the lanes round-robin (dense regions spread over
+        // the warp); pass 1 counts, pass 2 writes in bitmap order
         for (int q = 0; q < nslab; ++q) {
             const int b = q & 1;
             if (!__all_sync(0xffffffffu, mbar_wait(&done[b], (q >> 1) & 1))) {
                 if (lane == 0) atomicOr(status, ST_TIMEOUT);
                 return;
             }
-            uint32_t *words = bm + b * L.bmw;
-            int cnt = 0;
-            for (int w = w0; w < w1; ++w) cnt += __popc(words[w]);
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int total = scnt[b];
             const int t = t0 + q;
             const long long seg = (long long)t * B.nyb + yb;
             long long base = 0;
@@ -1076,20 +1024,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
                 W.seg_sstage[seg] = base;
                 if (base + total > W.scap) atomicOr(status, ST_SOVERFLOW);
             }
-            base = __shfl_sync(0xffffffffu, base, 0);
-            long long pos = base + incl - cnt;
-            for (int w = w0; w < w1; ++w) {
-                uint32_t bits = words[w];
-                words[w] = 0u;
-                while (bits) {
-                    const int bit = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const int idx = w * 32 + bit;
-                    const long long g = ((long long)t * ny + y0 + idx / nx) * nx + idx % nx;
-                    if (pos < W.scap) W.surv[pos] = g;
-                    ++pos;
-                }
+            if (total > 0) {
+                base = __shfl_sync(0xffffffffu, base, 0);
+                compact_bits<16>(bm + b * L.bmw, L.bmw, nx, 1.0f / (float)nx, (long long)t * ny + y0, base, W.surv,
+                             W.scap);
             }
+            __syncwarp();
+            if (lane == 0) scnt[b] = 0;
             __syncwarp();
             if (lane == 0) mbar_arrive(&freed[b]);
         }
@@ -1119,6 +1060,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     for (int k = 0; k < 11; ++k) fa[k] = fb[k] = fc[k] = MAGIC_BITS;
     uint32_t pprev = 0;
     int j = 0;
+    int nsv = 0;     // survivors this thread found in the current slab
     bool ok = true;
 
     for (int sl = 0; sl < nsl && ok; ++sl) {
@@ -1197,6 +1139,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
                         if (sv8) {
                             const int idx = i * nx + x0;
                             atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
+                            nsv += __popc(sv8);
                             if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
                         }
                     }
@@ -1209,6 +1152,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
                         if (sv8) {
                             const int idx = i * nx + x0;
                             atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
+                            nsv += __popc(sv8);
                             if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
                         }
                     }
@@ -1223,6 +1167,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
             }
         }
         if (sl > 0) {
+            const int n = __reduce_add_sync(0xffffffffu, nsv);
+            if (lane == 0 && n) atomicAdd(&scnt[q & 1], n);
+            nsv = 0;
             __syncwarp();
             if (lane == 0) mbar_arrive(&done[q & 1]);
         }
@@ -1241,10 +1188,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
                     if (sv8) {
                         const int idx = i * nx + x0;
                         atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
+                        nsv += __popc(sv8);
                         if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
                     }
                 }
             }
+            const int n = __reduce_add_sync(0xffffffffu, nsv);
+            if (lane == 0 && n) atomicAdd(&scnt[q & 1], n);
             __syncwarp();
             if (lane == 0) mbar_arrive(&done[q & 1]);
         }
@@ -1298,33 +1248,99 @@ __device__ unsigned long long eval_cube(const Field &F, long long g) {
     return m;
 }
 
-// one CTA per segment (grid-stride): evaluate its survivors, local scan of
-// their puncture counts, segment total
+// one thread per surviving cube (grid-stride over the survivor list): the
+// form for 2D, whose cubes have few corners and faces
 template <int N>
-__global__ void __launch_bounds__(NT) k_survive(Field F, Workspace W) {
-    __shared__ long long red[NT / 32 + 1];
+__global__ void __launch_bounds__(NT) k_survive_eval_thread(Field F, Workspace W) {
     if (W.ctr->status & ST_SOVERFLOW) return;
-    for (long long seg = blockIdx.x; seg < W.nseg; seg += gridDim.x) {
-        const int n = W.seg_scnt[seg];
-        if (n == 0) {
-            if (threadIdx.x == 0) W.seg_cnt[seg] = 0;
-            continue;
+    const long long ns = (long long)W.ctr->survivors;
+    for (long long s = blockIdx.x * (long long)NT + threadIdx.x; s < ns; s += (long long)gridDim.x * NT)
+        W.surv_mask[s] = eval_cube<N>(F, W.surv[s]);
+}
+
+// one warp per surviving cube (grid-stride over the survivor list): lanes
+// 0..2^(N+1)-1 load the corner gradients, then the face types are split over
+// the lanes; bit tt of the mask = face type tt punctured
+template <int N>
+__global__ void __launch_bounds__(NT) k_survive_eval(Field F, Workspace W) {
+    constexpr int D = N + 1;
+    constexpr int NCRN = 1 << D;
+    constexpr int T = MeshDims<N>::T;
+    constexpr int WPB = NT / 32;
+    __shared__ int32_t Gs[WPB][NCRN][N];
+    if (W.ctr->status & ST_SOVERFLOW) return;
+    const long long ns = (long long)W.ctr->survivors;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * WPB;
+    for (long long s = (long long)blockIdx.x * WPB + warp; s < ns; s += stride) {
+        const long long g = W.surv[s];
+        const Pt b = decode_vertex(F, g);
+        int inside = 0;   // bit a: axis a can step +1
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int slot = a == N ? 3 : a;
+            const int ext = a == N ? F.nt : ext_of(F, a);
+            if (b.c[slot] + 1 < ext) inside |= 1 << a;
         }
-        const long long base = W.seg_sstage[seg];
-        long long run = 0;
-        for (int b0 = 0; b0 < n; b0 += NT) {
-            const int q = b0 + threadIdx.x;
-            unsigned long long m = 0;
-            if (q < n) {
-                m = eval_cube<N>(F, W.surv[base + q]);
-                W.surv_mask[base + q] = m;
+        if (lane < NCRN) {
+            if (lane & ~inside) {
+#pragma unroll
+                for (int r = 0; r < N; ++r) Gs[warp][lane][r] = 0;
+            } else {
+                const Pt p = add_mask<N>(b, lane);
+#pragma unroll
+                for (int r = 0; r < N; ++r) Gs[warp][lane][r] = grad_global(F, p, r);
             }
-            long long tot;
-            const long long ex = block_excl_scan<long long>(__popcll(m), red, tot);
-            if (q < n) W.surv_off[base + q] = (int)(run + ex);
-            run += tot;
         }
-        if (threadIdx.x == 0) W.seg_cnt[seg] = (int)run;
+        __syncwarp();
+        unsigned long long m = 0;
+#pragma unroll
+        for (int t0 = 0; t0 < T; t0 += 32) {
+            const int tt = t0 + lane;
+            bool pun = false;
+            if (tt < T) {
+                const uint8_t *ch = mesh<N>().face[tt];
+                if (!(ch[N - 1] & ~inside)) {
+                    int32_t V[N + 1][N];
+#pragma unroll
+                    for (int k = 0; k <= N; ++k) {
+                        const int c = k == 0 ? 0 : ch[k - 1];
+#pragma unroll
+                        for (int r = 0; r < N; ++r) V[k][r] = Gs[warp][c][r];
+                    }
+                    pun = face_punctured<N>(V);
+                }
+            }
+            m |= (unsigned long long)__ballot_sync(0xffffffffu, pun) << t0;
+        }
+        if (lane == 0) W.surv_mask[s] = m;
+        __syncwarp();
+    }
+}
+
+// one warp per segment: offsets of the survivors' punctures within the
+// segment (exclusive scan of the mask popcounts) and the segment total
+__global__ void __launch_bounds__(NT) k_survive_scan(Workspace W) {
+    if (W.ctr->status & ST_SOVERFLOW) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * (NT / 32);
+    for (long long seg = (long long)blockIdx.x * (NT / 32) + warp; seg < W.nseg; seg += stride) {
+        const int n = W.seg_scnt[seg];
+        const long long base = W.seg_sstage[seg];
+        int run = 0;
+        for (int k0 = 0; k0 < n; k0 += 32) {
+            const int k = k0 + lane;
+            const int c = k < n ? __popcll(W.surv_mask[base + k]) : 0;
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (k < n) W.surv_off[base + k] = run + incl - c;
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) W.seg_cnt[seg] = run;
     }
 }
 
@@ -1570,7 +1586,10 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     const bool capturing = cap != cudaStreamCaptureStatusNone;
-    if (N == 2 && variant != VAR_TILE) {
+    if (N == 3 && variant != VAR_TILE) {
+        const cudaError_t e = launch_detect3(variant, F, B, W, s, capturing);
+        if (e != cudaSuccess) return e;
+    } else if (N == 2 && variant != VAR_TILE) {
         const size_t smem = stream2_smem_bytes(F.nx);
         const void *k = variant == VAR_STREAM2_EXACT ? stream2_kernel<true>(F.nx) : stream2_kernel<false>(F.nx);
         // the attribute only ever grows: a graph may replay a wider field's
@@ -1603,10 +1622,11 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
         k_detect<N><<<(unsigned)units, NT, smem, s>>>(F, B, W);
     }
     if (ev) cudaEventRecord(ev[1], s);
-    const bool stream = N == 2 && variant != VAR_TILE;
+    const bool stream = variant != VAR_TILE;
     if (stream) {
-        const long long ng = W.nseg < 65535LL * 8 ? W.nseg : 65535LL * 8;
-        k_survive<N><<<(unsigned)(ng > 0 ? ng : 1), NT, 0, s>>>(F, W);
+        if constexpr (N == 2) k_survive_eval_thread<N><<<sg, NT, 0, s>>>(F, W);
+        else k_survive_eval<N><<<sg * 2, NT, 0, s>>>(F, W);
+        k_survive_scan<<<sg, NT, 0, s>>>(W);
     }
     {
         cudaError_t e2 = cudaGetLastError();

@@ -114,7 +114,13 @@ enum : int {
     VAR_TILE = 0,           // smem-tile kernel: any 2D/3D shape
     VAR_STREAM2 = 1,        // streaming 2D kernel (nx % 4 == 0, 16-byte aligned rows)
     VAR_STREAM2_EXACT = 2,  // same, exact rounding for |f 2^S| > 2^22
+    VAR_STREAM3 = 3,        // streaming 3D kernel (nx % 4 == 0, nx <= 512, 16-byte aligned)
+    VAR_STREAM3_EXACT = 4,  // same, exact rounding
 };
+constexpr int STREAM3_MAX_NX = 512;   // widest row the 3D streaming kernel takes
+inline int exact_variant(int v) {
+    return v == VAR_STREAM2 ? VAR_STREAM2_EXACT : v == VAR_STREAM3 ? VAR_STREAM3_EXACT : v;
+}
 constexpr int STREAM2_ROWS = 16;      // cube rows per unit of the streaming kernel
 constexpr int STREAM2_MAX_NX = 2048;  // widest row the streaming kernel takes
 
@@ -122,6 +128,13 @@ size_t detect_smem_bytes(int ndim, const Field &F, const Blocking &B);
 size_t stream2_smem_bytes(int nx);
 int stream2_threads(int nx);
 int stream2_ctas_per_sm(int nx);
+// 3D streaming kernel: smem per CTA for B.ry, B.rz, B.ns; threads; resident
+// CTAs per SM; launch (the smem attribute is set outside graph capture)
+size_t stream3_smem_bytes(int nx, const Blocking &B);
+int stream3_threads();
+int stream3_ctas_per_sm(int nx, const Blocking &B);
+cudaError_t launch_detect3(int variant, const Field &F, const Blocking &B, const Workspace &W, cudaStream_t s,
+                           bool capturing);
 cudaError_t launch_pipeline(int ndim, int variant, const Field &F, const Blocking &B, const Workspace &W,
                             cudaStream_t s, cudaEvent_t *ev /* 6 events or null */);
 

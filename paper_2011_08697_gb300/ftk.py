@@ -48,6 +48,12 @@ class ftk_device_view(ctypes.Structure):
                 ("off", ctypes.c_void_p), ("morse", ctypes.c_void_p)]
 
 
+class ftk_plan_desc(ctypes.Structure):
+    _fields_ = [("detect_variant", ctypes.c_int32), ("kernels_per_execute", ctypes.c_int32),
+                ("rows_per_unit", ctypes.c_int32), ("slices_per_unit", ctypes.c_int32),
+                ("detect_units", ctypes.c_int64), ("capacity", ctypes.c_int64)]
+
+
 _lib = None
 
 # every symbol the header declares (checked by the CPU test-suite)
@@ -58,7 +64,7 @@ EXPORTS = [
     "ftk_plan_download", "ftk_plan_device_view", "ftk_plan_stage_times", "ftk_plan_destroy",
     "ftk_track_cp2d_noalloc",
     "ftk_batch_create", "ftk_batch_execute", "ftk_batch_counts", "ftk_batch_download",
-    "ftk_batch_destroy", "ftk_track_cp2d_batch",
+    "ftk_batch_destroy", "ftk_track_cp2d_batch", "ftk_plan_describe", "ftk_batch_kernels",
     "ftk_stream_open", "ftk_stream_push", "ftk_stream_close", "ftk_server_create",
     "ftk_server_used", "ftk_server_destroy", "ftk_stream_open_in",
 ]
@@ -92,6 +98,8 @@ def lib():
         "ftk_plan_device_view": (i32, [vp, ctypes.POINTER(ftk_device_view)]),
         "ftk_plan_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
         "ftk_plan_destroy": (i32, [vp]),
+        "ftk_plan_describe": (i32, [vp, ctypes.POINTER(ftk_plan_desc)]),
+        "ftk_batch_kernels": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ftk_track_cp2d_noalloc": (i32, [vp, i64, i64, i64, ctypes.POINTER(ftk_params), vp, i64,
                                          ctypes.POINTER(ctypes.c_int64), vp]),
         "ftk_batch_create": (i32, [i32, vp, ctypes.POINTER(ftk_params), pp]),
@@ -241,6 +249,11 @@ class Plan:
         _check(lib().ftk_plan_stage_times(self._h, ms, 8, ctypes.byref(n)))
         return list(ms[: n.value])
 
+    def describe(self) -> dict:
+        d = ftk_plan_desc()
+        _check(lib().ftk_plan_describe(self._h, ctypes.byref(d)))
+        return {k: getattr(d, k) for k, _ in ftk_plan_desc._fields_}
+
     def close(self):
         if getattr(self, "_h", None):
             lib().ftk_plan_destroy(self._h)
@@ -324,6 +337,11 @@ class Batch:
         out = np.zeros(self.n, dtype=np.int64)
         _check(lib().ftk_batch_counts(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         return out
+
+    def kernels(self) -> int:
+        k = ctypes.c_int64()
+        _check(lib().ftk_batch_kernels(self._h, ctypes.byref(k)))
+        return k.value
 
     def download(self):
         outs = (ctypes.c_void_p * self.n)()

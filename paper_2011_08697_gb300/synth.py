@@ -222,3 +222,33 @@ def poisson_arrivals(nstreams: int, rate_total: float, duration_s: float, seed: 
             events.append((t, s))
     events.sort()
     return events
+
+
+def blob_slices_torch(bs: BlobSet, k0: int, k1: int, device, chunk: int = 16):
+    """Slices k0..k1-1 of a 2D moving blob field as one float32 torch tensor
+    (k1-k0, ny, nx) computed on ``device``: the law of :func:`blob_slice`
+    (sum over blobs of separable Gaussians, FP64, cast once to float32),
+    written as a product over the blob axis.  Values may differ from the NumPy
+    generator in the last bit; both tracking sides always read the same
+    float32 array."""
+    import torch
+    nx, ny = bs.dims
+    f64 = torch.float64
+    cx = torch.as_tensor(bs.centre[:, 0], dtype=f64, device=device)
+    cy = torch.as_tensor(bs.centre[:, 1], dtype=f64, device=device)
+    vx = torch.as_tensor(bs.vel[:, 0], dtype=f64, device=device)
+    vy = torch.as_tensor(bs.vel[:, 1], dtype=f64, device=device)
+    inv = torch.as_tensor(1.0 / (2.0 * bs.sigma ** 2), dtype=f64, device=device)
+    amp = torch.as_tensor(bs.amp, dtype=f64, device=device)
+    xs = torch.arange(nx, dtype=f64, device=device)
+    ys = torch.arange(ny, dtype=f64, device=device)
+    out = torch.empty((k1 - k0, ny, nx), dtype=torch.float32, device=device)
+    for a in range(k0, k1, chunk):
+        ks = torch.arange(a, min(k1, a + chunk), dtype=f64, device=device)
+        ccx = cx[None, :] + vx[None, :] * ks[:, None]            # (K, nb)
+        ccy = cy[None, :] + vy[None, :] * ks[:, None]
+        ex = torch.exp(-((xs[None, None, :] - ccx[:, :, None]) ** 2) * inv[None, :, None])   # (K, nb, nx)
+        ey = torch.exp(-((ys[None, None, :] - ccy[:, :, None]) ** 2) * inv[None, :, None])   # (K, nb, ny)
+        ey = ey * amp[None, :, None]
+        out[a - k0: a - k0 + len(ks)] = torch.bmm(ey.transpose(1, 2), ex).to(torch.float32)
+    return out

@@ -60,6 +60,19 @@ CASES = [
                                                               sigma_range=(2.0, 9.0)), 20),
     ("stream_levels_20x37x7", lambda: synth.random_levels((7, 37, 20), levels=(-1, -.5, 0, .5, 1), seed=17), 20),
     ("stream_noisy_128x33x12", lambda: synth.spiral_woven(128, 12, sigma=0.05, seed=6, ny=33), 20),
+    # shapes taking the streaming 3D kernel (nx % 4 == 0, nx <= 512)
+    ("s3_levels_8x9x7x4", lambda: synth.random_levels((4, 7, 9, 8), seed=21), 20),
+    ("s3_levels5_12x5x6x3", lambda: synth.random_levels((3, 6, 5, 12), levels=(-1, -.5, 0, .5, 1), seed=22), 20),
+    ("s3_tiny_4x2x2x2", lambda: synth.random_levels((2, 2, 2, 4), seed=23), 20),
+    ("s3_nt1_16x10x9", lambda: synth.random_levels((1, 9, 10, 16), seed=24), 20),
+    ("s3_zero_8x6x5x3", lambda: np.zeros((3, 5, 6, 8), np.float32), 20),
+    ("s3_wide_132x4x3x2", lambda: synth.random_levels((2, 3, 4, 132), seed=25), 20),
+    ("s3_wide_264x3x3x2", lambda: synth.random_levels((2, 3, 3, 264), seed=26), 20),
+    ("s3_levels5_20x17x9x3", lambda: synth.random_levels((3, 9, 17, 20), levels=(-1, -.5, 0, .5, 1), seed=27), 20),
+    ("s3_blobs_36x40x20x6", lambda: synth.gaussian_blobs((36, 40, 20), 6, nblobs=16, seed=28,
+                                                          sigma_range=(2.0, 6.0)), 20),
+    ("s3_wide_values", lambda: synth.gaussian_blobs((24, 20, 18), 4, nblobs=10, seed=29,
+                                                     sigma_range=(2.0, 5.0)) * 10.0, 20),
 ]
 
 
