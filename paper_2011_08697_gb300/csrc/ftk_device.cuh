@@ -13,7 +13,7 @@
 //    by Simulation of Simplicity: entry (row r, column c) of a determinant
 //    whose columns are sorted by global vertex id is perturbed by
 //    eps^(2^(c*N + r)); the sign is that of the first nonzero coefficient
-//    in increasing exponent order, read from a compile-time term table.
+//    in increasing exponent order, written out term by term for N = 2, 3.
 //  * BigInt<W>: fixed-width two's-complement integers for the exact Morse
 //    classification (products up to ~2^390 in 3D).
 #pragma once
@@ -83,75 +83,16 @@ __host__ __device__ constexpr int chain_key(const int (&m)[N]) {
 // determinant in increasing exponent order, each with the permutations that
 // contain it.  Bit c*N + r of `mask` marks entry (row r, column c).
 // ----------------------------------------------------------------------------
-template <int N>
-struct SosTable {
-    static constexpr int NP = (N == 2) ? 2 : 6;
-    static constexpr int MAXT = (N == 2) ? 6 : 33;
-    int8_t perm[NP][N];
-    int8_t psign[NP];
-    uint16_t mask[MAXT];
-    uint8_t pset[MAXT];   // bit p set: permutation p contains the entry set
-    uint8_t ncols[MAXT];  // bitmask of columns whose entry is perturbed
-    int nterms;
-
-    __host__ __device__ constexpr SosTable() : perm{}, psign{}, mask{}, pset{}, ncols{}, nterms(0) {
-        // permutations of {0..N-1}, lexicographic
-        int p[N] = {};
-        for (int i = 0; i < N; ++i) p[i] = i;
-        int np = 0;
-        while (true) {
-            int inv = 0;
-            for (int i = 0; i < N; ++i)
-                for (int j = i + 1; j < N; ++j)
-                    if (p[i] > p[j]) ++inv;
-            for (int i = 0; i < N; ++i) perm[np][i] = (int8_t)p[i];
-            psign[np] = (inv & 1) ? -1 : 1;
-            ++np;
-            int i = N - 2;
-            while (i >= 0 && p[i] >= p[i + 1]) --i;
-            if (i < 0) break;
-            int j = N - 1;
-            while (p[j] <= p[i]) --j;
-            int t = p[i]; p[i] = p[j]; p[j] = t;
-            for (int a = i + 1, b = N - 1; a < b; ++a, --b) { t = p[a]; p[a] = p[b]; p[b] = t; }
-        }
-        // masks in increasing order = increasing exponent sum_{keys} 2^key
-        for (int m = 1; m < (1 << (N * N)); ++m) {
-            int rows = 0, cols = 0;
-            bool ok = true;
-            for (int c = 0; c < N && ok; ++c)
-                for (int r = 0; r < N && ok; ++r)
-                    if ((m >> (c * N + r)) & 1) {
-                        if (((rows >> r) & 1) || ((cols >> c) & 1)) ok = false;
-                        rows |= 1 << r;
-                        cols |= 1 << c;
-                    }
-            if (!ok) continue;
-            int ps = 0;
-            for (int q = 0; q < NP; ++q) {
-                bool has = true;
-                for (int c = 0; c < N; ++c)
-                    if (((cols >> c) & 1) && !((m >> (c * N + perm[q][c])) & 1)) has = false;
-                if (has) ps |= 1 << q;
-            }
-            mask[nterms] = (uint16_t)m;
-            pset[nterms] = (uint8_t)ps;
-            ncols[nterms] = (uint8_t)cols;
-            ++nterms;
-        }
-    }
-};
-
 // ----------------------------------------------------------------------------
 // Exact determinants and the SoS sign
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ int sgn128(__int128 v) { return (v > 0) - (v < 0); }
 
 // M[c][r]: column c = vertex (sorted by id), row r = vector component
-__device__ __forceinline__ __int128 det_exact(const int32_t (&M)[2][2]) {
+__host__ __device__ __forceinline__ __int128 det_exact(const int32_t (&M)[2][2]) {
     return (__int128)((int64_t)M[0][0] * M[1][1] - (int64_t)M[0][1] * M[1][0]);
 }
-__device__ __forceinline__ __int128 det_exact(const int32_t (&M)[3][3]) {
+__host__ __device__ __forceinline__ __int128 det_exact(const int32_t (&M)[3][3]) {
     // expansion along the first component row; 2x2 minors fit in int64
     const int64_t m0 = (int64_t)M[1][1] * M[2][2] - (int64_t)M[1][2] * M[2][1];
     const int64_t m1 = (int64_t)M[0][1] * M[2][2] - (int64_t)M[0][2] * M[2][1];
@@ -159,14 +100,58 @@ __device__ __forceinline__ __int128 det_exact(const int32_t (&M)[3][3]) {
     return (__int128)M[0][0] * m0 - (__int128)M[1][0] * m1 + (__int128)M[2][0] * m2;
 }
 
-template <int N>
-__device__ __noinline__ int sos_fallback(const int32_t (&M)[N][N]);
+// Sign of det(M + E(eps)) when det(M) = 0 (Simulation of Simplicity, Sec. 4.1;
+// Edelsbrunner-Muecke form): entry M[c][r] is perturbed by eps^(2^(c N + r)),
+// so every set S of perturbed entries has its own exponent sum_{S} 2^(c N + r)
+// and the sign is that of the first nonzero coefficient in increasing
+// exponent order.  A set contributes only if it is a partial permutation
+// (distinct columns and rows); its coefficient is the signed sum over the
+// permutations through S of the unperturbed entries.  In that order the
+// terms are: single entries (coefficient = cofactor), pairs (coefficient =
+// +-the remaining entry) and, at the latest with a full permutation,
+// a constant +-1.  Written out term by term for N = 2 and N = 3:
+__host__ __device__ __forceinline__ int sgn_nz(long long v) { return v > 0 ? 1 : -1; }
+
+__host__ __device__ __forceinline__ int sos_zero_sign(const int32_t (&M)[2][2]) {
+    // masks 1 {(0,0)}, 2 {(0,1)}, 4 {(1,0)}, 6 {(0,1),(1,0)}
+    if (M[1][1]) return sgn_nz(M[1][1]);
+    if (M[1][0]) return -sgn_nz(M[1][0]);
+    if (M[0][1]) return -sgn_nz(M[0][1]);
+    return -1;
+}
+
+__host__ __device__ __forceinline__ int sos_zero_sign(const int32_t (&M)[3][3]) {
+    typedef long long ll;
+    ll v;
+    // masks 1, 2, 4, 8: cofactors of (c,r) = (0,0), (0,1), (0,2), (1,0)
+    if ((v = (ll)M[1][1] * M[2][2] - (ll)M[1][2] * M[2][1])) return sgn_nz(v);
+    if ((v = (ll)M[1][2] * M[2][0] - (ll)M[1][0] * M[2][2])) return sgn_nz(v);
+    if ((v = (ll)M[1][0] * M[2][1] - (ll)M[1][1] * M[2][0])) return sgn_nz(v);
+    if ((v = (ll)M[0][2] * M[2][1] - (ll)M[0][1] * M[2][2])) return sgn_nz(v);
+    // mask 10 {(0,1),(1,0)}: -M[2][2]; mask 12 {(0,2),(1,0)}: +M[2][1]
+    if (M[2][2]) return -sgn_nz(M[2][2]);
+    if (M[2][1]) return sgn_nz(M[2][1]);
+    // mask 16: cofactor of (1,1)
+    if ((v = (ll)M[0][0] * M[2][2] - (ll)M[0][2] * M[2][0])) return sgn_nz(v);
+    // mask 17 {(0,0),(1,1)}: +M[2][2] (zero here); mask 20 {(0,2),(1,1)}: -M[2][0]
+    if (M[2][0]) return -sgn_nz(M[2][0]);
+    // mask 32: cofactor of (1,2); masks 33 (-M[2][1]) and 34 (+M[2][0]) are zero here
+    if ((v = (ll)M[0][1] * M[2][0] - (ll)M[0][0] * M[2][1])) return sgn_nz(v);
+    // mask 64: cofactor of (2,0)
+    if ((v = (ll)M[0][1] * M[1][2] - (ll)M[0][2] * M[1][1])) return sgn_nz(v);
+    // mask 66 {(0,1),(2,0)}: +M[1][2]; mask 68 {(0,2),(2,0)}: -M[1][1];
+    // mask 80 {(1,1),(2,0)}: -M[0][2]; mask 84 {(0,2),(1,1),(2,0)}: -1
+    if (M[1][2]) return sgn_nz(M[1][2]);
+    if (M[1][1]) return -sgn_nz(M[1][1]);
+    if (M[0][2]) return -sgn_nz(M[0][2]);
+    return -1;
+}
 
 template <int N>
-__device__ __forceinline__ int sos_det_sign(const int32_t (&M)[N][N]) {
+__host__ __device__ __forceinline__ int sos_det_sign(const int32_t (&M)[N][N]) {
     const __int128 d = det_exact(M);
     if (d != 0) return d > 0 ? 1 : -1;
-    return sos_fallback<N>(M);
+    return sos_zero_sign(M);
 }
 
 // ----------------------------------------------------------------------------

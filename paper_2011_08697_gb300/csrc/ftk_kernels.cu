@@ -32,40 +32,14 @@ namespace ftk {
 
 __constant__ MeshTables<2> c_mesh2 = MeshTables<2>();
 __constant__ MeshTables<3> c_mesh3 = MeshTables<3>();
-__constant__ SosTable<2> c_sos2 = SosTable<2>();
-__constant__ SosTable<3> c_sos3 = SosTable<3>();
 
 template <int N> __device__ __forceinline__ const MeshTables<N> &mesh();
 template <> __device__ __forceinline__ const MeshTables<2> &mesh<2>() { return c_mesh2; }
 template <> __device__ __forceinline__ const MeshTables<3> &mesh<3>() { return c_mesh3; }
-template <int N> __device__ __forceinline__ const SosTable<N> &sos();
-template <> __device__ __forceinline__ const SosTable<2> &sos<2>() { return c_sos2; }
-template <> __device__ __forceinline__ const SosTable<3> &sos<3>() { return c_sos3; }
 
 constexpr int NT = 256;              // threads per CTA of every kernel here
 constexpr float RANGE_LIMIT = 268435456.0f;   // 2^28
 constexpr int UF_LIMIT = 1 << 22;    // bound on union-find retries / path steps
-
-// ----------------------------------------------------------------------------
-// SoS fallback: first nonzero coefficient of det(M + E(eps)) in increasing
-// exponent order (the exact determinant has already been found to be 0).
-// ----------------------------------------------------------------------------
-template <int N>
-__device__ __noinline__ int sos_fallback(const int32_t (&M)[N][N]) {
-    const SosTable<N> &S = sos<N>();
-    for (int t = 0; t < S.nterms; ++t) {
-        long long coef = 0;
-        for (int q = 0; q < SosTable<N>::NP; ++q) {
-            if (!((S.pset[t] >> q) & 1)) continue;
-            long long term = S.psign[q];
-            for (int c = 0; c < N; ++c)
-                if (!((S.ncols[t] >> c) & 1)) term *= (long long)M[c][S.perm[q][c]];
-            coef += term;
-        }
-        if (coef != 0) return coef > 0 ? 1 : -1;
-    }
-    return -1;  // not reached: the fully perturbed terms have coefficient +-1
-}
 
 // Exact SoS puncture test of one face; V[k] = gradient at the k-th vertex in
 // increasing global-id order.
