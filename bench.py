@@ -708,6 +708,8 @@ def gpu_arm(args):
     det_ms = statistics.mean(det)
     desc = plan.describe()
     streaming = desc["detect_variant"] != 0
+    detect_kernel = {0: "k_detect", 1: "k_detect2_stream", 2: "k_detect2_stream<exact>",
+                     3: "k_detect3_stream", 4: "k_detect3_stream<exact>"}[desc["detect_variant"]]
     stage_names = (["detect", "survive+scan", "emit+locate", "link", "label"] if streaming
                    else ["detect", "scan", "finalize", "link", "label"])
     alg_bytes = 4.0 * nverts
@@ -769,7 +771,7 @@ def gpu_arm(args):
             "plan": desc,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(wl),
-                         "kernel": "k_detect2_stream" if streaming else "k_detect", "peak_kind": peak_kind,
+                         "kernel": detect_kernel, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": det_ms},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "simplices/s",

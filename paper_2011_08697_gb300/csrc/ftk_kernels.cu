@@ -813,6 +813,129 @@ __global__ void __launch_bounds__(NT) k_link(Field F, Blocking B, Workspace W) {
     }
 }
 
+// survivor index of the cube based at vertex b (its segment's survivors are
+// sorted by vertex id), or -1 if the cube did not survive the cull (then
+// none of its faces is punctured)
+__device__ __forceinline__ long long find_cube(const Field &F, const Blocking &B, const Workspace &W, const Pt &b) {
+    const long long seg = segment_of_coords(b.c[1], b.c[2], b.c[3], F, B);
+    const long long lo0 = W.seg_sstage[seg];
+    const long long hi0 = lo0 + W.seg_scnt[seg];
+    const long long key = (((long long)b.c[3] * F.nz + b.c[2]) * F.ny + b.c[1]) * F.nx + b.c[0];
+    long long lo = lo0, hi = hi0;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (W.surv[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < hi0 && W.surv[lo] == key) ? lo : -1;
+}
+
+// Linking for the streaming variants (Algorithm 1, second loop): the same
+// cells and pairing check as k_link, but a cell's faces lie in two cubes --
+// the cell's base cube (faces without the base vertex's first step dropped)
+// and the cube one step further (the face opposite the base vertex) -- so
+// one search for the other cube's punctured-face mask resolves every side
+// of the cell, and a face's position follows from its cube's offset and mask.
+template <int N>
+__global__ void __launch_bounds__(NT) k_link_cubes(Field F, Blocking B, Workspace W) {
+    constexpr int D = N + 1;
+    constexpr int FULL = (1 << D) - 1;
+    constexpr int T = MeshDims<N>::T;
+    if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
+    const long long P = W.ctr->punctures;
+    unsigned *status = &W.ctr->status;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        const long long fid = W.face[i];
+        int tt;
+        const Pt base = decode_face<N>(F, fid, tt);
+        const long long s_own = W.staging[i];
+        const unsigned long long mask_own = W.surv_mask[s_own];
+        int m[N];
+        for (int k = 0; k < N; ++k) m[k] = mesh<N>().face[tt][k];
+        Pt cb[2];
+        int cm[2][D];
+        int ncell = 0;
+        if (m[N - 1] == FULL) {
+            int prev = 0;
+            for (int j = 0; j < N; ++j) {
+                const int step = m[j] ^ prev;
+                if (__popc(step) == 2) {
+                    for (int a = 0; a < D; ++a) {
+                        if (!((step >> a) & 1)) continue;
+                        for (int q = 0; q < j; ++q) cm[ncell][q] = m[q];
+                        cm[ncell][j] = prev | (1 << a);
+                        for (int q = j; q < N; ++q) cm[ncell][q + 1] = m[q];
+                        cb[ncell] = base;
+                        ++ncell;
+                    }
+                    break;
+                }
+                prev = m[j];
+            }
+        } else {
+            const int a = __ffs(FULL ^ m[N - 1]) - 1;
+            const int ca = a == N ? 3 : a;
+            const int ext = a == N ? F.nt : (a == 0 ? F.nx : a == 1 ? F.ny : F.nz);
+            if (base.c[ca] >= 1) {
+                cb[ncell] = base;
+                cb[ncell].c[ca] -= 1;
+                cm[ncell][0] = 1 << a;
+                for (int q = 0; q < N; ++q) cm[ncell][q + 1] = m[q] | (1 << a);
+                ++ncell;
+            }
+            if (base.c[ca] + 1 < ext) {
+                cb[ncell] = base;
+                for (int q = 0; q < N; ++q) cm[ncell][q] = m[q];
+                cm[ncell][N] = FULL;
+                ++ncell;
+            }
+        }
+        for (int c = 0; c < ncell; ++c) {
+            // the cell's two cubes: base cb and cb + first step; one is ours
+            const Pt far = add_mask<N>(cb[c], cm[c][0]);
+            const bool own_is_base = cb[c].c[0] == base.c[0] && cb[c].c[1] == base.c[1] &&
+                                     cb[c].c[2] == base.c[2] && cb[c].c[3] == base.c[3];
+            const Pt other = own_is_base ? far : cb[c];
+            const long long s_oth = find_cube(F, B, W, other);
+            const unsigned long long mask_oth = s_oth >= 0 ? W.surv_mask[s_oth] : 0ull;
+            const long long seg_oth = segment_of_coords(other.c[1], other.c[2], other.c[3], F, B);
+            int hits = 0;
+            long long partner = -1;
+            for (int k = 0; k <= D; ++k) {
+                int sm[N];
+                bool in_far;
+                if (k == 0) {
+                    for (int q = 0; q < N; ++q) sm[q] = cm[c][q + 1] ^ cm[c][0];
+                    in_far = true;
+                } else if (k == D) {
+                    for (int q = 0; q < N; ++q) sm[q] = cm[c][q];
+                    in_far = false;
+                } else {
+                    int w = 0;
+                    for (int q = 0; q < D; ++q)
+                        if (q != k - 1) sm[w++] = cm[c][q];
+                    in_far = false;
+                }
+                const int ft = mesh<N>().lookup[chain_key<N>(sm)];
+                const bool in_own = in_far != own_is_base;
+                if (in_own && ft == tt) continue;              // the face itself
+                const unsigned long long mk = in_own ? mask_own : mask_oth;
+                if (!((mk >> ft) & 1)) continue;
+                ++hits;
+                const long long sc = in_own ? s_own : s_oth;
+                const long long seg = in_own ? segment_of_coords(base.c[1], base.c[2], base.c[3], F, B) : seg_oth;
+                partner = W.seg_off[seg] + W.surv_off[sc] + __popcll(mk & ((1ull << ft) - 1ull));
+            }
+            if (hits != 1) {
+                atomicOr(status, ST_PAIRING);
+                continue;
+            }
+            // both ends see the pair; one union suffices
+            if (partner > i) uf_unite(W.parent, (int)i, (int)partner, status);
+        }
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(NT) k_label(Field F, Workspace W) {
     if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
@@ -1334,6 +1457,7 @@ __global__ void __launch_bounds__(NT) k_emit(Field F, Blocking B, Workspace W) {
             m &= m - 1;
             W.face[i] = g * T + tt;
             W.parent[i] = (int)i;
+            W.staging[i] = s;          // the puncture's cube, for the link step
             ++i;
         }
     }
@@ -1344,7 +1468,8 @@ template <int N>
 __global__ void __launch_bounds__(NT) k_locate(Field F, Workspace W) {
     if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
     const long long P = W.ctr->punctures;
-    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+         i += (long long)gridDim.x * blockDim.x) {
         float4 o;
         int8_t mo;
         locate_classify<N>(F, W.face[i], o, mo);
@@ -1610,12 +1735,15 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
     if (ev) cudaEventRecord(ev[2], s);
     if (stream) {
         k_emit<N><<<sg, NT, 0, s>>>(F, B, W);
-        k_locate<N><<<sg, NT, 0, s>>>(F, W);
+        // few, long-running threads in 3D: small blocks spread them over every SM
+        if constexpr (N == 3) k_locate<N><<<sg * 2, 64, 0, s>>>(F, W);
+        else k_locate<N><<<sg, NT, 0, s>>>(F, W);
     } else {
         k_finalize<N><<<sg, NT, 0, s>>>(F, B, W);
     }
     if (ev) cudaEventRecord(ev[3], s);
-    k_link<N><<<sg, NT, 0, s>>>(F, B, W);
+    if (stream) k_link_cubes<N><<<sg, NT, 0, s>>>(F, B, W);
+    else k_link<N><<<sg, NT, 0, s>>>(F, B, W);
     if (ev) cudaEventRecord(ev[4], s);
     k_label<N><<<sg, NT, 0, s>>>(F, W);
     if (ev) cudaEventRecord(ev[5], s);

@@ -74,7 +74,8 @@ struct Workspace {
     int *seg_cnt;            // [nseg] punctures per segment
     long long *seg_stage;    // [nseg] offset of the segment's run in staging
     long long *seg_off;      // [nseg] exclusive scan of seg_cnt
-    long long *staging;      // [cap] face ids, per-segment runs
+    long long *staging;      // [cap] tiled variant: face ids, per-segment runs;
+                             //       streaming variants: surviving cube of each puncture
     long long *face;         // [cap] face ids sorted
     int *parent;             // [cap] union-find
     float4 *off;             // [cap] in-cell offsets x, y, z, t
