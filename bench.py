@@ -251,6 +251,18 @@ def _max_over_ranks(dist, v: float) -> float:
     return float(t.item())
 
 
+def weak_value(units_per_rank: float, world: int, steps: int, tot_ms: float) -> float:
+    """Whole-job throughput of a weak-scaling run: every rank processes its
+    own units (an independent replica), the job's time is the slowest rank's."""
+    return units_per_rank * world * steps / (tot_ms / 1e3)
+
+
+def shard_seed(workload: str, rank: int) -> int:
+    """Seed of rank's replica: ranks process independent synthetic inputs."""
+    return {"batch2d": rank * WORKLOADS["batch2d"]["count"],
+            "serve2d": rank * WORKLOADS["serve2d"]["count"]}.get(workload, rank)
+
+
 def _pct(xs, q):
     xs = sorted(xs)
     return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
@@ -296,7 +308,7 @@ def batch_arm(args):
     _b.build()
     ftk.lib()
     W = WORKLOADS["batch2d"]
-    specs = synth.batch_fields(W["count"], seed0=rank * W["count"], materialise=False)
+    specs = synth.batch_fields(W["count"], seed0=shard_seed("batch2d", rank), materialise=False)
     xs = [synth.blob_slices_torch(bs, 0, nt, dev) for (n, _, nt, _, bs) in specs]
     shapes = [tuple(x.shape) for x in xs]
     faces = sum(face_count((n, n), nt) for (n, _, nt, _, _) in specs)
@@ -362,8 +374,8 @@ def batch_arm(args):
     p_ms = timed(run_plain, plain_steps)
     tot_b = _max_over_ranks(dist, sum(b_ms))
     tot_p = _max_over_ranks(dist, sum(p_ms))
-    value = faces * world * args.steps / (tot_b / 1e3)
-    plain_value = faces * world * plain_steps / (tot_p / 1e3)
+    value = weak_value(faces, world, args.steps, tot_b)
+    plain_value = weak_value(faces, world, plain_steps, tot_p)
 
     # e2e: pinned host fields copied in, batch, results copied out
     hosts = [x.cpu().pin_memory() for x in xs]
@@ -441,7 +453,7 @@ def serve_arm(args):
     ftk.lib()
     W = WORKLOADS["serve2d"]
     ns = W["count"]
-    specs = synth.stream_specs(ns, seed0=rank * ns)
+    specs = synth.stream_specs(ns, seed0=shard_seed("serve2d", rank))
     events = synth.poisson_arrivals(ns, W["rate"], args.duration, seed=rank)
     arrivals = [0] * ns
     for _, s_ in events:
@@ -630,21 +642,14 @@ def gpu_arm(args):
     import torch
     from paper_2011_08697_gb300 import build as _b, ftk
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("gloo", rank=rank, world_size=world)
+    dist, rank, world, local = _dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     _b.build()
-    lib = ftk.lib()
+    ftk.lib()
     wl = args.workload
     W = WORKLOADS[wl]
-    f_np = make_field(wl, seed=rank)
+    f_np = make_field(wl, seed=shard_seed(wl, rank))
     nverts = f_np.size
     faces = face_count(W["dims"], W["nt"])
     x = torch.from_numpy(f_np).to(dev)
@@ -686,13 +691,8 @@ def gpu_arm(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     P_check = plan.count()
     assert P_check == P, "puncture count changed between steps"
-    my_ms = sum(step_ms)
-    tot_ms = my_ms
-    if dist is not None:
-        t = torch.tensor([my_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = faces * world * args.steps / (tot_ms / 1e3)
+    tot_ms = _max_over_ranks(dist, sum(step_ms))
+    value = weak_value(faces, world, args.steps, tot_ms)
 
     # ---- roofline of the dominant kernel (detect), live CUDA events ---------
     det = []
@@ -728,11 +728,7 @@ def gpu_arm(args):
             e2e_plan.execute(host, stream)
             r = e2e_plan.download()
         e2e_s = time.perf_counter() - t0
-    e2e_val = faces * args.steps / e2e_s
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = faces * world * args.steps / float(t.item())
+    e2e_val = weak_value(faces, world, args.steps, 1e3 * _max_over_ranks(dist, e2e_s))
 
     # ---- bit-exact self-check on the oracle's bounded sample + CPU baseline --
     cpu = None
