@@ -1522,16 +1522,21 @@ int stream2_ctas_per_sm(int nx) {
 // In-situ streaming: merging one push (a 2-slice or 1-slice run) into the
 // stream's global union-find over every puncture seen so far.
 //
-// The run's punctures get global slots gi = n_base + i.  Ordinal faces of the
-// run's first slice were already reported by the previous push: they are
-// "shadows", linked to their earlier slot through the previous push's sorted
-// list of last-slice ordinal faces.  Component minima (face ids) are kept at
-// union-find roots; a delta label is the minimum over every face known so far
-// that is connected to the face.
+// Push k runs the pipeline on slices [k-1, k] (k = 0: slice 0 alone).  The
+// run's punctures get global slots gi = n + i.  Ordinal faces of the run's
+// first slice were already reported by push k-1: they are "shadows", linked
+// to their earlier slot through push k-1's sorted list of last-slice ordinal
+// faces.  Component minima (face ids) are kept at union-find roots; a delta
+// label is the minimum over every face known so far that is connected to the
+// face.  The stream's scalars (n, k, ordinal counts) live on the device and
+// the last merge kernel advances them, so the whole push can be a replayed
+// graph.  A run whose pipeline status is bad (range, overflow, exact re-run
+// needed) is not merged: the host repairs the run and merges it again.
 // ----------------------------------------------------------------------------
+constexpr unsigned RUN_BAD = ST_RANGE | ST_OVERFLOW | ST_SOVERFLOW | ST_WIDE | ST_TIMEOUT | ST_PAIRING;
 
-__device__ __forceinline__ bool run_is_shadow(const StreamMerge &M, long long fid_local) {
-    if (M.first) return false;
+__device__ __forceinline__ bool run_is_shadow(const StreamMerge &M, long long k, long long fid_local) {
+    if (k == 0) return false;
     const long long g = fid_local / M.T;
     const int tt = (int)(fid_local - g * M.T);
     return g < M.slice_verts && !(M.tbit & (M.T == 12 ? mesh<2>().face[tt][1] : mesh<3>().face[tt][2]));
@@ -1549,27 +1554,33 @@ __device__ __forceinline__ long long bsearch_ll(const long long *a, long long n,
 }
 
 __global__ void __launch_bounds__(NT) k_stream_place(StreamMerge M) {
+    if (M.ctr->status & RUN_BAD) return;
     const long long P = M.ctr->punctures;
+    const long long k = M.S->k, n_base = M.S->n;
+    const int pp = (int)((k - 1) & 1);
+    const long long shift_t = k == 0 ? 0 : k - 1;
+    const long long shift_g = shift_t * M.slice_verts;
+    const long long n_ord = k == 0 ? 0 : M.S->n_ord[pp];
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
-        const long long gi = M.n_base + i;
+        const long long gi = n_base + i;
         const long long fl = M.face[i];
-        const long long fg = fl + M.shift_g * M.T;
-        const bool sh = run_is_shadow(M, fl);
+        const long long fg = fl + shift_g * M.T;
+        const bool sh = run_is_shadow(M, k, fl);
         M.gfid[gi] = fg;
         M.gparent[gi] = (int)gi;
         M.gmin[gi] = sh ? LLONG_MAX : fg;
         M.gshadow[gi] = sh ? 1 : 0;
         ftk_cp r = M.packed[i];
         r.face_id = fg;
-        r.base[3] += M.shift_t;
+        r.base[3] += (int32_t)shift_t;
         M.grec[gi] = r;
         int lp = -1, orr = -1;
         if (sh) {
-            const long long j = bsearch_ll(M.ord_fid, M.n_ord, fg);
-            if (j < 0) atomicOr(M.status, ST_PAIRING);   // must have been reported before
+            const long long j = bsearch_ll(M.ord_fid[pp], n_ord, fg);
+            if (j < 0) atomicOr(&M.S->status, ST_PAIRING);   // must have been reported before
             else {
-                lp = M.ord_gi[j];
-                orr = uf_find(M.gparent, lp, M.status);
+                lp = M.ord_gi[pp][j];
+                orr = uf_find(M.gparent, lp, &M.S->status);
             }
         }
         M.link_prev[i] = lp;
@@ -1578,64 +1589,166 @@ __global__ void __launch_bounds__(NT) k_stream_place(StreamMerge M) {
 }
 
 __global__ void __launch_bounds__(NT) k_stream_unite(StreamMerge M) {
+    if (M.ctr->status & RUN_BAD) return;
     const long long P = M.ctr->punctures;
+    const long long n_base = M.S->n;
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
-        const long long gi = M.n_base + i;
+        const long long gi = n_base + i;
         // the run's component: its root is the slot of the run label
         const long long r = bsearch_ll(M.face, P, M.label[i]);
-        if (r < 0) { atomicOr(M.status, ST_PAIRING); continue; }
-        if (r != i) uf_unite(M.gparent, (int)gi, (int)(M.n_base + r), M.status);
-        if (M.link_prev[i] >= 0) uf_unite(M.gparent, (int)gi, M.link_prev[i], M.status);
+        if (r < 0) { atomicOr(&M.S->status, ST_PAIRING); continue; }
+        if (r != i) uf_unite(M.gparent, (int)gi, (int)(n_base + r), &M.S->status);
+        if (M.link_prev[i] >= 0) uf_unite(M.gparent, (int)gi, M.link_prev[i], &M.S->status);
     }
 }
 
 __global__ void __launch_bounds__(NT) k_stream_minima(StreamMerge M) {
+    if (M.ctr->status & RUN_BAD) return;
     const long long P = M.ctr->punctures;
+    const long long n_base = M.S->n;
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
-        const long long gi = M.n_base + i;
-        const int root = uf_find(M.gparent, (int)gi, M.status);
+        const long long gi = n_base + i;
+        const int root = uf_find(M.gparent, (int)gi, &M.S->status);
         if (M.link_prev[i] >= 0) atomicMin(&M.gmin[root], M.gmin[M.old_root[i]]);
         else atomicMin(&M.gmin[root], M.gfid[gi]);
     }
 }
 
-// ordered compaction of the delta (non-shadow) records with their
-// provisional labels, and of the last-slice ordinal faces (one CTA)
-__global__ void __launch_bounds__(NT) k_stream_delta(StreamMerge M) {
-    __shared__ long long red[NT / 32 + 1];
-    const long long P = M.ctr->punctures;
-    long long run_d = 0, run_o = 0;
-    for (long long b0 = 0; b0 < P; b0 += NT) {
-        const long long i = b0 + threadIdx.x;
-        int keep = 0, last = 0;
-        long long gi = 0;
-        if (i < P) {
-            gi = M.n_base + i;
-            keep = M.gshadow[gi] ? 0 : 1;
-            last = M.first ? 1 : (M.face[i] / M.T >= M.slice_verts ? 1 : 0);
-        }
-        long long td, to;
-        const long long pd = run_d + block_excl_scan<long long>(keep, red, td);
-        const long long po = run_o + block_excl_scan<long long>(last, red, to);
-        if (keep) {
-            ftk_cp r = M.grec[gi];
-            r.label = M.gmin[uf_find(M.gparent, (int)gi, M.status)];
-            M.delta[pd] = r;
-        }
-        if (last) {
-            M.ord_fid_next[po] = M.gfid[gi];
-            M.ord_gi_next[po] = (int)gi;
-        }
-        run_d += td;
-        run_o += to;
-    }
-    if (threadIdx.x == 0) {
-        *M.delta_count = run_d;
-        *M.ord_count_next = run_o;
+// Ordered compaction of the delta (non-shadow) records with their
+// provisional labels, and of the last-slice ordinal faces, in three passes
+// over blocks of DELTA_BLOCK punctures: per-block counts, a scan of the block
+// counts, per-block writes.  Then the report to the host and the advance of
+// the stream's scalars.
+__device__ __forceinline__ void delta_flags(const StreamMerge &M, long long k, long long n_base, long long i,
+                                            long long P, int &keep, int &last) {
+    keep = 0;
+    last = 0;
+    if (i < P) {
+        keep = M.gshadow[n_base + i] ? 0 : 1;
+        last = k == 0 ? 1 : (M.face[i] / M.T >= M.slice_verts ? 1 : 0);
     }
 }
 
-// final labels of every non-shadow slot, compacted in slot order (one CTA)
+__global__ void __launch_bounds__(NT) k_delta_count(StreamMerge M) {
+    __shared__ long long red[NT / 32 + 1];
+    if (M.ctr->status & RUN_BAD) return;
+    const long long P = M.ctr->punctures;
+    const long long k = M.S->k, n_base = M.S->n;
+    const long long nb = (P + DELTA_BLOCK - 1) / DELTA_BLOCK;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        long long ck = 0, cl = 0;
+        for (int o = threadIdx.x; o < DELTA_BLOCK; o += NT) {
+            int keep, last;
+            delta_flags(M, k, n_base, b * DELTA_BLOCK + o, P, keep, last);
+            ck += keep;
+            cl += last;
+        }
+        long long tk, tl;
+        block_excl_scan<long long>(ck, red, tk);
+        block_excl_scan<long long>(cl, red, tl);
+        if (threadIdx.x == 0) {
+            M.blk[b] = tk;
+            M.blk[nb + b] = tl;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_delta_scan(StreamMerge M) {
+    __shared__ long long red[NT / 32 + 1];
+    if (M.ctr->status & RUN_BAD) return;
+    const long long P = M.ctr->punctures;
+    const long long nb = (P + DELTA_BLOCK - 1) / DELTA_BLOCK;
+    long long run_k = 0, run_l = 0;
+    for (long long b0 = 0; b0 < nb; b0 += NT) {
+        const long long b = b0 + threadIdx.x;
+        const long long ck = b < nb ? M.blk[b] : 0, cl = b < nb ? M.blk[nb + b] : 0;
+        long long tk, tl;
+        const long long ek = block_excl_scan<long long>(ck, red, tk);
+        const long long el = block_excl_scan<long long>(cl, red, tl);
+        if (b < nb) {
+            M.blk[2 * nb + b] = run_k + ek;
+            M.blk[3 * nb + b] = run_l + el;
+        }
+        run_k += tk;
+        run_l += tl;
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_delta_write(StreamMerge M) {
+    __shared__ long long red[NT / 32 + 1];
+    if (M.ctr->status & RUN_BAD) return;
+    const long long P = M.ctr->punctures;
+    const long long k = M.S->k, n_base = M.S->n;
+    const int cp = (int)(k & 1);
+    const long long nb = (P + DELTA_BLOCK - 1) / DELTA_BLOCK;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        long long run_d = M.blk[2 * nb + b], run_o = M.blk[3 * nb + b];
+        for (int o0 = 0; o0 < DELTA_BLOCK; o0 += NT) {
+            const long long i = b * DELTA_BLOCK + o0 + threadIdx.x;
+            int keep, last;
+            delta_flags(M, k, n_base, i, P, keep, last);
+            long long td, to;
+            const long long pd = run_d + block_excl_scan<long long>(keep, red, td);
+            const long long po = run_o + block_excl_scan<long long>(last, red, to);
+            if (keep) {
+                const long long gi = n_base + i;
+                ftk_cp r = M.grec[gi];
+                r.label = M.gmin[uf_find(M.gparent, (int)gi, &M.S->status)];
+                M.delta[pd] = r;
+            }
+            if (last) {
+                M.ord_fid[cp][po] = M.gfid[n_base + i];
+                M.ord_gi[cp][po] = (int)(n_base + i);
+            }
+            run_d += td;
+            run_o += to;
+        }
+    }
+}
+
+// one thread: the report to the host and the advance of the scalars (after
+// every kernel of the push has read them)
+__global__ void k_stream_advance(StreamMerge M) {
+    const unsigned run_status = M.ctr->status;
+    const long long P = M.ctr->punctures;
+    M.view->run_status = run_status;
+    M.view->punctures = P;
+    if (run_status & RUN_BAD) {
+        M.view->status = 0;
+        M.view->delta = 0;
+        __threadfence_system();
+        return;
+    }
+    const long long k = M.S->k;
+    const long long nb = (P + DELTA_BLOCK - 1) / DELTA_BLOCK;
+    const long long nd = nb ? M.blk[2 * nb + nb - 1] + M.blk[nb - 1] : 0;
+    const long long no = nb ? M.blk[3 * nb + nb - 1] + M.blk[nb + nb - 1] : 0;
+    M.view->status = M.S->status;
+    M.view->delta = nd;
+    M.S->n_ord[k & 1] = no;
+    M.S->n += P;
+    M.S->k = k + 1;
+    M.S->status = 0;
+    __threadfence_system();
+}
+
+__global__ void __launch_bounds__(NT) k_stream_copy(const StreamSrc *src, float *dst, long long n) {
+    const float *p = src->ptr;
+    const long long stride = (long long)gridDim.x * NT;
+    // the vector path only when both ends are 16-byte aligned (the second
+    // slice of a two-slice buffer is not, unless the slice size is a
+    // multiple of 4 floats)
+    if (((((uintptr_t)p) | ((uintptr_t)dst)) & 15u) == 0) {
+        const long long n4 = n >> 2;
+        const float4 *p4 = reinterpret_cast<const float4 *>(p);
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n4; i += stride) d4[i] = p4[i];
+        for (long long i = (n4 << 2) + blockIdx.x * (long long)NT + threadIdx.x; i < n; i += stride) dst[i] = p[i];
+    } else {
+        for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += stride) dst[i] = p[i];
+    }
+}
+
 __global__ void __launch_bounds__(NT) k_stream_final(long long n, const int *gshadow, int *gparent, const long long *gmin,
                                                      const ftk_cp *grec, ftk_cp *out, long long *count,
                                                      unsigned *status) {
@@ -1661,7 +1774,17 @@ cudaError_t launch_stream_merge(const StreamMerge &M, cudaStream_t s) {
     k_stream_place<<<sg, NT, 0, s>>>(M);
     k_stream_unite<<<sg, NT, 0, s>>>(M);
     k_stream_minima<<<sg, NT, 0, s>>>(M);
-    k_stream_delta<<<1, NT, 0, s>>>(M);
+    k_delta_count<<<sg, NT, 0, s>>>(M);
+    k_delta_scan<<<1, NT, 0, s>>>(M);
+    k_delta_write<<<sg, NT, 0, s>>>(M);
+    k_stream_advance<<<1, 1, 0, s>>>(M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_copy(const StreamSrc *src, float *dst, long long n, cudaStream_t s) {
+    const long long want = (n / 4 + NT - 1) / NT;
+    const int grid = (int)(want < sparse_grid() ? (want > 0 ? want : 1) : sparse_grid());
+    k_stream_copy<<<grid, NT, 0, s>>>(src, dst, n);
     return cudaGetLastError();
 }
 

@@ -139,39 +139,56 @@ cudaError_t launch_detect3(int variant, const Field &F, const Blocking &B, const
 cudaError_t launch_pipeline(int ndim, int variant, const Field &F, const Blocking &B, const Workspace &W,
                             cudaStream_t s, cudaEvent_t *ev /* 6 events or null */);
 
+// Device-resident scalars of an in-situ stream, advanced by the merge
+// kernels themselves so that one captured push can be replayed unchanged.
+struct StreamDev {
+    long long n;          // global union-find slots in use
+    long long k;          // pushes merged
+    long long n_ord[2];   // last-slice ordinal faces of push k, stored at parity k & 1
+    unsigned status;      // merge status bits of the current push
+    unsigned pad;
+};
+// Written by the merge kernels into pinned, mapped host memory.
+struct StreamView {
+    unsigned run_status;  // status bits of the push's pipeline run
+    unsigned status;      // merge status bits
+    long long punctures;  // P of the run
+    long long delta;      // delta records written
+};
+// Holder of the next slice's address (pinned, mapped host memory).
+struct StreamSrc {
+    const float *ptr;
+};
+
 struct StreamMerge {
     // run (plan workspace, sorted by local face id)
     const long long *face;      // [P] local face ids
     const long long *label;     // [P] local labels (smallest local face id of the run's component)
     const ftk_cp *packed;       // [P] records of the run
-    const RunCounters *ctr;     // run counters (P)
-    long long shift_g;          // global vertex id of the run's first vertex
-    int shift_t;                // global slice index of the run's first slice
-    int first;                  // 1 for the stream's first push (no shadows)
+    const RunCounters *ctr;     // run counters (P, status)
     long long slice_verts;      // vertices per slice
     int T;                      // face types
     int tbit;                   // time bit of a chain
+    StreamDev *S;
     // stream state
-    long long n_base;           // global slots in use before this push
     long long *gfid;            // [acap] global face id per slot
     int *gparent;               // [acap]
     long long *gmin;            // [acap] component minimum (valid at roots)
     int *gshadow;               // [acap] 1 if the slot repeats an earlier slot
     ftk_cp *grec;               // [acap] global records
-    const long long *ord_fid;   // [n_ord] previous push's last-slice ordinal faces (global ids, sorted)
-    const int *ord_gi;          // [n_ord] their slots
-    int n_ord;
+    long long *ord_fid[2];      // last-slice ordinal faces of a push (global ids, sorted), by parity
+    int *ord_gi[2];             // their slots
     int *link_prev;             // [P] earlier slot of a shadow, -1 otherwise
     int *old_root;              // [P] root of that earlier slot before this push's unions
-    ftk_cp *delta;              // [P] compacted delta records (out)
-    long long *delta_count;     // (out)
-    long long *ord_fid_next;    // [P] this push's last-slice ordinal faces (out)
-    int *ord_gi_next;           // [P]
-    long long *ord_count_next;  // (out)
-    unsigned *status;
+    long long *blk;             // [4 * (P / DELTA_BLOCK + 1)] per-block counts and offsets
+    ftk_cp *delta;              // [P] delta records (mapped host memory)
+    StreamView *view;           // (mapped host memory)
 };
+constexpr int DELTA_BLOCK = 1024;     // punctures per block of the delta compaction
 
 cudaError_t launch_stream_merge(const StreamMerge &M, cudaStream_t s);
+// copies n floats from the address in *src (device or mapped host memory) to dst
+cudaError_t launch_stream_copy(const StreamSrc *src, float *dst, long long n, cudaStream_t s);
 cudaError_t launch_stream_final(long long n, const int *gshadow, int *gparent, const long long *gmin,
                                 const ftk_cp *grec, ftk_cp *out, long long *count, unsigned *status,
                                 cudaStream_t s);

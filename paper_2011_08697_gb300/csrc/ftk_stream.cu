@@ -10,9 +10,17 @@
 // provisional labels (smallest face id connected so far); closing the stream
 // returns every puncture with its final label, equal to the whole-field
 // result.
+//
+// A steady-state push (k >= 2) of a device slice is one replay of a captured
+// CUDA graph and one synchronisation: the slice's address is read by the copy
+// kernel from mapped host memory, the stream's scalars live on the device,
+// and the delta records and counts land directly in pinned, mapped host
+// memory.  Host slices take the same kernels launched directly, after an
+// ordinary host-to-device copy.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -41,34 +49,40 @@ struct ftk_stream {
     float *d2 = nullptr;          // two slices, [previous | current]
     long long slice_verts = 0;
     int T = 12, tbit = 4;
-    int k = 0;                    // pushes done
+    long long k = 0;              // pushes done (host copy)
+    long long n = 0;              // global slots in use (host copy)
+    bool failed = false;          // a push failed: the stream accepts no more
     cudaStream_t cs = nullptr;
+    cudaEvent_t done = nullptr;   // end of a push (blocking sync)
+    StreamDev *dS = nullptr;      // device-resident scalars
+    StreamView *hV = nullptr;     // mapped host memory: host and device addresses
+    StreamView *dV = nullptr;
+    StreamSrc *hSrc = nullptr, *dSrc = nullptr;
+    ftk_cp *h_delta = nullptr, *d_delta = nullptr;   // mapped delta records
+    long long dcap = 0;
     // global union-find over all punctures so far
-    long long acap = 0, n = 0;
+    long long acap = 0;
     long long *gfid = nullptr;
     int *gparent = nullptr;
     long long *gmin = nullptr;
     int *gshadow = nullptr;
     ftk_cp *grec = nullptr;
-    // last-slice ordinal faces of the previous push (double-buffered)
     long long *ord_fid[2] = {nullptr, nullptr};
     int *ord_gi[2] = {nullptr, nullptr};
-    long long ocap[2] = {0, 0};
-    int n_ord = 0, cur = 0;
-    // per-push scratch
+    long long ocap = 0;
     long long lcap = 0;
     int *link_prev = nullptr, *old_root = nullptr;
-    ftk_cp *delta = nullptr;
-    long long *d_small = nullptr;     // delta count, ordinal count
-    unsigned *d_status = nullptr;
-    long long *h_small = nullptr;     // pinned
-    unsigned *h_status = nullptr;     // pinned
+    long long *blk = nullptr;     // per-block counts of the delta compaction
+    long long bcap = 0;
+    // one captured push (k >= 2) replayed for every later push
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
 
 template <typename T>
-ftk_status grow(T **ptr, long long &cap, long long need, long long keep, cudaStream_t s) {
+ftk_status grow(T **ptr, long long cap, long long need, long long keep, cudaStream_t s, long long *newcap) {
+    *newcap = cap;
     if (need <= cap) return FTK_OK;
     long long nc = std::max<long long>(need + need / 2, 1 << 12);
     T *np = nullptr;
@@ -83,61 +97,163 @@ ftk_status grow(T **ptr, long long &cap, long long need, long long keep, cudaStr
     }
     cudaFree(*ptr);
     *ptr = np;
-    cap = nc;
+    *newcap = nc;
     return FTK_OK;
 }
 
-ftk_status ensure_global(ftk_stream *st, long long need) {
-    if (need <= st->acap) return FTK_OK;
-    long long c0 = st->acap, c1 = st->acap, c2 = st->acap, c3 = st->acap, c4 = st->acap;
-    ftk_status s;
-    if ((s = grow(&st->gfid, c0, need, st->n, st->cs)) != FTK_OK) return s;
-    if ((s = grow(&st->gparent, c1, need, st->n, st->cs)) != FTK_OK) return s;
-    if ((s = grow(&st->gmin, c2, need, st->n, st->cs)) != FTK_OK) return s;
-    if ((s = grow(&st->gshadow, c3, need, st->n, st->cs)) != FTK_OK) return s;
-    if ((s = grow(&st->grec, c4, need, st->n, st->cs)) != FTK_OK) return s;
+void drop_graph(ftk_stream *st) {
+    if (st->exec) cudaGraphExecDestroy(st->exec);
+    st->exec = nullptr;
+}
+
+void account(ftk_stream *st, size_t add) {
+    st->footprint += add;
     if (st->server) {
         std::lock_guard<std::mutex> lock(st->server->mu);
-        const size_t add = (size_t)(c0 - st->acap) * (8 + 4 + 8 + 4 + sizeof(ftk_cp));
         st->server->used += add;
-        st->footprint += add;
     }
-    st->acap = c0;
+}
+
+// every per-push array sized for a run of up to cap punctures on top of the
+// n slots in use; a reallocation invalidates the captured push
+ftk_status ensure_all(ftk_stream *st, long long cap) {
+    ftk_status s;
+    const long long need = st->n + cap;
+    if (need > st->acap) {
+        long long c0, c1, c2, c3, c4;
+        if ((s = grow(&st->gfid, st->acap, need, st->n, st->cs, &c0)) != FTK_OK ||
+            (s = grow(&st->gparent, st->acap, need, st->n, st->cs, &c1)) != FTK_OK ||
+            (s = grow(&st->gmin, st->acap, need, st->n, st->cs, &c2)) != FTK_OK ||
+            (s = grow(&st->gshadow, st->acap, need, st->n, st->cs, &c3)) != FTK_OK ||
+            (s = grow(&st->grec, st->acap, need, st->n, st->cs, &c4)) != FTK_OK)
+            return s;
+        account(st, (size_t)(c0 - st->acap) * (8 + 4 + 8 + 4 + sizeof(ftk_cp)));
+        st->acap = c0;
+        drop_graph(st);
+    }
+    if (cap > st->lcap) {
+        long long a, b;
+        if ((s = grow(&st->link_prev, st->lcap, cap, 0, st->cs, &a)) != FTK_OK ||
+            (s = grow(&st->old_root, st->lcap, cap, 0, st->cs, &b)) != FTK_OK)
+            return s;
+        account(st, (size_t)(a - st->lcap) * 8);
+        st->lcap = a;
+        drop_graph(st);
+    }
+    const long long nblk = 4 * (cap / DELTA_BLOCK + 1);
+    if (nblk > st->bcap) {
+        long long a;
+        if ((s = grow(&st->blk, st->bcap, nblk, 0, st->cs, &a)) != FTK_OK) return s;
+        account(st, (size_t)(a - st->bcap) * 8);
+        st->bcap = a;
+        drop_graph(st);
+    }
+    if (cap > st->ocap) {
+        // the buffer of the last push's parity keeps its ordinal faces
+        const int keep = (int)((st->k - 1) & 1);
+        long long nk = 0;
+        if (st->k > 0) cudaMemcpy(&nk, &st->dS->n_ord[keep], sizeof(long long), cudaMemcpyDeviceToHost);
+        long long a = 0, b = 0;
+        for (int q = 0; q < 2; ++q) {
+            if ((s = grow(&st->ord_fid[q], st->ocap, cap, q == keep ? nk : 0, st->cs, &a)) != FTK_OK ||
+                (s = grow(&st->ord_gi[q], st->ocap, cap, q == keep ? nk : 0, st->cs, &b)) != FTK_OK)
+                return s;
+        }
+        account(st, (size_t)(a - st->ocap) * 24);
+        st->ocap = a;
+        drop_graph(st);
+    }
+    if (cap > st->dcap) {
+        const long long nc = std::max<long long>(cap + cap / 2, 1 << 12);
+        ftk_cp *h = nullptr;
+        if (cudaHostAlloc(&h, sizeof(ftk_cp) * nc, cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FTK_ERR_NOMEM, "pinned delta buffer allocation failed");
+        }
+        if (st->h_delta) cudaFreeHost(st->h_delta);
+        st->h_delta = h;
+        cudaHostGetDevicePointer((void **)&st->d_delta, h, 0);
+        st->dcap = nc;
+        drop_graph(st);
+    }
     return FTK_OK;
 }
 
-ftk_status ensure_scratch(ftk_stream *st, long long P) {
-    if (P <= st->lcap && P <= st->ocap[0] && P <= st->ocap[1]) return FTK_OK;
-    long long need = std::max<long long>(P, 1);
-    long long a = st->lcap, b = st->lcap, c = st->lcap;
-    ftk_status s;
-    if ((s = grow(&st->link_prev, a, need, 0, st->cs)) != FTK_OK) return s;
-    if ((s = grow(&st->old_root, b, need, 0, st->cs)) != FTK_OK) return s;
-    if ((s = grow(&st->delta, c, need, 0, st->cs)) != FTK_OK) return s;
-    st->lcap = a;
-    // ordinal buffers: the current one keeps its contents
-    for (int q = 0; q < 2; ++q) {
-        long long oc = st->ocap[q];
-        if ((s = grow(&st->ord_fid[q], oc, need, q == st->cur ? st->n_ord : 0, st->cs)) != FTK_OK) return s;
-        long long oc2 = st->ocap[q];
-        if ((s = grow(&st->ord_gi[q], oc2, need, q == st->cur ? st->n_ord : 0, st->cs)) != FTK_OK) return s;
-        st->ocap[q] = oc;
-    }
+StreamMerge merge_args(ftk_stream *st, ftk_plan *pl) {
+    StreamMerge M;
+    std::memset(&M, 0, sizeof(M));
+    M.face = pl->W.face;
+    M.label = pl->W.label;
+    M.packed = pl->W.packed;
+    M.ctr = pl->W.ctr;
+    M.slice_verts = st->slice_verts;
+    M.T = st->T;
+    M.tbit = st->tbit;
+    M.S = st->dS;
+    M.gfid = st->gfid; M.gparent = st->gparent; M.gmin = st->gmin; M.gshadow = st->gshadow; M.grec = st->grec;
+    for (int q = 0; q < 2; ++q) { M.ord_fid[q] = st->ord_fid[q]; M.ord_gi[q] = st->ord_gi[q]; }
+    M.link_prev = st->link_prev;
+    M.old_root = st->old_root;
+    M.blk = st->blk;
+    M.delta = st->d_delta;
+    M.view = st->dV;
+    return M;
+}
+
+// one push's device work: bring in the slice (host_slice: a host pointer to
+// copy from; otherwise the device address in *dSrc), run the pipeline, merge
+ftk_status enqueue_push(ftk_stream *st, ftk_plan *pl, long long k, const float *host_slice) {
+    const size_t sbytes = sizeof(float) * (size_t)st->slice_verts;
+    float *dst = k == 0 ? st->d2 : st->d2 + st->slice_verts;
+    cudaError_t e;
+    if (k >= 2 && (e = cudaMemcpyAsync(st->d2, st->d2 + st->slice_verts, sbytes, cudaMemcpyDeviceToDevice, st->cs)) !=
+                      cudaSuccess)
+        return cuda_fail(e, "slice shift");
+    if (host_slice) e = cudaMemcpyAsync(dst, host_slice, sbytes, cudaMemcpyHostToDevice, st->cs);
+    else e = launch_stream_copy(st->dSrc, dst, st->slice_verts, st->cs);
+    if (e != cudaSuccess) return cuda_fail(e, "slice copy");
+    ftk_status s = plan_launch(pl, st->d2, st->cs);
+    if (s != FTK_OK) return s;
+    if ((e = launch_stream_merge(merge_args(st, pl), st->cs)) != cudaSuccess) return cuda_fail(e, "stream merge launch");
     return FTK_OK;
+}
+
+// captures the steady-state push (k >= 2) into a graph
+void capture_push(ftk_stream *st) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st->cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const ftk_status s = enqueue_push(st, st->plan2, 2, nullptr);
+    const cudaError_t e = cudaStreamEndCapture(st->cs, &g);
+    if (s != FTK_OK || e != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return;
+    }
+    if (cudaGraphInstantiate(&st->exec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        st->exec = nullptr;
+    }
+    cudaGraphDestroy(g);
 }
 
 void release(ftk_stream *st) {
     if (!st) return;
     if (st->cs) cudaStreamSynchronize(st->cs);
+    drop_graph(st);
     if (st->plan1) ftk_plan_destroy(st->plan1);
     if (st->plan2) ftk_plan_destroy(st->plan2);
     cudaFree(st->d2);
+    cudaFree(st->dS);
+    if (st->hV) cudaFreeHost(st->hV);
+    if (st->hSrc) cudaFreeHost(st->hSrc);
+    if (st->h_delta) cudaFreeHost(st->h_delta);
     cudaFree(st->gfid); cudaFree(st->gparent); cudaFree(st->gmin); cudaFree(st->gshadow); cudaFree(st->grec);
     for (int q = 0; q < 2; ++q) { cudaFree(st->ord_fid[q]); cudaFree(st->ord_gi[q]); }
-    cudaFree(st->link_prev); cudaFree(st->old_root); cudaFree(st->delta);
-    cudaFree(st->d_small); cudaFree(st->d_status);
-    if (st->h_small) cudaFreeHost(st->h_small);
-    if (st->h_status) cudaFreeHost(st->h_status);
+    cudaFree(st->link_prev); cudaFree(st->old_root); cudaFree(st->blk);
+    if (st->done) cudaEventDestroy(st->done);
     if (st->cs) cudaStreamDestroy(st->cs);
     if (st->server) {
         std::lock_guard<std::mutex> lock(st->server->mu);
@@ -177,10 +293,13 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
     }
     if (cudaStreamCreateWithFlags(&st->cs, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&st->d2, sizeof(float) * 2 * st->slice_verts) != cudaSuccess ||
-        cudaMalloc(&st->d_small, sizeof(long long) * 2) != cudaSuccess ||
-        cudaMalloc(&st->d_status, sizeof(unsigned)) != cudaSuccess ||
-        cudaMallocHost(&st->h_small, sizeof(long long) * 2) != cudaSuccess ||
-        cudaMallocHost(&st->h_status, sizeof(unsigned)) != cudaSuccess) {
+        cudaMalloc(&st->dS, sizeof(StreamDev)) != cudaSuccess ||
+        cudaMemset(st->dS, 0, sizeof(StreamDev)) != cudaSuccess ||
+        cudaHostAlloc(&st->hV, sizeof(StreamView), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostAlloc(&st->hSrc, sizeof(StreamSrc), cudaHostAllocMapped) != cudaSuccess ||
+        cudaEventCreateWithFlags(&st->done, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&st->dV, st->hV, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&st->dSrc, st->hSrc, 0) != cudaSuccess) {
         cudaGetLastError();
         release(st);
         return fail(FTK_ERR_NOMEM, "stream allocation failed");
@@ -201,6 +320,24 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
     }
     *out = st;
     return FTK_OK;
+}
+
+// the merge kernels' report, written by the device into mapped host memory
+StreamView read_view(const ftk_stream *st) {
+    const volatile StreamView *p = st->hV;
+    StreamView v;
+    v.run_status = p->run_status;
+    v.status = p->status;
+    v.punctures = p->punctures;
+    v.delta = p->delta;
+    return v;
+}
+
+// marks the stream failed; msg = nullptr keeps the message already set
+ftk_status stream_error(ftk_stream *st, ftk_status s, const char *msg) {
+    st->failed = true;
+    if (!msg) return s;
+    return fail(s, msg);
 }
 
 }  // namespace
@@ -247,70 +384,56 @@ ftk_status ftk_stream_open_in(ftk_server *srv, int ndim, int64_t nx, int64_t ny,
 ftk_status ftk_stream_push(ftk_stream *st, const float *slice, ftk_result **delta) {
     if (delta) *delta = nullptr;
     if (!st || !slice || !delta) return fail(FTK_ERR_ARG, "stream, slice and delta must be non-NULL");
-    const size_t sbytes = sizeof(float) * (size_t)st->slice_verts;
-    const cudaMemcpyKind kind = is_device_pointer(slice) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (st->failed) return fail(FTK_ERR_STATE, "an earlier push of this stream failed");
+    const long long k = st->k;
+    ftk_plan *pl = k == 0 ? st->plan1 : st->plan2;
+    // device slices: the copy kernel reads the address from mapped memory
+    // (the captured push is replayed); host slices: an ordinary copy
+    const bool on_dev = is_device_pointer(slice);
+    if (on_dev) {
+        st->hSrc->ptr = slice;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+    }
+    ftk_status s = ensure_all(st, pl->W.cap);
+    if (s != FTK_OK) return stream_error(st, s, nullptr);
     cudaError_t e;
-    ftk_plan *pl = st->k == 0 ? st->plan1 : st->plan2;
-    float *cur = st->k == 0 ? st->d2 : st->d2 + st->slice_verts;
-    if (st->k >= 2) {
-        e = cudaMemcpyAsync(st->d2, st->d2 + st->slice_verts, sbytes, cudaMemcpyDeviceToDevice, st->cs);
-        if (e != cudaSuccess) return cuda_fail(e, "slice shift");
+    if (on_dev && k >= 2 && !st->exec) capture_push(st);
+    if (on_dev && k >= 2 && st->exec) {
+        if ((e = cudaGraphLaunch(st->exec, st->cs)) != cudaSuccess) return stream_error(st, FTK_ERR_CUDA, cudaGetErrorString(e));
+    } else if ((s = enqueue_push(st, pl, k, on_dev ? nullptr : slice)) != FTK_OK) {
+        return stream_error(st, s, nullptr);
     }
-    e = cudaMemcpyAsync(cur, slice, sbytes, kind, st->cs);
-    if (e != cudaSuccess) return cuda_fail(e, "slice copy");
-    ftk_status s = plan_launch(pl, st->d2, st->cs);
-    if (s != FTK_OK) return s;
-    int64_t P = 0;
-    if ((s = ftk_plan_count(pl, &P)) != FTK_OK) return s;
-    if ((s = ensure_global(st, st->n + P)) != FTK_OK) return s;
-    if ((s = ensure_scratch(st, P)) != FTK_OK) return s;
-    StreamMerge M;
-    std::memset(&M, 0, sizeof(M));
-    M.face = pl->W.face;
-    M.label = pl->W.label;
-    M.packed = pl->W.packed;
-    M.ctr = pl->W.ctr;
-    M.shift_t = st->k == 0 ? 0 : st->k - 1;
-    M.shift_g = (long long)M.shift_t * st->slice_verts;
-    M.first = st->k == 0 ? 1 : 0;
-    M.slice_verts = st->slice_verts;
-    M.T = st->T;
-    M.tbit = st->tbit;
-    M.n_base = st->n;
-    M.gfid = st->gfid; M.gparent = st->gparent; M.gmin = st->gmin; M.gshadow = st->gshadow; M.grec = st->grec;
-    M.ord_fid = st->ord_fid[st->cur];
-    M.ord_gi = st->ord_gi[st->cur];
-    M.n_ord = st->n_ord;
-    M.link_prev = st->link_prev;
-    M.old_root = st->old_root;
-    M.delta = st->delta;
-    M.delta_count = st->d_small;
-    M.ord_fid_next = st->ord_fid[1 - st->cur];
-    M.ord_gi_next = st->ord_gi[1 - st->cur];
-    M.ord_count_next = st->d_small + 1;
-    M.status = st->d_status;
-    if ((e = cudaMemsetAsync(st->d_status, 0, sizeof(unsigned), st->cs)) != cudaSuccess) return cuda_fail(e, "status reset");
-    if ((e = launch_stream_merge(M, st->cs)) != cudaSuccess) return cuda_fail(e, "stream merge launch");
-    if ((e = cudaMemcpyAsync(st->h_small, st->d_small, sizeof(long long) * 2, cudaMemcpyDeviceToHost, st->cs)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(st->h_status, st->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st->cs)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st->cs)) != cudaSuccess)
-        return cuda_fail(e, "stream merge");
-    if (*st->h_status & ST_TIMEOUT) return fail(FTK_ERR_TIMEOUT, "a bounded device loop gave up");
-    if (*st->h_status & ST_PAIRING) return fail(FTK_ERR_INVARIANT, "a repeated face was not found in the previous push");
-    const long long D = st->h_small[0];
+    // a blocking-sync event: the waiting thread sleeps instead of spinning
+    if ((e = cudaEventRecord(st->done, st->cs)) != cudaSuccess || (e = cudaEventSynchronize(st->done)) != cudaSuccess)
+        return stream_error(st, FTK_ERR_CUDA, cudaGetErrorString(e));
+    StreamView v = read_view(st);
+    if (v.run_status & (ST_OVERFLOW | ST_SOVERFLOW | ST_WIDE)) {
+        // not merged: repair the run (larger capacity or exact rounding),
+        // then merge it
+        int64_t P = 0;
+        if ((s = ftk_plan_count(pl, &P)) != FTK_OK) return stream_error(st, s, nullptr);
+        if ((s = ensure_all(st, pl->W.cap)) != FTK_OK) return stream_error(st, s, nullptr);
+        drop_graph(st);   // the run's capacity changed
+        if ((e = launch_stream_merge(merge_args(st, pl), st->cs)) != cudaSuccess ||
+            (e = cudaEventRecord(st->done, st->cs)) != cudaSuccess || (e = cudaEventSynchronize(st->done)) != cudaSuccess)
+            return stream_error(st, FTK_ERR_CUDA, cudaGetErrorString(e));
+        v = read_view(st);
+    }
+    if (v.run_status & ST_RANGE)
+        return stream_error(st, FTK_ERR_RANGE, "a sample is non-finite or |f * 2^quant_shift| exceeds 2^28");
+    if ((v.run_status | v.status) & ST_TIMEOUT) return stream_error(st, FTK_ERR_TIMEOUT, "a bounded device loop gave up");
+    if ((v.run_status | v.status) & ST_PAIRING)
+        return stream_error(st, FTK_ERR_INVARIANT, "the pairing invariant or a repeated face failed");
+    const long long D = v.delta;
     ftk_result *r = new (std::nothrow) ftk_result;
-    if (!r) return fail(FTK_ERR_NOMEM, "host allocation failed");
-    r->count = (size_t)D;
-    r->data = (ftk_cp *)std::malloc(std::max<size_t>(1, (size_t)D) * sizeof(ftk_cp));
-    if (!r->data) { delete r; return fail(FTK_ERR_NOMEM, "host allocation failed"); }
-    if (D > 0 && (e = cudaMemcpy(r->data, st->delta, sizeof(ftk_cp) * D, cudaMemcpyDeviceToHost)) != cudaSuccess) {
-        std::free(r->data);
+    if (r) r->data = (ftk_cp *)std::malloc(std::max<size_t>(1, (size_t)D) * sizeof(ftk_cp));
+    if (!r || !r->data) {
         delete r;
-        return cuda_fail(e, "delta download");
+        return stream_error(st, FTK_ERR_NOMEM, "host allocation failed");
     }
-    st->n += P;
-    st->n_ord = (int)st->h_small[1];
-    st->cur = 1 - st->cur;
+    r->count = (size_t)D;
+    if (D > 0) std::memcpy(r->data, st->h_delta, sizeof(ftk_cp) * (size_t)D);
+    st->n += v.punctures;
     st->k += 1;
     *delta = r;
     return FTK_OK;
@@ -323,14 +446,16 @@ ftk_status ftk_stream_close(ftk_stream *st, ftk_result **final) {
     if (final) {
         ftk_cp *d_out = nullptr;
         long long *d_cnt = nullptr;
+        unsigned *d_st = nullptr;
         cudaError_t e = cudaSuccess;
         if (cudaMalloc(&d_out, sizeof(ftk_cp) * std::max<long long>(1, st->n)) != cudaSuccess ||
-            cudaMalloc(&d_cnt, sizeof(long long)) != cudaSuccess) {
+            cudaMalloc(&d_cnt, sizeof(long long)) != cudaSuccess ||
+            cudaMalloc(&d_st, sizeof(unsigned)) != cudaSuccess) {
             cudaGetLastError();
             s = fail(FTK_ERR_NOMEM, "final result allocation failed");
-        } else if ((e = cudaMemsetAsync(st->d_status, 0, sizeof(unsigned), st->cs)) != cudaSuccess ||
-                   (e = launch_stream_final(st->n, st->gshadow, st->gparent, st->gmin, st->grec, d_out, d_cnt,
-                                            st->d_status, st->cs)) != cudaSuccess ||
+        } else if ((e = cudaMemsetAsync(d_st, 0, sizeof(unsigned), st->cs)) != cudaSuccess ||
+                   (e = launch_stream_final(st->n, st->gshadow, st->gparent, st->gmin, st->grec, d_out, d_cnt, d_st,
+                                            st->cs)) != cudaSuccess ||
                    (e = cudaStreamSynchronize(st->cs)) != cudaSuccess) {
             s = cuda_fail(e, "final labels");
         } else {
@@ -340,21 +465,20 @@ ftk_status ftk_stream_close(ftk_stream *st, ftk_result **final) {
             if (r) r->data = (ftk_cp *)std::malloc(std::max<size_t>(1, (size_t)cnt) * sizeof(ftk_cp));
             if (!r || !r->data) {
                 delete r;
-                cudaFree(d_out);
-                cudaFree(d_cnt);
-                release(st);
-                return fail(FTK_ERR_NOMEM, "host allocation failed");
+                s = fail(FTK_ERR_NOMEM, "host allocation failed");
+            } else {
+                r->count = (size_t)cnt;
+                if (cnt > 0) cudaMemcpy(r->data, d_out, sizeof(ftk_cp) * cnt, cudaMemcpyDeviceToHost);
+                // pushes interleave in face-id order (interval faces of slab
+                // [k-1, k] arrive one push after the ordinal faces of slice k-1)
+                std::sort(r->data, r->data + r->count,
+                          [](const ftk_cp &a, const ftk_cp &b) { return a.face_id < b.face_id; });
+                *final = r;
             }
-            r->count = (size_t)cnt;
-            if (cnt > 0) cudaMemcpy(r->data, d_out, sizeof(ftk_cp) * cnt, cudaMemcpyDeviceToHost);
-            // pushes interleave in face-id order (interval faces of slab
-            // [k-1, k] arrive one push after the ordinal faces of slice k-1)
-            std::sort(r->data, r->data + r->count,
-                      [](const ftk_cp &a, const ftk_cp &b) { return a.face_id < b.face_id; });
-            *final = r;
         }
         cudaFree(d_out);
         cudaFree(d_cnt);
+        cudaFree(d_st);
     }
     release(st);
     return s;
