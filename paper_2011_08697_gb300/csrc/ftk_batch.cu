@@ -62,18 +62,7 @@ void release(ftk_batch *b) {
 // the device pointer a field's pipeline reads: the caller's, or the plan's
 // aligned copy when the streaming kernel needs 16-byte aligned rows
 ftk_status source_of(ftk_plan *pl, const float *f, cudaStream_t s, const float **src) {
-    *src = f;
-    if (pl->variant != VAR_TILE && ((uintptr_t)f & 15u) != 0) {
-        const size_t bytes = (size_t)pl->nverts * sizeof(float);
-        if (!pl->d_input && cudaMalloc(&pl->d_input, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(FTK_ERR_NOMEM, "device input buffer allocation failed");
-        }
-        cudaError_t e = cudaMemcpyAsync(pl->d_input, f, bytes, cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(e, "aligned input copy");
-        *src = pl->d_input;
-    }
-    return FTK_OK;
+    return plan_source(pl, f, false, s, src);
 }
 
 // launch every field on the worker pool, joined back into `origin`

@@ -146,26 +146,36 @@ void choose_time_chunks(const Field &F, Blocking &B, long long spatial, long lon
     B.ntc = (F.nt + B.tc - 1) / B.tc;
 }
 
+// row pitch of the field the kernels read: the width rounded up to 4 floats
+// when a streaming kernel takes the shape, else the width itself (the tiled
+// kernel reads any width in place)
+int stream_pitch(int ndim, int nx) {
+    const int p = (nx + 3) & ~3;
+    return p <= (ndim == 2 ? STREAM2_MAX_NX : STREAM3_MAX_NX) ? p : nx;
+}
+
 ftk_status choose_blocking(int ndim, const Field &F, Blocking &B, int &variant) {
     static const int cand2[] = {16, 8, 4, 2, 1};
     static const int cand3[][2] = {{8, 4}, {8, 2}, {4, 4}, {4, 2}, {2, 2}, {2, 1}, {1, 1}};
     const int sms = sm_count();
-    if (ndim == 2 && F.nx % 4 == 0 && F.nx <= STREAM2_MAX_NX) {
+    // the streaming kernels read rows padded to a multiple of 4 floats
+    // (F.pitch, chosen by stream_pitch)
+    if (ndim == 2 && F.pitch % 4 == 0 && F.pitch <= STREAM2_MAX_NX) {
         variant = VAR_STREAM2;
         B.ry = STREAM2_ROWS; B.rz = 1;
         B.nyb = (F.ny + B.ry - 1) / B.ry;
         B.nzb = 1;
-        choose_time_chunks(F, B, B.nyb, (long long)sms * stream2_ctas_per_sm(F.nx));
+        choose_time_chunks(F, B, B.nyb, (long long)sms * stream2_ctas_per_sm(F.pitch));
         return FTK_OK;
     }
-    if (ndim == 3 && F.nx % 4 == 0 && F.nx <= STREAM3_MAX_NX) {
+    if (ndim == 3 && F.pitch % 4 == 0 && F.pitch <= STREAM3_MAX_NX) {
         variant = VAR_STREAM3;
         // plane chunks of (ry + 3) rows of about 10 KB or less; 8 cube planes
-        B.ry = std::max(1, std::min(15, std::min(F.ny, 10240 / (F.nx * 4) - 3)));
+        B.ry = std::max(1, std::min(15, std::min(F.ny, 10240 / (F.pitch * 4) - 3)));
         B.rz = std::min(8, F.nz);
         B.nyb = (F.ny + B.ry - 1) / B.ry;
         B.nzb = (F.nz + B.rz - 1) / B.rz;
-        choose_time_chunks(F, B, (long long)B.nyb * B.nzb, (long long)sms * stream3_ctas_per_sm(F.nx, B));
+        choose_time_chunks(F, B, (long long)B.nyb * B.nzb, (long long)sms * stream3_ctas_per_sm(F.pitch, B));
         return FTK_OK;
     }
     variant = VAR_TILE;
@@ -320,6 +330,36 @@ void apply_tuned(ftk_plan *pl) {
 
 }  // namespace
 
+// the device field the kernels read: f itself when they can read it in
+// place, else the plan's own copy (host input, a padded row pitch, or a
+// start that is not 16-byte aligned for the bulk copies), queued on s
+ftk_status ftk::plan_source(ftk_plan *pl, const float *f, bool host, cudaStream_t s, const float **src) {
+    const Field &F = pl->F;
+    const long long rows = (long long)F.nt * F.nz * F.ny;
+    const bool padded = F.pitch != F.nx;
+    const bool misaligned = pl->variant != VAR_TILE && ((uintptr_t)f & 15u) != 0;
+    *src = f;
+    if (!host && !padded && !misaligned) return FTK_OK;
+    const size_t bytes = (size_t)rows * F.pitch * sizeof(float);
+    if (!pl->d_input && cudaMalloc(&pl->d_input, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FTK_ERR_NOMEM, "device input buffer allocation failed");
+    }
+    cudaError_t e;
+    if (!padded) {
+        e = cudaMemcpyAsync(pl->d_input, f, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+    } else if (host) {
+        e = cudaMemcpy2DAsync(pl->d_input, (size_t)F.pitch * 4, f, (size_t)F.nx * 4, (size_t)F.nx * 4, (size_t)rows,
+                              cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_fill_pad(pl->d_input, F.nx, F.pitch, rows, s);
+    } else {
+        e = launch_pad_rows(f, pl->d_input, F.nx, F.pitch, rows, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "input copy");
+    *src = pl->d_input;
+    return FTK_OK;
+}
+
 ftk_status ftk::plan_launch(ftk_plan *pl, const float *f, cudaStream_t s) {
     pl->last_f = f;
     pl->last_dev = f;
@@ -431,6 +471,7 @@ ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_
     pl->ndim = ndim;
     cudaGetDevice(&pl->device);
     pl->F.nx = (int)nx; pl->F.ny = (int)ny; pl->F.nz = (int)nz; pl->F.nt = (int)nt;
+    pl->F.pitch = stream_pitch(ndim, (int)nx);
     pl->F.scale = (float)std::ldexp(1.0, pl->p.quant_shift);
     field_divisors(pl->F);
     pl->nverts = (long long)nx * ny * nz * nt;
@@ -492,20 +533,9 @@ ftk_status ftk_plan_execute(ftk_plan *pl, const float *f, void *cuda_stream) {
     if (!pl || !f) return fail(FTK_ERR_ARG, "plan and field must be non-NULL");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const bool host = !is_device_pointer(f);
-    // the streaming kernel copies rows with TMA: they must start on 16 bytes
-    const bool misaligned = pl->variant != VAR_TILE && ((uintptr_t)f & 15u) != 0;
     const float *src = f;
-    if (host || misaligned) {
-        const size_t bytes = (size_t)pl->nverts * sizeof(float);
-        if (!pl->d_input) {
-            if (cudaMalloc(&pl->d_input, bytes) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(FTK_ERR_NOMEM, "device input buffer allocation failed");
-            }
-        }
-        FTK_CUDA(cudaMemcpyAsync(pl->d_input, f, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
-        src = pl->d_input;
-    }
+    ftk_status st = ftk::plan_source(pl, f, host, s, &src);
+    if (st != FTK_OK) return st;
     pl->last_f = f;
     pl->last_dev = src;
     pl->last_host = host;

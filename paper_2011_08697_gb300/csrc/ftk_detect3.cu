@@ -115,7 +115,9 @@ __device__ __forceinline__ uint32_t qd(uint32_t a, uint32_t b) {
 template <bool EXACT>
 __global__ void __launch_bounds__(S3_THREADS, 2) k_detect3_stream(Field F, Blocking B, Workspace W) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int nx = F.nx, ny = F.ny, nz = F.nz, nt = F.nt;
+    // the sweep covers the padded row (pitch columns, the padding repeating
+    // column nx-1); survivors are the grid's (columns < nxl)
+    const int nx = F.pitch, nxl = F.nx, ny = F.ny, nz = F.nz, nt = F.nt;
     const int RY = B.ry, RZ = B.rz;
     constexpr int NS = S3_NS;
     const int XC = s3_chunks(nx);
@@ -224,8 +226,8 @@ __global__ void __launch_bounds__(S3_THREADS, 2) k_detect3_stream(Field F, Block
                 }
                 if (total == 0) continue;   // warp-uniform; the words are all zero already
                 base = __shfl_sync(ALL, base, 0);
-                compact_bits<2>(bm + (b * RZ + ci) * L.rw, L.rw, nx, inv_nx, ((long long)t * nz + z) * ny + y0, base,
-                             W.surv, W.scap);
+                compact_bits<2>(bm + (b * RZ + ci) * L.rw, L.rw, nx, nxl, inv_nx, ((long long)t * nz + z) * ny + y0,
+                                base, W.surv, W.scap);
             }
             __syncwarp();
             if (lane < RZ) scnt[b * RZ + lane] = 0;
@@ -243,6 +245,8 @@ __global__ void __launch_bounds__(S3_THREADS, 2) k_detect3_stream(Field F, Block
     const bool act = xb < nx;
     const int xa = act ? xb : 0;           // a safe address for idle lanes
     const bool xlast = act && xb + 4 >= nx;
+    // the lane's columns inside the grid (the rest is padding)
+    const uint32_t gmask = act ? (1u << max(0, min(4, nxl - xb))) - 1u : 0u;
     const int gper = (GR + NG - 1) / NG;
     const int gr0 = min(GR, grp * gper), gr1 = min(GR, gr0 + gper);
     const int cper = (RY + NG - 1) / NG;
@@ -387,7 +391,7 @@ __global__ void __launch_bounds__(S3_THREADS, 2) k_detect3_stream(Field F, Block
                     if (sl >= 1 && act) {
                         const uint32_t c4 = cmb(P, *ts);
                         const uint32_t mixed = (c4 >> 16) & ~c4 & 0xFFFu;
-                        const uint32_t sv = mixed & (mixed >> 4) & (mixed >> 8) & 0xFu;
+                        const uint32_t sv = mixed & (mixed >> 4) & (mixed >> 8) & gmask;
                         if (sv) {
                             emit(bq, ci, cr, sv);
                             nsv += __popc(sv);
@@ -419,8 +423,8 @@ __global__ void __launch_bounds__(S3_THREADS, 2) k_detect3_stream(Field F, Block
                 for (int cr = cr0; cr < cr1 && cr < ncy; ++cr) {
                     const uint32_t P = TS[((ci * RY + cr) * XC + c) * 32 + lane];
                     const uint32_t mixed = (P >> 16) & ~P & 0xFFFu;
-                    const uint32_t sv = mixed & (mixed >> 4) & (mixed >> 8) & 0xFu;
-                    if (sv && act) {
+                    const uint32_t sv = mixed & (mixed >> 4) & (mixed >> 8) & gmask;
+                    if (sv) {
                         emit(bq, ci, cr, sv);
                         nsv += __popc(sv);
                     }
@@ -459,7 +463,7 @@ cudaError_t launch_detect3(int variant, const Field &F, const Blocking &B, const
                            bool capturing) {
     const bool exact = variant == VAR_STREAM3_EXACT;
     const void *k = exact ? s3_kernel<true>() : s3_kernel<false>();
-    const size_t smem = stream3_smem_bytes(F.nx, B);
+    const size_t smem = stream3_smem_bytes(F.pitch, B);
     // the attribute only ever grows: a captured graph may replay a larger
     // launch after a smaller one was configured
     static size_t configured[2] = {0, 0};

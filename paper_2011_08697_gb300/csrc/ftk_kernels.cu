@@ -161,7 +161,7 @@ __device__ void load_tile(const Field &F, const TileGeom &g, int s, int32_t *T, 
         const int y = g.y0 - 1 + ty;
         const int z = N == 3 ? g.z0 - 1 + tz : 0;
         if (y < 0 || y >= g.ny || z < 0 || z >= g.nz) continue;
-        const long long idx = (((long long)s * g.nz + z) * g.ny + y) * g.nx + x;
+        const long long idx = (((long long)s * g.nz + z) * g.ny + y) * F.pitch + x;
         T[i] = quantise(__ldg(F.f + idx), F.scale, status);
     }
 }
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(NT) k_scan(Workspace W, int stream_mode) {
 struct Pt { int c[4]; };   // x, y, z, t (z = 0 in 2D)
 
 __device__ __forceinline__ int qload(const Field &F, int x, int y, int z, int t) {
-    const long long idx = (((long long)t * F.nz + z) * F.ny + y) * F.nx + x;
+    const long long idx = (((long long)t * F.nz + z) * F.ny + y) * F.pitch + x;
     const float v = __ldg(F.f + idx) * F.scale;
     return fabsf(v) <= RANGE_LIMIT ? __float2int_rn(v) : 0;
 }
@@ -1036,7 +1036,10 @@ __device__ __forceinline__ uint32_t survivors8(uint32_t c) {
 template <bool EXACT, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking B, Workspace W) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int nx = F.nx, ny = F.ny, nt = F.nt;
+    // the sweep covers the padded row (pitch columns; padding repeats column
+    // nx-1, so every grid vertex's gradient signs are exact and the extra
+    // corners only make cubes survive more easily); survivors are the grid's
+    const int nx = F.pitch, nxl = F.nx, ny = F.ny, nt = F.nt;
     const int NC = (int)blockDim.x - 64;
     const int CW = NC >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1123,8 +1126,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
             }
             if (total > 0) {
                 base = __shfl_sync(0xffffffffu, base, 0);
-                compact_bits<16>(bm + b * L.bmw, L.bmw, nx, 1.0f / (float)nx, (long long)t * ny + y0, base, W.surv,
-                             W.scap);
+                compact_bits<16>(bm + b * L.bmw, L.bmw, nx, nxl, 1.0f / (float)nx, (long long)t * ny + y0, base,
+                                 W.surv, W.scap);
             }
             __syncwarp();
             if (lane == 0) scnt[b] = 0;
@@ -1138,7 +1141,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     const int x0 = (int)threadIdx.x * CX;
     const bool act = x0 < nx;
     const int ncol = act ? min(CX, nx - x0) : 0;           // 8, or 4 on the last thread
-    const uint32_t vmask = ncol == 8 ? 0xFFu : ncol == 4 ? 0x0Fu : 0u;
+    const int ngrid = act ? max(0, min(CX, nxl - x0)) : 0;       // columns inside the grid
+    const uint32_t vmask = (ncol == 8 ? 0xFFu : ncol == 4 ? 0x0Fu : 0u) & ((1u << ngrid) - 1u);
     const int xa = act ? x0 : 0;                           // safe address for idle threads
     const int xb = ncol == 8 ? x0 + 4 : xa;                // second float4 (duplicate when absent)
     const int xl = max(xa - 1, 0);
@@ -1749,6 +1753,36 @@ __global__ void __launch_bounds__(NT) k_stream_copy(const StreamSrc *src, float 
     }
 }
 
+// one warp per row: rows of nx floats -> rows of pitch floats, the padding
+// repeating column nx-1
+__device__ __forceinline__ void pad_rows(const float *src, float *dst, int nx, int pitch, long long rows) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (NT / 32);
+    for (long long r = blockIdx.x * (long long)(NT / 32) + (threadIdx.x >> 5); r < rows; r += nw) {
+        const float *a = src + r * nx;
+        float *b = dst + r * pitch;
+        for (int x = lane; x < pitch; x += 32) b[x] = a[x < nx ? x : nx - 1];
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_pad_rows(const float *src, float *dst, int nx, int pitch, long long rows) {
+    pad_rows(src, dst, nx, pitch, rows);
+}
+
+__global__ void __launch_bounds__(NT) k_stream_copy_pad(const StreamSrc *src, float *dst, int nx, int pitch,
+                                                        long long rows) {
+    pad_rows(src->ptr, dst, nx, pitch, rows);
+}
+
+__global__ void __launch_bounds__(NT) k_fill_pad(float *dst, int nx, int pitch, long long rows) {
+    const int w = pitch - nx;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < rows * w; i += (long long)gridDim.x * NT) {
+        const long long r = i / w;
+        float *row = dst + r * pitch;
+        row[nx + (int)(i - r * w)] = row[nx - 1];
+    }
+}
+
 __global__ void __launch_bounds__(NT) k_stream_final(long long n, const int *gshadow, int *gparent, const long long *gmin,
                                                      const ftk_cp *grec, ftk_cp *out, long long *count,
                                                      unsigned *status) {
@@ -1781,10 +1815,25 @@ cudaError_t launch_stream_merge(const StreamMerge &M, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_stream_copy(const StreamSrc *src, float *dst, long long n, cudaStream_t s) {
-    const long long want = (n / 4 + NT - 1) / NT;
-    const int grid = (int)(want < sparse_grid() ? (want > 0 ? want : 1) : sparse_grid());
-    k_stream_copy<<<grid, NT, 0, s>>>(src, dst, n);
+cudaError_t launch_stream_copy(const StreamSrc *src, float *dst, int nx, int pitch, long long rows, cudaStream_t s) {
+    const int sg = sparse_grid();
+    if (pitch == nx) {
+        const long long n = (long long)nx * rows;
+        const long long want = (n / 4 + NT - 1) / NT;
+        k_stream_copy<<<(int)(want < sg ? (want > 0 ? want : 1) : sg), NT, 0, s>>>(src, dst, n);
+    } else {
+        k_stream_copy_pad<<<sg, NT, 0, s>>>(src, dst, nx, pitch, rows);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_rows(const float *src, float *dst, int nx, int pitch, long long rows, cudaStream_t s) {
+    k_pad_rows<<<sparse_grid(), NT, 0, s>>>(src, dst, nx, pitch, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_pad(float *dst, int nx, int pitch, long long rows, cudaStream_t s) {
+    if (pitch > nx) k_fill_pad<<<sparse_grid(), NT, 0, s>>>(dst, nx, pitch, rows);
     return cudaGetLastError();
 }
 
@@ -1812,12 +1861,12 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
         const cudaError_t e = launch_detect3(variant, F, B, W, s, capturing);
         if (e != cudaSuccess) return e;
     } else if (N == 2 && variant != VAR_TILE) {
-        const size_t smem = stream2_smem_bytes(F.nx);
-        const void *k = variant == VAR_STREAM2_EXACT ? stream2_kernel<true>(F.nx) : stream2_kernel<false>(F.nx);
+        const size_t smem = stream2_smem_bytes(F.pitch);
+        const void *k = variant == VAR_STREAM2_EXACT ? stream2_kernel<true>(F.pitch) : stream2_kernel<false>(F.pitch);
         // the attribute only ever grows: a graph may replay a wider field's
         // launch after a narrower one was configured
         static size_t configured[4] = {0, 0, 0, 0};
-        const int slot = (variant == VAR_STREAM2_EXACT ? 2 : 0) + (F.nx <= 1024 ? 0 : 1);
+        const int slot = (variant == VAR_STREAM2_EXACT ? 2 : 0) + (F.pitch <= 1024 ? 0 : 1);
         cudaError_t e = cudaSuccess;
         if (smem > configured[slot]) {
             if (capturing) return cudaErrorInvalidValue;   // configured by the first, uncaptured launch
@@ -1830,7 +1879,7 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
         Blocking Ba = B;
         Workspace Wa = W;
         void *args[] = {&Fa, &Ba, &Wa};
-        e = cudaLaunchKernel(k, dim3(units), dim3(stream2_threads(F.nx)), args, smem, s);
+        e = cudaLaunchKernel(k, dim3(units), dim3(stream2_threads(F.pitch)), args, smem, s);
         if (e != cudaSuccess) return e;
     } else {
         const size_t smem = detect_smem_bytes(N, F, B);

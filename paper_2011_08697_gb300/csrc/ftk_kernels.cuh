@@ -47,8 +47,9 @@ __host__ __device__ inline unsigned fdiv(unsigned n, const FastDiv &f) {
 }
 
 struct Field {
-    const float *f;      // C-contiguous f[t][z][y][x]
+    const float *f;      // f[t][z][y][x], rows of `pitch` floats (the first nx are the grid's)
     int nx, ny, nz, nt;  // nz = 1 in 2D
+    int pitch;           // floats from one grid row to the next (>= nx)
     float scale;         // 2^quant_shift
     int small;           // nx*ny*nz*nt < 2^31: vertex ids decode with FastDiv
     FastDiv dx, dy, dz;  // division by nx, ny, nz
@@ -136,6 +137,11 @@ int stream3_threads();
 int stream3_ctas_per_sm(int nx, const Blocking &B);
 cudaError_t launch_detect3(int variant, const Field &F, const Blocking &B, const Workspace &W, cudaStream_t s,
                            bool capturing);
+// rows of nx floats at src (any alignment) -> rows of pitch floats at dst,
+// columns nx..pitch-1 repeating column nx-1
+cudaError_t launch_pad_rows(const float *src, float *dst, int nx, int pitch, long long rows, cudaStream_t s);
+// columns nx..pitch-1 of every row of dst := column nx-1
+cudaError_t launch_fill_pad(float *dst, int nx, int pitch, long long rows, cudaStream_t s);
 cudaError_t launch_pipeline(int ndim, int variant, const Field &F, const Blocking &B, const Workspace &W,
                             cudaStream_t s, cudaEvent_t *ev /* 6 events or null */);
 
@@ -187,8 +193,9 @@ struct StreamMerge {
 constexpr int DELTA_BLOCK = 1024;     // punctures per block of the delta compaction
 
 cudaError_t launch_stream_merge(const StreamMerge &M, cudaStream_t s);
-// copies n floats from the address in *src (device or mapped host memory) to dst
-cudaError_t launch_stream_copy(const StreamSrc *src, float *dst, long long n, cudaStream_t s);
+// copies `rows` rows of nx floats from the address in *src (device memory)
+// to dst with row pitch `pitch` (padding as launch_pad_rows)
+cudaError_t launch_stream_copy(const StreamSrc *src, float *dst, int nx, int pitch, long long rows, cudaStream_t s);
 cudaError_t launch_stream_final(long long n, const int *gshadow, int *gparent, const long long *gmin,
                                 const ftk_cp *grec, ftk_cp *out, long long *count, unsigned *status,
                                 cudaStream_t s);

@@ -90,6 +90,7 @@ extern "C" ftk_status ftk_track_cp2d_noalloc(const float *f_dev, int64_t nx, int
     Field F;
     F.f = f_dev;
     F.nx = (int)nx; F.ny = (int)ny; F.nz = 1; F.nt = (int)nt;
+    F.pitch = (int)nx;   // the tiled kernel reads the field in place
     F.scale = (float)std::ldexp(1.0, prm.quant_shift);
     field_divisors(F);
 

@@ -46,8 +46,11 @@ struct ftk_stream {
     ftk_server *server = nullptr;
     size_t footprint = 0;
     ftk_plan *plan1 = nullptr, *plan2 = nullptr;
-    float *d2 = nullptr;          // two slices, [previous | current]
-    long long slice_verts = 0;
+    float *d2 = nullptr;          // two slices, [previous | current], rows of the plans' pitch
+    long long slice_verts = 0;    // grid vertices per slice
+    long long slice_rows = 0;     // rows per slice (ny * nz)
+    long long slice_elems = 0;    // floats per slice in d2 (slice_rows * pitch)
+    int pitch = 0;
     int T = 12, tbit = 4;
     long long k = 0;              // pushes done (host copy)
     long long n = 0;              // global slots in use (host copy)
@@ -203,14 +206,23 @@ StreamMerge merge_args(ftk_stream *st, ftk_plan *pl) {
 // one push's device work: bring in the slice (host_slice: a host pointer to
 // copy from; otherwise the device address in *dSrc), run the pipeline, merge
 ftk_status enqueue_push(ftk_stream *st, ftk_plan *pl, long long k, const float *host_slice) {
-    const size_t sbytes = sizeof(float) * (size_t)st->slice_verts;
-    float *dst = k == 0 ? st->d2 : st->d2 + st->slice_verts;
+    const size_t ebytes = sizeof(float) * (size_t)st->slice_elems;
+    float *dst = k == 0 ? st->d2 : st->d2 + st->slice_elems;
     cudaError_t e;
-    if (k >= 2 && (e = cudaMemcpyAsync(st->d2, st->d2 + st->slice_verts, sbytes, cudaMemcpyDeviceToDevice, st->cs)) !=
+    if (k >= 2 && (e = cudaMemcpyAsync(st->d2, st->d2 + st->slice_elems, ebytes, cudaMemcpyDeviceToDevice, st->cs)) !=
                       cudaSuccess)
         return cuda_fail(e, "slice shift");
-    if (host_slice) e = cudaMemcpyAsync(dst, host_slice, sbytes, cudaMemcpyHostToDevice, st->cs);
-    else e = launch_stream_copy(st->dSrc, dst, st->slice_verts, st->cs);
+    if (host_slice) {
+        if (st->pitch == st->nx) {
+            e = cudaMemcpyAsync(dst, host_slice, ebytes, cudaMemcpyHostToDevice, st->cs);
+        } else {
+            e = cudaMemcpy2DAsync(dst, (size_t)st->pitch * 4, host_slice, (size_t)st->nx * 4, (size_t)st->nx * 4,
+                                  (size_t)st->slice_rows, cudaMemcpyHostToDevice, st->cs);
+            if (e == cudaSuccess) e = launch_fill_pad(dst, st->nx, st->pitch, st->slice_rows, st->cs);
+        }
+    } else {
+        e = launch_stream_copy(st->dSrc, dst, st->nx, st->pitch, st->slice_rows, st->cs);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "slice copy");
     ftk_status s = plan_launch(pl, st->d2, st->cs);
     if (s != FTK_OK) return s;
@@ -291,8 +303,11 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
         release(st);
         return s;
     }
+    st->pitch = st->plan2->F.pitch;
+    st->slice_rows = (long long)ny * nz;
+    st->slice_elems = st->slice_rows * st->pitch;
     if (cudaStreamCreateWithFlags(&st->cs, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMalloc(&st->d2, sizeof(float) * 2 * st->slice_verts) != cudaSuccess ||
+        cudaMalloc(&st->d2, sizeof(float) * 2 * st->slice_elems) != cudaSuccess ||
         cudaMalloc(&st->dS, sizeof(StreamDev)) != cudaSuccess ||
         cudaMemset(st->dS, 0, sizeof(StreamDev)) != cudaSuccess ||
         cudaHostAlloc(&st->hV, sizeof(StreamView), cudaHostAllocMapped) != cudaSuccess ||
@@ -304,7 +319,7 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
         release(st);
         return fail(FTK_ERR_NOMEM, "stream allocation failed");
     }
-    st->footprint = sizeof(float) * 2 * st->slice_verts + plan_bytes(st->plan1) + plan_bytes(st->plan2);
+    st->footprint = sizeof(float) * 2 * st->slice_elems + plan_bytes(st->plan1) + plan_bytes(st->plan2);
     if (srv) {
         std::lock_guard<std::mutex> lock(srv->mu);
         if (srv->used + st->footprint > srv->budget) {

@@ -61,15 +61,16 @@ __device__ __forceinline__ void named_sync(int id, int threads) {
 
 // Compactor of the streaming detect kernels (one warp): writes the set bits
 // of words[0..nw) -- bit i stands for cube row i / nx, column i % nx of a
-// segment -- as vertex ids (row0 + i / nx) * nx + i % nx to out[pos..] in
-// bit order, and clears the words.  A chunk of 32 * WPL words gives each lane
+// segment -- as vertex ids (row0 + i / nx) * nx_ids + i % nx to out[pos..] in
+// bit order (nx_ids = the grid's width, nx = the bitmap's row length), and
+// clears the words.  A chunk of 32 * WPL words gives each lane
 // WPL consecutive words, so a dense region spreads over the warp with one
 // warp scan per chunk; chunks without a set bit are skipped.  inv_nx = 1 / nx
 // (float); i < 2^24 keeps the row estimate within one of floor(i / nx), and
 // the estimate is corrected.
 template <int WPL>
-__device__ __forceinline__ void compact_bits(uint32_t *words, int nw, int nx, float inv_nx, long long row0,
-                                             long long pos, long long *out, long long cap) {
+__device__ __forceinline__ void compact_bits(uint32_t *words, int nw, int nx, int nx_ids, float inv_nx,
+                                             long long row0, long long pos, long long *out, long long cap) {
     const int lane = threadIdx.x & 31;
     for (int k0 = 0; k0 < nw; k0 += 32 * WPL) {
         const int w0 = k0 + lane * WPL;
@@ -108,7 +109,7 @@ __device__ __forceinline__ void compact_bits(uint32_t *words, int nw, int nx, fl
                         x -= nx;
                         ++crr;
                     }
-                    if (p < cap) out[p] = (row0 + crr) * nx + x;
+                    if (p < cap) out[p] = (row0 + crr) * nx_ids + x;
                     ++p;
                 }
                 xw += 32;
