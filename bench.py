@@ -167,7 +167,8 @@ def profiled_traffic(wl: str):
     """DRAM bytes per detect launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2011_08697_gb300", "csrc", "ftk_kernels.cu")
+    src_file = "ftk_detect3.cu" if wl == "blobs3d" else "ftk_kernels.cu"
+    src = os.path.join(ROOT, "paper_2011_08697_gb300", "csrc", src_file)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", f"detect_{wl}_traffic.txt")
     if not os.path.exists(path):
