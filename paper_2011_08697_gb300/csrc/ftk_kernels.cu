@@ -1059,10 +1059,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     const int t0 = tci * B.tc;
     const int t_end = min(nt, t0 + B.tc);
     const int s_last = min(t_end, nt - 1);
-    const int nsl = s_last - t0 + 1;      // slices streamed
+    const int nsl = s_last - t0 + 1;      // slices of the unit
     const int nslab = t_end - t0;         // slabs (base slices) owned
     constexpr int RS = RY2 + 3;           // rows streamed per slice
-    const int J = nsl * RS;
+    const int sl0 = B.st_mode == 2 ? 1 : 0;   // slice 0's words come from st_in
+    const int J = (nsl - sl0) * RS;
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < NS2; ++k) {
@@ -1090,7 +1091,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
                     ok = false;
                     break;
                 }
-                const int s = t0 + j / RS;
+                const int s = t0 + sl0 + j / RS;
                 const int y = min(max(y0 - 1 + j % RS, 0), ny - 1);
                 mbar_arrive_expect_tx(&full[slot], (uint32_t)nx * 4u);
                 tma_row(ring + (size_t)slot * nx, F.f + ((long long)s * ny + y) * nx, (uint32_t)nx * 4u, &full[slot]);
@@ -1156,6 +1157,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     uint32_t st[RY2];
 #pragma unroll
     for (int i = 0; i < RY2; ++i) st[i] = 0;
+    // incremental mode: slice 0's cube-row words from the previous push
+    const long long st_base = ((long long)yb * RY2) * NC + threadIdx.x;
+    if (B.st_mode == 2) {
+#pragma unroll
+        for (int i = 0; i < RY2; ++i) st[i] = B.st_in[st_base + (long long)i * NC];
+    }
     uint32_t fa[11], fb[11], fc[11];
 #pragma unroll
     for (int k = 0; k < 11; ++k) fa[k] = fb[k] = fc[k] = MAGIC_BITS;
@@ -1164,7 +1171,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     int nsv = 0;     // survivors this thread found in the current slab
     bool ok = true;
 
-    for (int sl = 0; sl < nsl && ok; ++sl) {
+    for (int sl = sl0; sl < nsl && ok; ++sl) {
         // slice sl > 0 completes slab q = sl-1, whose bits go to buffer q & 1:
         // wait until the compactor has released that buffer (slab q-2)
         const int q = sl - 1;
@@ -1299,6 +1306,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
             __syncwarp();
             if (lane == 0) mbar_arrive(&done[q & 1]);
         }
+    }
+    if (ok && B.st_mode) {
+        // the last slice's cube-row words for the next push
+#pragma unroll
+        for (int i = 0; i < RY2; ++i) B.st_out[st_base + (long long)i * NC] = st[i];
     }
     if (!ok) atomicOr(status, ST_TIMEOUT);
     if (bad & (EXACT ? 1u : 0xFF800000u)) atomicOr(status, EXACT ? ST_RANGE : ST_WIDE);
@@ -1511,6 +1523,10 @@ static void *stream2_kernel(int nx) {
     return (void *)k_detect2_stream<EXACT, 320, 1>;
 }
 
+long long stream2_state_words(const Field &F, const Blocking &B) {
+    return (long long)B.nyb * RY2 * stream2_consumers(F.pitch);
+}
+
 int stream2_ctas_per_sm(int nx) {
     int n = 0;
     const size_t smem = stream2_smem_bytes(nx);
@@ -1710,6 +1726,14 @@ __global__ void __launch_bounds__(NT) k_delta_write(StreamMerge M) {
     }
 }
 
+// after a merged push: the run's incremental detect state becomes the input
+// of the next push (a run that was not merged keeps the old state)
+__global__ void __launch_bounds__(NT) k_state_commit(StreamMerge M) {
+    if (M.ctr->status & RUN_BAD) return;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < M.st_words; i += (long long)gridDim.x * NT)
+        M.st_in[i] = M.st_out[i];
+}
+
 // one thread: the report to the host and the advance of the scalars (after
 // every kernel of the push has read them)
 __global__ void k_stream_advance(StreamMerge M) {
@@ -1753,15 +1777,17 @@ __global__ void __launch_bounds__(NT) k_stream_copy(const StreamSrc *src, float 
     }
 }
 
-// one warp per row: rows of nx floats -> rows of pitch floats, the padding
-// repeating column nx-1
-__device__ __forceinline__ void pad_rows(const float *src, float *dst, int nx, int pitch, long long rows) {
-    const int lane = threadIdx.x & 31;
-    const long long nw = (long long)gridDim.x * (NT / 32);
-    for (long long r = blockIdx.x * (long long)(NT / 32) + (threadIdx.x >> 5); r < rows; r += nw) {
-        const float *a = src + r * nx;
-        float *b = dst + r * pitch;
-        for (int x = lane; x < pitch; x += 32) b[x] = a[x < nx ? x : nx - 1];
+// rows of nx floats -> rows of pitch floats, the padding repeating column
+// nx-1; one element per thread and step (coalesced, no dependent chain)
+__device__ __forceinline__ void pad_rows(const float *__restrict__ src, float *__restrict__ dst, int nx, int pitch,
+                                         long long rows) {
+    const long long n = rows * pitch;
+    const long long stride = (long long)gridDim.x * NT;
+#pragma unroll 4
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += stride) {
+        const long long r = i / pitch;
+        const int x = (int)(i - r * pitch);
+        dst[i] = __ldg(src + r * nx + (x < nx ? x : nx - 1));
     }
 }
 
@@ -1812,6 +1838,7 @@ cudaError_t launch_stream_merge(const StreamMerge &M, cudaStream_t s) {
     k_delta_scan<<<1, NT, 0, s>>>(M);
     k_delta_write<<<sg, NT, 0, s>>>(M);
     k_stream_advance<<<1, 1, 0, s>>>(M);
+    if (M.st_words > 0) k_state_commit<<<sg, NT, 0, s>>>(M);
     return cudaGetLastError();
 }
 
@@ -1822,13 +1849,17 @@ cudaError_t launch_stream_copy(const StreamSrc *src, float *dst, int nx, int pit
         const long long want = (n / 4 + NT - 1) / NT;
         k_stream_copy<<<(int)(want < sg ? (want > 0 ? want : 1) : sg), NT, 0, s>>>(src, dst, n);
     } else {
-        k_stream_copy_pad<<<sg, NT, 0, s>>>(src, dst, nx, pitch, rows);
+        const long long want = ((long long)pitch * rows + NT - 1) / NT;
+        k_stream_copy_pad<<<(int)(want < 4LL * sg ? (want > 0 ? want : 1) : 4LL * sg), NT, 0, s>>>(src, dst, nx,
+                                                                                                  pitch, rows);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_pad_rows(const float *src, float *dst, int nx, int pitch, long long rows, cudaStream_t s) {
-    k_pad_rows<<<sparse_grid(), NT, 0, s>>>(src, dst, nx, pitch, rows);
+    const long long want = ((long long)pitch * rows + NT - 1) / NT;
+    const long long cap = 4LL * sparse_grid();
+    k_pad_rows<<<(int)(want < cap ? (want > 0 ? want : 1) : cap), NT, 0, s>>>(src, dst, nx, pitch, rows);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,12 @@ struct Blocking {
     int ry, rz;          // rows / planes of base vertices per unit
     int nyb, nzb;        // y and z blocks
     int tc, ntc;         // slices per time chunk, number of time chunks
+    // incremental mode of the 2D streaming kernel for in-situ streams: 0 off;
+    // 1 store the last slice's cube-row words to st_out; 2 take slice 0's
+    // words from st_in (only slice 1 is streamed) and store slice 1's to st_out
+    int st_mode;
+    const uint32_t *st_in;
+    uint32_t *st_out;
 };
 
 struct Workspace {
@@ -130,6 +136,8 @@ size_t detect_smem_bytes(int ndim, const Field &F, const Blocking &B);
 size_t stream2_smem_bytes(int nx);
 int stream2_threads(int nx);
 int stream2_ctas_per_sm(int nx);
+// words of incremental detect state of a 2D streaming plan (0 if it has none)
+long long stream2_state_words(const Field &F, const Blocking &B);
 // 3D streaming kernel: smem per CTA for B.ry, B.rz, B.ns; threads; resident
 // CTAs per SM; launch (the smem attribute is set outside graph capture)
 size_t stream3_smem_bytes(int nx, const Blocking &B);
@@ -187,6 +195,9 @@ struct StreamMerge {
     int *link_prev;             // [P] earlier slot of a shadow, -1 otherwise
     int *old_root;              // [P] root of that earlier slot before this push's unions
     long long *blk;             // [4 * (P / DELTA_BLOCK + 1)] per-block counts and offsets
+    uint32_t *st_in;            // incremental detect state: committed after a good push
+    const uint32_t *st_out;
+    long long st_words;
     ftk_cp *delta;              // [P] delta records (mapped host memory)
     StreamView *view;           // (mapped host memory)
 };

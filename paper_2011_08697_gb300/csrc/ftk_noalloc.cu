@@ -94,7 +94,7 @@ extern "C" ftk_status ftk_track_cp2d_noalloc(const float *f_dev, int64_t nx, int
     F.scale = (float)std::ldexp(1.0, prm.quant_shift);
     field_divisors(F);
 
-    Blocking B;
+    Blocking B{};
     static const int cand[] = {16, 8, 4, 2, 1};
     bool ok = false;
     for (int ry : cand) {

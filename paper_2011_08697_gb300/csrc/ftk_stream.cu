@@ -77,6 +77,9 @@ struct ftk_stream {
     int *link_prev = nullptr, *old_root = nullptr;
     long long *blk = nullptr;     // per-block counts of the delta compaction
     long long bcap = 0;
+    // incremental 2D detect: the last slice's cube-row words (committed, pending)
+    uint32_t *st_in = nullptr, *st_out = nullptr;
+    long long st_words = 0;
     // one captured push (k >= 2) replayed for every later push
     cudaGraphExec_t exec = nullptr;
 };
@@ -198,6 +201,9 @@ StreamMerge merge_args(ftk_stream *st, ftk_plan *pl) {
     M.link_prev = st->link_prev;
     M.old_root = st->old_root;
     M.blk = st->blk;
+    M.st_in = st->st_in;
+    M.st_out = st->st_out;
+    M.st_words = st->st_words;
     M.delta = st->d_delta;
     M.view = st->dV;
     return M;
@@ -265,6 +271,7 @@ void release(ftk_stream *st) {
     cudaFree(st->gfid); cudaFree(st->gparent); cudaFree(st->gmin); cudaFree(st->gshadow); cudaFree(st->grec);
     for (int q = 0; q < 2; ++q) { cudaFree(st->ord_fid[q]); cudaFree(st->ord_gi[q]); }
     cudaFree(st->link_prev); cudaFree(st->old_root); cudaFree(st->blk);
+    cudaFree(st->st_in); cudaFree(st->st_out);
     if (st->done) cudaEventDestroy(st->done);
     if (st->cs) cudaStreamDestroy(st->cs);
     if (st->server) {
@@ -303,6 +310,25 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
         release(st);
         return s;
     }
+    // incremental detect (2D streaming plans): push 0 stores slice 0's
+    // cube-row words, every later push streams only its new slice
+    if (ndim == 2 && st->plan1->variant != VAR_TILE && st->plan2->variant != VAR_TILE &&
+        st->plan1->B.nyb == st->plan2->B.nyb) {
+        st->st_words = stream2_state_words(st->plan2->F, st->plan2->B);
+        if (cudaMalloc(&st->st_in, sizeof(uint32_t) * st->st_words) != cudaSuccess ||
+            cudaMalloc(&st->st_out, sizeof(uint32_t) * st->st_words) != cudaSuccess) {
+            cudaGetLastError();
+            release(st);
+            return fail(FTK_ERR_NOMEM, "stream allocation failed");
+        }
+        st->plan1->B.st_mode = 1;
+        st->plan1->B.st_out = st->st_out;
+        st->plan2->B.st_mode = 2;
+        st->plan2->B.st_in = st->st_in;
+        st->plan2->B.st_out = st->st_out;
+        st->plan2->B.tc = 2;     // one unit per row block covers both slices
+        st->plan2->B.ntc = 1;
+    }
     st->pitch = st->plan2->F.pitch;
     st->slice_rows = (long long)ny * nz;
     st->slice_elems = st->slice_rows * st->pitch;
@@ -319,7 +345,8 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
         release(st);
         return fail(FTK_ERR_NOMEM, "stream allocation failed");
     }
-    st->footprint = sizeof(float) * 2 * st->slice_elems + plan_bytes(st->plan1) + plan_bytes(st->plan2);
+    st->footprint = sizeof(float) * 2 * st->slice_elems + plan_bytes(st->plan1) + plan_bytes(st->plan2) +
+                    sizeof(uint32_t) * 2 * (size_t)st->st_words;
     if (srv) {
         std::lock_guard<std::mutex> lock(srv->mu);
         if (srv->used + st->footprint > srv->budget) {
