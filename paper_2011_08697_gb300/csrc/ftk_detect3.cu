@@ -40,7 +40,7 @@ namespace ftk {
 
 namespace {
 
-constexpr int S3_NW = 8;                  // consumer warps
+constexpr int S3_NW = 4;                  // consumer warps (each takes 4 of 16 G rows per plane)
 constexpr int S3_NS = 5;                  // smem ring slots (plane chunks)
 constexpr int S3_THREADS = (S3_NW + 2) * 32;
 constexpr float S3_RANGE = 268435456.0f;  // 2^28
@@ -113,7 +113,7 @@ __device__ __forceinline__ uint32_t qd(uint32_t a, uint32_t b) {
 }
 
 template <bool EXACT>
-__global__ void __launch_bounds__(S3_THREADS, 2) k_detect3_stream(Field F, Blocking B, Workspace W) {
+__global__ void __launch_bounds__(S3_THREADS, 3) k_detect3_stream(Field F, Blocking B, Workspace W) {
     extern __shared__ __align__(128) unsigned char smem[];
     // the sweep covers the padded row (pitch columns, the padding repeating
     // column nx-1); survivors are the grid's (columns < nxl)
@@ -257,9 +257,14 @@ __global__ void __launch_bounds__(S3_THREADS, 2) k_detect3_stream(Field F, Block
     bool ok = true;
 
     auto srw = [&](int buf, int row, int cc) -> uint32_t * { return SR + ((buf * GR + row) * XC + cc) * 32; };
-    auto rowp = [&](const float *p, int yy) -> const float * {
-        return p + (size_t)(min(max(yy, 0), ny - 1) - ylo) * nx;
-    };
+    // offset (floats) of this lane's first column of grid row yy (clamped)
+    // within a plane chunk
+    auto roff = [&](int yy) -> int { return (min(max(yy, 0), ny - 1) - ylo) * nx + xa; };
+    const int yfirst = y0 + gr0;
+    const int ngr = max(0, min(gr1, ny - y0) - gr0);       // this warp's G rows inside the grid
+    // halo sample of this lane: lane 0 the column left of the chunk (itself
+    // at x = 0), lane 31 the column right of it (unused at the grid's edge)
+    const int hoff = !act ? 0 : lane == 0 ? (xa == 0 ? 0 : -1) : (lane == 31 && !xlast ? 4 : 0);
     // cube word of chunk cc, lane l of cube row (rows cr, cr2) between G planes a and b
     auto cube_word = [&](int ba, int bb, int cr, int cr2, int cc, int l) -> uint32_t {
         const uint32_t t0w = cmb(srw(ba, cr, cc)[l], srw(bb, cr, cc)[l]);
@@ -288,44 +293,41 @@ __global__ void __launch_bounds__(S3_THREADS, 2) k_detect3_stream(Field F, Block
             for (int jj = gi == 0 ? jb : jb + gi + 2; jj <= jb + gi + 2; ++jj)
                 if (ok && !wait_ab(&full[jj % NS], (jj / NS) & 1, abort)) ok = false;
             ok = __all_sync(ALL, ok);
-            if (ok && z0 + gi <= nz - 1) {
+            if (ok && z0 + gi <= nz - 1 && ngr > 0) {
                 const float *pm = ring + (size_t)((jb + gi) % NS) * L.slot_floats;
                 const float *p0 = ring + (size_t)((jb + gi + 1) % NS) * L.slot_floats;
                 const float *pp = ring + (size_t)((jb + gi + 2) % NS) * L.slot_floats;
                 uint32_t *dst = SR + (((gi % 3) * GR + gr0) * XC + c) * 32 + lane;
-                // rolling rows y-1, y, y+1 of the own plane (quantised)
-                uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-                const int yfirst = y0 + gr0;
-                const float *rown = rowp(p0, yfirst) + xa;     // row y
-                const float *rnext = rowp(p0, yfirst + 1) + xa; // row y+1 (clamped)
-                const float *rm = rowp(pm, yfirst) + xa;
-                const float *rpp = rowp(pp, yfirst) + xa;
-                if (gr0 < gr1 && yfirst <= ny - 1) {
-                    const float4 va = *reinterpret_cast<const float4 *>(rowp(p0, yfirst - 1) + xa);
-                    const float4 vb = *reinterpret_cast<const float4 *>(rown);
-                    a0 = q3<EXACT>(va.x, scale, bad); a1 = q3<EXACT>(va.y, scale, bad);
-                    a2 = q3<EXACT>(va.z, scale, bad); a3 = q3<EXACT>(va.w, scale, bad);
-                    b0 = q3<EXACT>(vb.x, scale, bad); b1 = q3<EXACT>(vb.y, scale, bad);
-                    b2 = q3<EXACT>(vb.z, scale, bad); b3 = q3<EXACT>(vb.w, scale, bad);
-                }
-                for (int gr = gr0; gr < gr1; ++gr) {
-                    const int y = y0 + gr;
-                    if (y > ny - 1) break;
-                    const float4 vc = *reinterpret_cast<const float4 *>(rnext);
-                    const float4 vm = *reinterpret_cast<const float4 *>(rm);
-                    const float4 vp = *reinterpret_cast<const float4 *>(rpp);
+                // rolling rows y-1 (a), y (b) of the own plane, quantised, and
+                // the lane's halo sample of row y
+                const int ob0 = roff(yfirst);
+                const float4 va = *reinterpret_cast<const float4 *>(p0 + roff(yfirst - 1));
+                const float4 vb = *reinterpret_cast<const float4 *>(p0 + ob0);
+                uint32_t a0 = q3<EXACT>(va.x, scale, bad), a1 = q3<EXACT>(va.y, scale, bad);
+                uint32_t a2 = q3<EXACT>(va.z, scale, bad), a3 = q3<EXACT>(va.w, scale, bad);
+                uint32_t b0 = q3<EXACT>(vb.x, scale, bad), b1 = q3<EXACT>(vb.y, scale, bad);
+                uint32_t b2 = q3<EXACT>(vb.z, scale, bad), b3 = q3<EXACT>(vb.w, scale, bad);
+                uint32_t hb = q3<EXACT>(p0[ob0 + hoff], scale, bad);
+#pragma unroll 2
+                for (int r = 0; r < ngr; ++r) {
+                    const int y = yfirst + r;
+                    const int o0 = roff(y), oc = roff(y + 1);
+                    const float4 vc = *reinterpret_cast<const float4 *>(p0 + oc);
+                    const float4 vm = *reinterpret_cast<const float4 *>(pm + o0);
+                    const float4 vp = *reinterpret_cast<const float4 *>(pp + o0);
+                    const uint32_t hc = q3<EXACT>(p0[oc + hoff], scale, bad);
                     const uint32_t c0 = q3<EXACT>(vc.x, scale, bad), c1 = q3<EXACT>(vc.y, scale, bad);
                     const uint32_t c2 = q3<EXACT>(vc.z, scale, bad), c3 = q3<EXACT>(vc.w, scale, bad);
                     const uint32_t m0 = q3<EXACT>(vm.x, scale, bad), m1 = q3<EXACT>(vm.y, scale, bad);
                     const uint32_t m2 = q3<EXACT>(vm.z, scale, bad), m3 = q3<EXACT>(vm.w, scale, bad);
                     const uint32_t p0q = q3<EXACT>(vp.x, scale, bad), p1q = q3<EXACT>(vp.y, scale, bad);
                     const uint32_t p2q = q3<EXACT>(vp.z, scale, bad), p3q = q3<EXACT>(vp.w, scale, bad);
-                    // columns xb-1 and xb+4 (clamped) of the own row
-                    uint32_t lq = __shfl_up_sync(ALL, b3, 1);
-                    uint32_t rq = __shfl_down_sync(ALL, b0, 1);
-                    if (lane == 0) lq = xa == 0 ? b0 : q3<EXACT>(rown[-1], scale, bad);
-                    if (xlast) rq = b3;
-                    else if (lane == 31) rq = q3<EXACT>(rown[4], scale, bad);
+                    // columns xb-1 and xb+4 (clamped) of the own row: neighbours'
+                    // samples, or this lane's halo sample at the warp's edges
+                    const uint32_t up = __shfl_up_sync(ALL, b3, 1);
+                    const uint32_t dn = __shfl_down_sync(ALL, b0, 1);
+                    const uint32_t lq = lane == 0 ? hb : up;
+                    const uint32_t rq = xlast ? b3 : lane == 31 ? hb : dn;
                     if (!EXACT && act) {
                         // own samples must lie in the fast encoding's range (the
                         // exact form checks every sample it quantises)
@@ -346,12 +348,10 @@ __global__ void __launch_bounds__(S3_THREADS, 2) k_detect3_stream(Field F, Block
                     w = __funnelshift_l(qd<EXACT>(b3, b1), w, 1);
                     w = __funnelshift_l(qd<EXACT>(b2, b0), w, 1);
                     w = __funnelshift_l(qd<EXACT>(b1, lq), w, 1);
-                    *dst = w | (w << 16);
-                    dst += XC * 32;
+                    dst[r * XC * 32] = w | (w << 16);
                     a0 = b0; a1 = b1; a2 = b2; a3 = b3;
                     b0 = c0; b1 = c1; b2 = c2; b3 = c3;
-                    rown += nx; rm += nx; rpp += nx;
-                    if (y + 2 <= ny - 1) rnext += nx;
+                    hb = hc;
                 }
             }
             // release the plane chunk that no later G plane of this slice reads
