@@ -984,7 +984,7 @@ __global__ void __launch_bounds__(NT) k_label(Field F, Workspace W) {
 // No CTA-wide barrier runs inside the main loop.
 // ----------------------------------------------------------------------------
 constexpr int RY2 = 16;       // cube rows per unit
-constexpr int NS2 = 16;       // TMA ring slots (rows)
+constexpr int NS2 = 8;        // TMA ring slots (rows)
 constexpr int CX = 8;         // columns per consumer thread
 // quantised sample in offset encoding: MAGIC_BITS + rint(v 2^S) (mod 2^32);
 // differences of two encodings are exact integer differences
@@ -1003,7 +1003,7 @@ __device__ __forceinline__ uint32_t qbits(float v, float scale, uint32_t &bad) {
 __host__ __device__ inline int stream2_consumers(int nx) { return ((nx + CX - 1) / CX + 31) / 32 * 32; }
 
 struct Stream2Layout {
-    int ring, bars, bm, bmw, cnt, total;
+    int ring, bars, bm, bmw, cnt, st, total;
 };
 __host__ __device__ inline Stream2Layout stream2_layout(int nx) {
     Stream2Layout L;
@@ -1012,7 +1012,8 @@ __host__ __device__ inline Stream2Layout stream2_layout(int nx) {
     L.bmw = (RY2 * nx + 31) / 32;
     L.bm = round_up16(L.bars + (2 * NS2 + 4) * 8);
     L.cnt = L.bm + 2 * L.bmw * 4;     // [2] survivors per slab buffer
-    L.total = round_up16(L.cnt + 2 * 4);
+    L.st = round_up16(L.cnt + 2 * 4); // [RY2][consumers] cube-row words of the previous slice
+    L.total = round_up16(L.st + RY2 * stream2_consumers(nx) * 4);
     return L;
 }
 
@@ -1154,14 +1155,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     const bool dbl3 = ncol == 4;                           // ... at x = nx-1 (column 3)
     const float scale = F.scale;
     uint32_t bad = 0, dummy = 0;
-    uint32_t st[RY2];
-#pragma unroll
-    for (int i = 0; i < RY2; ++i) st[i] = 0;
+    // cube-row words of the previous slice, one smem column per thread
+    // (row i at sst[i * NC]): indexed by the row, so the row loop need not be
+    // unrolled completely
+    uint32_t *sst = reinterpret_cast<uint32_t *>(smem + L.st) + threadIdx.x;
+    for (int i = 0; i < RY2; ++i) sst[i * NC] = 0;
     // incremental mode: slice 0's cube-row words from the previous push
     const long long st_base = ((long long)yb * RY2) * NC + threadIdx.x;
     if (B.st_mode == 2) {
 #pragma unroll
-        for (int i = 0; i < RY2; ++i) st[i] = B.st_in[st_base + (long long)i * NC];
+        for (int i = 0; i < RY2; ++i) sst[i * NC] = B.st_in[st_base + (long long)i * NC];
     }
     uint32_t fa[11], fb[11], fc[11];
 #pragma unroll
@@ -1178,7 +1181,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
         uint32_t *bq = bm + (q & 1) * L.bmw;
         if (sl > 0 && q >= 2 && !mbar_wait(&freed[q & 1], ((q >> 1) - 1) & 1)) ok = false;
         ok = __all_sync(0xffffffffu, ok);
-#pragma unroll
+#pragma unroll 3
         for (int vi = 0; vi < RS; ++vi) {
             const int slot = j % NS2;
             if (ok && !mbar_wait(&full[slot], (j / NS2) & 1)) ok = false;
@@ -1243,7 +1246,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
                     const int i = vi >= 3 ? vi - 3 : 0;
                     const uint32_t sq = combine(pprev, p);
                     if (sl > 0) {
-                        const uint32_t sv8 = survivors8(combine(sq, st[i])) & vmask;
+                        const uint32_t sv8 = survivors8(combine(sq, sst[i * NC])) & vmask;
                         if (sv8) {
                             const int idx = i * nx + x0;
                             atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
@@ -1251,12 +1254,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
                             if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
                         }
                     }
-                    st[i] = sq;
+                    sst[i * NC] = sq;
                 }
                 if (u == ny - 1 && vi >= 2 && vi - 2 < RY2) {
                     const int i = vi >= 2 ? vi - 2 : 0;
                     if (sl > 0) {
-                        const uint32_t sv8 = survivors8(combine(p, st[i])) & vmask;
+                        const uint32_t sv8 = survivors8(combine(p, sst[i * NC])) & vmask;
                         if (sv8) {
                             const int idx = i * nx + x0;
                             atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
@@ -1264,7 +1267,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
                             if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
                         }
                     }
-                    st[i] = p;
+                    sst[i * NC] = p;
                 }
                 pprev = p;
             }
@@ -1292,7 +1295,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
 #pragma unroll
             for (int i = 0; i < RY2; ++i) {
                 if (y0 + i < ny) {
-                    const uint32_t sv8 = survivors8(st[i]) & vmask;
+                    const uint32_t sv8 = survivors8(sst[i * NC]) & vmask;
                     if (sv8) {
                         const int idx = i * nx + x0;
                         atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
@@ -1310,7 +1313,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     if (ok && B.st_mode) {
         // the last slice's cube-row words for the next push
 #pragma unroll
-        for (int i = 0; i < RY2; ++i) B.st_out[st_base + (long long)i * NC] = st[i];
+        for (int i = 0; i < RY2; ++i) B.st_out[st_base + (long long)i * NC] = sst[i * NC];
     }
     if (!ok) atomicOr(status, ST_TIMEOUT);
     if (bad & (EXACT ? 1u : 0xFF800000u)) atomicOr(status, EXACT ? ST_RANGE : ST_WIDE);
