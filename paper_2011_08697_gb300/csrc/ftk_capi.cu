@@ -582,7 +582,7 @@ ftk_status ftk_plan_describe(ftk_plan *pl, ftk_plan_desc *d) {
     if (!pl || !d) return fail(FTK_ERR_ARG, "NULL argument");
     std::memset(d, 0, sizeof(*d));
     d->detect_variant = pl->variant;
-    d->kernels_per_execute = pl->variant != VAR_TILE ? 8 : 5;
+    d->kernels_per_execute = pl->variant == VAR_TILE ? 5 : pl->ndim == 3 ? 9 : 8;
     d->rows_per_unit = pl->B.ry;
     d->slices_per_unit = pl->B.tc;
     d->detect_units = (int64_t)pl->B.ntc * pl->B.nyb * pl->B.nzb;

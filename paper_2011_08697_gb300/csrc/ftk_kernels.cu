@@ -464,6 +464,70 @@ __device__ __forceinline__ float i128_to_float(__int128 v) {
     return neg ? -r : r;
 }
 
+// Morse index of the symmetric 3x3 S from an FP32 evaluation, when its
+// signs are certain (the index is unchanged by a positive scale of S, so the
+// weights come in scaled by a power of two into [1, 2) for the largest).
+// Sd = S evaluated in FP32 from the scaled weights and the exact int64
+// Hessian sums: conversion, product and a 4-term sum stay within
+// 9u sum_k |w_k h_k| of the exact scaled entry, u = 2^-24; denormal
+// rounding adds at most 2^-100 absolutely.  Ad = sum_k |w_k h_k| in FP32.
+// With e = 16u Ad + 2^-90 bounding each entry's error and M = |Sd| + e
+// bounding each exact entry, the errors of tr, m2 and det are bounded by the
+// change of each monomial under the entry perturbations (prod M - prod |Sd|)
+// plus the rounding of their evaluation.  Returns false (the caller decides
+// exactly) unless every invariant exceeds twice its bound.
+__device__ __forceinline__ bool morse_filter3(const float (&Sd)[3][3], const float (&Ad)[3][3], int &morse) {
+    const float u = 5.9604644775390625e-8f;   // 2^-24
+    const float floor_abs = 8.0779356e-28f;   // 2^-90
+    float e[3][3], M[3][3], a[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            e[i][j] = 16.0f * u * Ad[i][j] + floor_abs;
+            a[i][j] = fabsf(Sd[i][j]);
+            M[i][j] = a[i][j] + e[i][j];
+        }
+    const float tr = Sd[0][0] + Sd[1][1] + Sd[2][2];
+    const float err_tr = (e[0][0] + e[1][1] + e[2][2]) + 4.0f * u * (M[0][0] + M[1][1] + M[2][2]);
+    float m2 = 0.0f, err_m2 = 0.0f, mag_m2 = 0.0f;
+    const int P[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int i = P[q][0], j = P[q][1];
+        m2 += Sd[i][i] * Sd[j][j] - Sd[i][j] * Sd[i][j];
+        err_m2 += (M[i][i] * M[j][j] - a[i][i] * a[j][j]) + (M[i][j] * M[i][j] - a[i][j] * a[i][j]);
+        mag_m2 += M[i][i] * M[j][j] + M[i][j] * M[i][j];
+    }
+    err_m2 += 8.0f * u * mag_m2;
+    const float c0 = Sd[1][1] * Sd[2][2] - Sd[1][2] * Sd[2][1];
+    const float c1 = Sd[1][0] * Sd[2][2] - Sd[1][2] * Sd[2][0];
+    const float c2 = Sd[1][0] * Sd[2][1] - Sd[1][1] * Sd[2][0];
+    const float det = Sd[0][0] * c0 - Sd[0][1] * c1 + Sd[0][2] * c2;
+    // the six monomials of det: perturbation bound and magnitude
+    const int pm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    float err_det = 0.0f, mag_det = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float Mp = M[0][pm[q][0]] * M[1][pm[q][1]] * M[2][pm[q][2]];
+        const float ap = a[0][pm[q][0]] * a[1][pm[q][1]] * a[2][pm[q][2]];
+        err_det += Mp - ap;
+        mag_det += Mp;
+    }
+    err_det += 12.0f * u * mag_det;
+    // every comparison is false for a non-finite value: then the exact path
+    if (!(fabsf(tr) > 2.0f * err_tr && fabsf(m2) > 2.0f * err_m2 && fabsf(det) > 2.0f * err_det)) return false;
+    const int s[3] = {tr > 0.0f ? 1 : -1, m2 > 0.0f ? 1 : -1, det > 0.0f ? 1 : -1};
+    int prev = 1, changes = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (s[i] != prev) ++changes;
+        prev = s[i];
+    }
+    morse = changes;
+    return true;
+}
+
 // coordinates (x, y, z, t) of vertex id g
 __device__ __forceinline__ Pt decode_vertex(const Field &F, long long g) {
     Pt p;
@@ -562,7 +626,12 @@ __device__ int cmp_prod128(__int128 a, __int128 b, __int128 c, __int128 d) {
     return s1 > 0 ? mag : -mag;   // both products positive, or both negative
 }
 
-template <int N>
+constexpr int8_t MORSE_PENDING = -2;   // 3D: left to the exact classification
+
+// location and Morse index of one puncture.  In 3D with FILTER_ONLY the
+// index comes from the floating-point filter, or MORSE_PENDING when the
+// filter cannot certify it (the exact evaluation then runs separately).
+template <int N, bool FILTER_ONLY = false>
 __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8_t &morse) {
     constexpr int BW = N == 2 ? 8 : 16;
     int tt;
@@ -628,6 +697,91 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
         const __int128 tr = S00 + S11;
         morse = (int8_t)(d < 0 ? 1 : d > 0 ? (tr < 0 ? 2 : 0) : -1);
         return;
+    }
+    {
+        // S exactly in int128 (|w| < 2^93, |h| < 2^34) and in FP32 from
+        // weights scaled by one power of two (the index is unchanged by a
+        // positive scale).  Small S (every entry < 2^40, e.g. near-flat,
+        // quantised regions): tr, m2 and det exactly in int128 (products
+        // < 2^121).  Otherwise the FP32 filter, and the multiword evaluation
+        // below only when the filter cannot certify every sign.
+        __int128 wmax = 0;
+        for (int k = 0; k <= N; ++k) {
+            const __int128 w = D[k] < 0 ? -D[k] : D[k];
+            if (w > wmax) wmax = w;
+        }
+        const unsigned long long whi = (unsigned long long)(wmax >> 64), wlo = (unsigned long long)wmax;
+        const int wbits = whi ? 128 - __clzll((long long)whi) : (wlo ? 64 - __clzll((long long)wlo) : 1);
+        __int128 Si[3][3];
+        float Sd[3][3], Ad[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                Si[a][b] = 0;
+                Sd[a][b] = Ad[a][b] = 0.0f;
+            }
+        for (int k = 0; k <= N; ++k) {
+            const __int128 w = sg < 0 ? -D[k] : D[k];
+            const float wd = ldexpf(i128_to_float(w), 1 - wbits), aw = fabsf(wd);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = a; b < 3; ++b) {
+                    const long long h = a == b ? 2 * hess_global(F, v[k], a, a)
+                                               : hess_global(F, v[k], a, b) + hess_global(F, v[k], b, a);
+                    Si[a][b] += w * (__int128)h;
+                    const float hd = (float)h;
+                    Sd[a][b] = __fmaf_rn(wd, hd, Sd[a][b]);
+                    Ad[a][b] = __fmaf_rn(aw, fabsf(hd), Ad[a][b]);
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < a; ++b) {
+                Si[a][b] = Si[b][a];
+                Sd[a][b] = Sd[b][a];
+                Ad[a][b] = Ad[b][a];
+            }
+        const __int128 LIM = (__int128)1 << 40;
+        // the int128 sums cannot wrap: 4 terms of |w| < 2^wbits, |h| < 2^35
+        bool small = wbits <= 88;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a; b < 3; ++b) small &= Si[a][b] < LIM && Si[a][b] > -LIM;
+        if (small) {
+            const __int128 tr = Si[0][0] + Si[1][1] + Si[2][2];
+            const __int128 m2 = Si[0][0] * Si[1][1] - Si[0][1] * Si[0][1] + Si[0][0] * Si[2][2] -
+                                Si[0][2] * Si[0][2] + Si[1][1] * Si[2][2] - Si[1][2] * Si[1][2];
+            const __int128 det = Si[0][0] * (Si[1][1] * Si[2][2] - Si[1][2] * Si[1][2]) -
+                                 Si[0][1] * (Si[0][1] * Si[2][2] - Si[1][2] * Si[0][2]) +
+                                 Si[0][2] * (Si[0][1] * Si[1][2] - Si[1][1] * Si[0][2]);
+            if (det == 0) {
+                morse = -1;
+                return;
+            }
+            const int sgn3[3] = {sgn128(tr), sgn128(m2), sgn128(det)};
+            int prev = 1, changes = 0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                if (sgn3[i] != 0) {
+                    if (sgn3[i] != prev) ++changes;
+                    prev = sgn3[i];
+                }
+            morse = (int8_t)changes;
+            return;
+        }
+        int m = 0;
+        if (morse_filter3(Sd, Ad, m)) {
+            morse = (int8_t)m;
+            return;
+        }
+        if (FILTER_ONLY) {
+            morse = MORSE_PENDING;
+            return;
+        }
     }
     BigInt<BW> S[N][N];
 #pragma unroll
@@ -1491,8 +1645,27 @@ __global__ void __launch_bounds__(NT) k_locate(Field F, Workspace W) {
          i += (long long)gridDim.x * blockDim.x) {
         float4 o;
         int8_t mo;
-        locate_classify<N>(F, W.face[i], o, mo);
+        locate_classify<N, N == 3>(F, W.face[i], o, mo);
         W.off[i] = o;
+        W.morse[i] = mo;
+        if (N == 3 && mo == MORSE_PENDING) {
+            // W.label is free until k_label: the list of pending punctures
+            const unsigned long long q = atomicAdd(&W.ctr->pending, 1ull);
+            W.label[q] = i;
+        }
+    }
+}
+
+// 3D: exact (multiword) Morse index of the punctures the filter left
+template <int N>
+__global__ void __launch_bounds__(NT) k_classify_exact(Field F, Workspace W) {
+    if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
+    const long long n = (long long)W.ctr->pending;
+    for (long long q = blockIdx.x * (long long)NT + threadIdx.x; q < n; q += (long long)gridDim.x * NT) {
+        const long long i = W.label[q];
+        float4 o;
+        int8_t mo;
+        locate_classify<N, false>(F, W.face[i], o, mo);
         W.morse[i] = mo;
     }
 }
@@ -1942,8 +2115,12 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
     if (stream) {
         k_emit<N><<<sg, NT, 0, s>>>(F, B, W);
         // few, long-running threads in 3D: small blocks spread them over every SM
-        if constexpr (N == 3) k_locate<N><<<sg * 2, 64, 0, s>>>(F, W);
-        else k_locate<N><<<sg, NT, 0, s>>>(F, W);
+        if constexpr (N == 3) {
+            k_locate<N><<<sg * 2, 64, 0, s>>>(F, W);
+            k_classify_exact<N><<<sg, NT, 0, s>>>(F, W);
+        } else {
+            k_locate<N><<<sg, NT, 0, s>>>(F, W);
+        }
     } else {
         k_finalize<N><<<sg, NT, 0, s>>>(F, B, W);
     }

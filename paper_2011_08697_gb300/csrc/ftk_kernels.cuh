@@ -23,6 +23,7 @@ struct RunCounters {
     unsigned long long staged;     // punctures written (or attempted) to staging
     long long punctures;           // final count P (set by the scan kernel)
     unsigned long long survivors;  // spacetime cubes that survived the sign cull
+    unsigned long long pending;    // 3D punctures left to the exact classification
 };
 
 // Division by a fixed divisor d for numerators n < 2^31: with
