@@ -610,7 +610,7 @@ def serve_arm(args):
         for k in range(3):
             st.push(f3[k])
         oracle_ok = _oracle_check(st.close(), f3)
-    launches_per_push = 8 + 4      # the two-slice pipeline + the stream merge
+    launches_per_push = 1 + 8 + 8  # slice copy, the two-slice pipeline, the stream merge
     if rank == 0:
         line = {
             "metric": "timesteps/s", "value": served_steps_s, "unit": "timesteps/s", "n_gpus": world,
