@@ -77,6 +77,8 @@ void free_workspace(Workspace &W) {
     cudaFree(W.surv_off);
     cudaFree(W.seg_scnt);
     cudaFree(W.seg_sstage);
+    cudaFree(W.tile);
+    cudaFree(W.seg_tile);
     std::memset(&W, 0, sizeof(W));
 }
 
@@ -84,10 +86,15 @@ ftk_status alloc_survivors(Workspace &W, long long scap) {
     cudaFree(W.surv); W.surv = nullptr;
     cudaFree(W.surv_mask); W.surv_mask = nullptr;
     cudaFree(W.surv_off); W.surv_off = nullptr;
+    cudaFree(W.tile); W.tile = nullptr;
     W.scap = 0;
+    const long long ntile = (scap + LB_TILE - 1) / LB_TILE;
     if (cudaMalloc(&W.surv, scap * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&W.surv_mask, scap * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&W.surv_off, scap * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&W.surv_off, scap * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&W.tile, ntile * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(W.tile, 0, ntile * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {   // the plan's streams do not wait on the legacy stream
         cudaGetLastError();
         return fail(FTK_ERR_NOMEM, "device allocation of the survivor arrays failed");
     }
@@ -500,8 +507,12 @@ ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_
                         : std::max<long long>(1 << 16, std::min<long long>(pl->nverts / 32, 1LL << 26));
     s = alloc_capacity(W, cap);
     if (s == FTK_OK && pl->variant != VAR_TILE) {
+        const long long nst = (W.nseg + SEG_TILE - 1) / SEG_TILE;
         if (cudaMalloc(&W.seg_scnt, W.nseg * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&W.seg_sstage, W.nseg * sizeof(long long)) != cudaSuccess) {
+            cudaMalloc(&W.seg_sstage, W.nseg * sizeof(long long)) != cudaSuccess ||
+            cudaMalloc(&W.seg_tile, nst * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMemset(W.seg_tile, 0, nst * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess) {
             cudaGetLastError();
             s = fail(FTK_ERR_NOMEM, "device allocation failed");
         } else {

@@ -71,6 +71,65 @@ struct MeshTables {
     }
 };
 
+// Cells ((N+1)-simplices) of one unit cube, one per order in which the axes
+// are stepped: chain m_0 < m_1 < .. < m_N = FULL from the base vertex b.  Of
+// a cell's N+2 sides, the N+1 through b are faces based at b (drop vertex
+// b + m_k: chain without m_k); the side opposite b is based at b + m_0 with
+// chain (m_1 ^ m_0, .., m_N ^ m_0), i.e. a face of the next cube along the
+// first step's axis.
+template <int N>
+struct CellTables {
+    using M = MeshDims<N>;
+    // cells are ordered by the axis of their first step: cells
+    // [a C / (N+1), (a+1) C / (N+1)) step first along axis a
+    unsigned long long own[M::C];   // bit set of the types of the sides through b
+    unsigned long long own_axis[M::D];  // union of own[] over the cells of one first axis
+    uint8_t side[M::C][N + 1];      // those types, side k dropping vertex b + m_k
+    uint8_t far[M::C];              // type of the side opposite b
+    uint8_t axis[M::C];             // axis of the first step
+
+    __host__ __device__ constexpr CellTables() : own{}, own_axis{}, side{}, far{}, axis{} {
+        const MeshTables<N> mt;
+        constexpr int D = M::D;
+        int tuples = 1;
+        for (int i = 0; i < D; ++i) tuples *= D;
+        int cnt = 0;
+        for (int code = 0; code < tuples; ++code) {
+            int p[D] = {};
+            int c = code, used = 0;
+            bool ok = true;
+            for (int j = D - 1; j >= 0; --j) {   // p[0] is the slowest digit
+                p[j] = c % D;
+                c /= D;
+                if ((used >> p[j]) & 1) ok = false;
+                used |= 1 << p[j];
+            }
+            if (!ok) continue;
+            int m[D] = {};
+            int acc = 0;
+            for (int j = 0; j < D; ++j) {
+                acc |= 1 << p[j];
+                m[j] = acc;
+            }
+            unsigned long long bits = 0;
+            for (int k = 0; k < D; ++k) {
+                int key = 0, w = 0;
+                for (int j = 0; j < D; ++j)
+                    if (j != k) key |= m[j] << (4 * w++);
+                side[cnt][k] = mt.lookup[key];
+                bits |= 1ull << mt.lookup[key];
+            }
+            own[cnt] = bits;
+            own_axis[p[0]] |= bits;
+            int key = 0;
+            for (int j = 1; j < D; ++j) key |= (m[j] ^ m[0]) << (4 * (j - 1));
+            far[cnt] = mt.lookup[key];
+            axis[cnt] = (uint8_t)p[0];
+            ++cnt;
+        }
+    }
+};
+
 template <int N>
 __host__ __device__ constexpr int chain_key(const int (&m)[N]) {
     int key = 0;
@@ -78,11 +137,6 @@ __host__ __device__ constexpr int chain_key(const int (&m)[N]) {
     return key;
 }
 
-// ----------------------------------------------------------------------------
-// SoS term table: the perturbed-entry sets (partial permutations) of an N x N
-// determinant in increasing exponent order, each with the permutations that
-// contain it.  Bit c*N + r of `mask` marks entry (row r, column c).
-// ----------------------------------------------------------------------------
 // ----------------------------------------------------------------------------
 // Exact determinants and the SoS sign
 // ----------------------------------------------------------------------------

@@ -1,25 +1,36 @@
 // CUDA kernels of the exact critical-point tracking pipeline (sm_103a).
 //
-// Pipeline of one field (paper Algorithm 1, left column, plus Sec. 4.1/4.3):
-//   k_detect   dense, HBM-bound: per unit (y-block x z-block x time chunk)
-//              march through the time slices; per slice load the tile,
-//              quantise F = rint(f 2^S), integer central-difference gradient,
-//              2N sign bits per vertex; per spacetime cube AND the sign bits
-//              of its corners -- a component that is < 0 on every corner, or
-//              >= 0 on every corner, rules out every face owned by the cube,
-//              exactly: the symbolic perturbation is infinitesimal and adds a
-//              positive term to a zero component.  Surviving
-//              cubes (rare) run the exact SoS predicate on each of their
-//              faces; punctured faces are compacted in face-id order per
-//              segment (t, z, y-block).
-//   k_scan     exclusive scan of the per-segment counts (segment order is
-//              face-id order), total count.
-//   k_finalize per puncture: its rank in face-id order, location from the
-//              barycentric coordinates of Eq. (1) (FP32), Morse index of the
-//              interpolated Hessian (exact multiword integers).
-//   k_link     per puncture: its <= 2 spacetime cells, the other punctured
-//              side of each (binary search), lock-free union-find.
-//   k_label    label = smallest face id of the component; pack records.
+// Two forms of paper Algorithm 1 (left column, with Sec. 4.1 / 4.3).
+//
+// Streaming variants (the default; the dense pass is in k_detect2_stream
+// here and k_detect3_stream in ftk_detect3.cu):
+//   detect       dense, HBM-bound: stream the field once, quantise
+//                F = rint(f 2^S), integer central-difference gradient, and
+//                cull every spacetime cube exactly -- a gradient component
+//                that is < 0 on every corner, or >= 0 on every corner, rules
+//                out every face owned by the cube (the symbolic perturbation
+//                is infinitesimal and adds a positive term to a zero
+//                component).  Surviving cubes are listed per segment
+//                (t, z, y-block) in vertex order.
+//   k_survive_eval  exact SoS predicate on every face of a surviving cube:
+//                a mask of punctured face types.
+//   k_survive_scan  global exclusive scan of the masks' popcounts.
+//   k_seg_scan   segment totals and offsets in face-id order (look-back scan).
+//   k_emit       punctured faces written at their sorted positions.
+//   k_locate     location from the barycentric coordinates of Eq. (1) (FP32)
+//                and Morse index of the interpolated Hessian (exact;
+//                floating-point filters decide where they can certify).
+//   k_link_survivors  per surviving cube: the cells it holds, each joining
+//                its two punctured sides (lock-free union-find).
+//   k_label      label = smallest face id of the component; pack records.
+//
+// Tiled variant (a fallback for rows the streaming kernels do not take):
+//   k_detect     per unit: cull, exact predicate and compaction in one kernel.
+//   k_scan       exclusive scan of the per-segment counts.
+//   k_finalize   per puncture: rank, location, Morse index.
+//   k_link       per puncture: its <= 2 cells, the other punctured side of
+//                each (binary search), union-find.
+//   k_label      as above.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -36,6 +47,11 @@ __constant__ MeshTables<3> c_mesh3 = MeshTables<3>();
 template <int N> __device__ __forceinline__ const MeshTables<N> &mesh();
 template <> __device__ __forceinline__ const MeshTables<2> &mesh<2>() { return c_mesh2; }
 template <> __device__ __forceinline__ const MeshTables<3> &mesh<3>() { return c_mesh3; }
+__constant__ CellTables<2> c_cell2 = CellTables<2>();
+__constant__ CellTables<3> c_cell3 = CellTables<3>();
+template <int N> __device__ __forceinline__ const CellTables<N> &cells();
+template <> __device__ __forceinline__ const CellTables<2> &cells<2>() { return c_cell2; }
+template <> __device__ __forceinline__ const CellTables<3> &cells<3>() { return c_cell3; }
 
 constexpr int NT = 256;              // threads per CTA of every kernel here
 constexpr float RANGE_LIMIT = 268435456.0f;   // 2^28
@@ -106,6 +122,54 @@ __device__ __forceinline__ T block_excl_scan(T v, T *red, T &total) {
     total = red[NT / 32 - 1];
     __syncthreads();
     return before + x - v;
+}
+
+// ----------------------------------------------------------------------------
+// Single-pass scan across tiles by decoupled look-back (Merrill & Garland,
+// "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016).  A tile
+// publishes its total as soon as it is known, then walks back over its
+// predecessors 32 at a time, summing their totals until one of them has
+// published its inclusive prefix.  Tiles are numbered in the order blocks
+// claim them, so every predecessor belongs to a running or finished block.
+// State word: bits 62-63 = 1 (total) or 2 (inclusive prefix), bits 0-61 =
+// the value; 0 = nothing yet.  The payload travels in the flag's own word,
+// so plain volatile accesses suffice.  Called by one full warp; returns the
+// exclusive prefix of tile t on every lane.
+// ----------------------------------------------------------------------------
+constexpr unsigned long long LB_AGG = 1ull << 62, LB_INC = 2ull << 62, LB_VAL = (1ull << 62) - 1;
+
+__device__ long long warp_lookback(unsigned long long *tile_state, long long t, long long total,
+                                   unsigned *status) {
+    volatile unsigned long long *st = tile_state;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) st[t] = (t == 0 ? LB_INC : LB_AGG) | (unsigned long long)total;
+    if (t == 0) return 0;
+    long long ex = 0;
+    long long hi = t - 1;   // highest predecessor not yet summed
+    const long long t0 = clock64();
+    while (true) {
+        const long long j = hi - lane;
+        unsigned long long v = LB_INC;   // before tile 0: prefix 0
+        if (j >= 0) v = st[j];
+        if (__any_sync(0xffffffffu, (v >> 62) == 0)) {
+            if (clock64() - t0 > WAIT_CYCLES) {
+                if (lane == 0) atomicOr(status, ST_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        const unsigned inc = __ballot_sync(0xffffffffu, (v >> 62) == 2);
+        const int stop = inc ? __ffs(inc) - 1 : 31;
+        long long x = lane <= stop ? (long long)(v & LB_VAL) : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        ex += x;
+        if (inc) break;
+        hi -= 32;
+    }
+    if (lane == 0) st[t] = LB_INC | (unsigned long long)(ex + total);
+    return ex;
 }
 
 // ----------------------------------------------------------------------------
@@ -386,10 +450,9 @@ __global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W)
 // ----------------------------------------------------------------------------
 // Scan of per-segment counts (one CTA)
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_scan(Workspace W, int stream_mode) {
+__global__ void __launch_bounds__(NT) k_scan(Workspace W) {
     __shared__ long long red[NT / 32 + 1];
     constexpr int PER = 16;
-    if (stream_mode && (W.ctr->status & ST_SOVERFLOW)) return;
     long long run = 0;
     for (long long b0 = 0; b0 < W.nseg; b0 += (long long)NT * PER) {
         const long long i0 = b0 + (long long)threadIdx.x * PER;
@@ -411,13 +474,82 @@ __global__ void __launch_bounds__(NT) k_scan(Workspace W, int stream_mode) {
         }
         run += tot;
     }
-    if (threadIdx.x == 0) {
-        W.ctr->punctures = run;
-        if (stream_mode) {
-            // the streaming variant writes punctures straight to their sorted slots
-            W.ctr->staged = (unsigned long long)run;
-            if (run > W.cap) atomicOr(&W.ctr->status, ST_OVERFLOW);
+    if (threadIdx.x == 0) W.ctr->punctures = run;
+}
+
+// Streaming variants: scan over the segments in face-id order, many blocks
+// with decoupled look-back (tiles of SEG_TILE segments).  A segment's count
+// is the difference of surv_off across its survivor run, and seg_off[seg] is
+// stored minus surv_off at the run's start, so that seg_off[seg] +
+// surv_off[s] is the sorted position of survivor s's first puncture.  The
+// survivor scan's tile states are cleared here for the next run (that scan
+// has finished); the segment scan's own are cleared by k_emit.
+__global__ void __launch_bounds__(NT) k_seg_scan(Workspace W) {
+    constexpr int PER = SEG_TILE / NT;
+    __shared__ long long red[NT / 32 + 1];
+    __shared__ long long sh[2];
+    if (W.ctr->status & ST_SOVERFLOW) return;
+    const long long ns = (long long)W.ctr->survivors;
+    const long long total = W.ctr->surv_total;
+    const long long nst = (ns + LB_TILE - 1) / LB_TILE;
+    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < nst; t += (long long)gridDim.x * NT)
+        W.tile[t] = 0ull;
+    while (true) {
+        if (threadIdx.x == 0) sh[1] = (long long)atomicAdd(&W.ctr->seg_tiles, 1ull);
+        __syncthreads();
+        const long long t = sh[1];
+        if (t * SEG_TILE >= W.nseg) break;
+        const long long i0 = t * SEG_TILE + (long long)threadIdx.x * PER;
+        // loads are unconditional (clamped indices) so that each round of
+        // them is issued at once: the counts, then the offsets they point at
+        int n[PER];
+        long long a[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const long long i = i0 + j < W.nseg ? i0 + j : 0;
+            n[j] = i0 + j < W.nseg ? W.seg_scnt[i] : 0;
+            a[j] = W.seg_sstage[i];
         }
+        int v1[PER], v2[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const long long e = a[j] + n[j];
+            v1[j] = W.surv_off[n[j] > 0 ? a[j] : 0];
+            v2[j] = W.surv_off[n[j] > 0 && e < ns ? e : 0];
+        }
+        long long loc[PER], first[PER];
+        long long s = 0;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const long long e = a[j] + n[j];
+            first[j] = n[j] > 0 ? v1[j] : 0;
+            loc[j] = n[j] > 0 ? (e < ns ? (long long)v2[j] : total) - first[j] : 0;
+            s += loc[j];
+        }
+        long long tot;
+        long long ex = block_excl_scan<long long>(s, red, tot);
+        if (threadIdx.x < 32) {
+            const long long before = warp_lookback(W.seg_tile, t, tot, &W.ctr->status);
+            if (threadIdx.x == 0) {
+                sh[0] = before;
+                if ((t + 1) * SEG_TILE >= W.nseg) {
+                    // the last tile: the puncture count; punctures go straight
+                    // to their sorted slots
+                    const long long run = before + tot;
+                    W.ctr->punctures = run;
+                    W.ctr->staged = (unsigned long long)run;
+                    if (run > W.cap) atomicOr(&W.ctr->status, ST_OVERFLOW);
+                }
+            }
+        }
+        __syncthreads();
+        ex += sh[0];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            if (i0 + j < W.nseg) W.seg_off[i0 + j] = ex - first[j];
+            ex += loc[j];
+        }
+        __syncthreads();
     }
 }
 
@@ -426,34 +558,97 @@ __global__ void __launch_bounds__(NT) k_scan(Workspace W, int stream_mode) {
 // ----------------------------------------------------------------------------
 struct Pt { int c[4]; };   // x, y, z, t (z = 0 in 2D)
 
-__device__ __forceinline__ int qload(const Field &F, int x, int y, int z, int t) {
-    const long long idx = (((long long)t * F.nz + z) * F.ny + y) * F.pitch + x;
-    const float v = __ldg(F.f + idx) * F.scale;
+__device__ __forceinline__ int ext_of(const Field &F, int a) { return a == 0 ? F.nx : a == 1 ? F.ny : F.nz; }
+
+// element offset of grid point p in the (row-padded) field, and the element
+// stride of axis a (0 = x, 1 = y, 2 = z, 3 = t): samples around a point are
+// addressed from its offset, not recomputed from coordinates
+__device__ __forceinline__ long long vindex(const Field &F, const Pt &p) {
+    return (((long long)p.c[3] * F.nz + p.c[2]) * F.ny + p.c[1]) * F.pitch + p.c[0];
+}
+__device__ __forceinline__ long long vstride(const Field &F, int a) {
+    return a == 0 ? 1LL : a == 1 ? (long long)F.pitch : a == 2 ? (long long)F.ny * F.pitch
+                                                            : (long long)F.nz * F.ny * F.pitch;
+}
+// quantised sample rint(f 2^S) at element i (0 outside the exact range,
+// which the dense pass reports)
+__device__ __forceinline__ int qat(const Field &F, long long i) {
+    const float v = __ldg(F.f + i) * F.scale;
     return fabsf(v) <= RANGE_LIMIT ? __float2int_rn(v) : 0;
 }
 
-__device__ __forceinline__ int ext_of(const Field &F, int a) { return a == 0 ? F.nx : a == 1 ? F.ny : F.nz; }
-
-// gradient component a (spatial axis 0 = x, 1 = y, 2 = z) at point p
-__device__ int grad_global(const Field &F, Pt p, int a) {
+// gradient component a (spatial axis 0 = x, 1 = y, 2 = z) at point p of
+// element offset ip: central difference f[p + e_a] - f[p - e_a], one-sided
+// and doubled at either end of the axis, 2 (f[p + e_a] - f[p]) or
+// 2 (f[p] - f[p - e_a]); equivalently, with the neighbours clamped into the
+// grid, m_a (f[hi_a] - f[lo_a]) where m_a = 2 at an end, else 1.  a must be a
+// compile-time constant after unrolling (p.c[a]).
+__device__ __forceinline__ int grad_at(const Field &F, const Pt &p, long long ip, int a) {
     const int n = ext_of(F, a);
-    Pt lo = p, hi = p;
-    if (p.c[a] == 0) { hi.c[a] = 1; return 2 * (qload(F, hi.c[0], hi.c[1], hi.c[2], hi.c[3]) - qload(F, p.c[0], p.c[1], p.c[2], p.c[3])); }
-    if (p.c[a] == n - 1) { lo.c[a] = n - 2; return 2 * (qload(F, p.c[0], p.c[1], p.c[2], p.c[3]) - qload(F, lo.c[0], lo.c[1], lo.c[2], lo.c[3])); }
-    lo.c[a] -= 1;
-    hi.c[a] += 1;
-    return qload(F, hi.c[0], hi.c[1], hi.c[2], hi.c[3]) - qload(F, lo.c[0], lo.c[1], lo.c[2], lo.c[3]);
+    const long long st = vstride(F, a);
+    const long long lo = p.c[a] > 0 ? ip - st : ip;
+    const long long hi = p.c[a] + 1 < n ? ip + st : ip;
+    const int m = (p.c[a] == 0 || p.c[a] == n - 1) ? 2 : 1;
+    return m * (qat(F, hi) - qat(F, lo));
 }
 
-// Hessian entry H_ab = difference of G_a along axis b (same boundary rule)
-__device__ long long hess_global(const Field &F, Pt p, int a, int b) {
-    const int n = ext_of(F, b);
-    Pt lo = p, hi = p;
-    if (p.c[b] == 0) { hi.c[b] = 1; return 2LL * ((long long)grad_global(F, hi, a) - grad_global(F, p, a)); }
-    if (p.c[b] == n - 1) { lo.c[b] = n - 2; return 2LL * ((long long)grad_global(F, p, a) - grad_global(F, lo, a)); }
-    lo.c[b] -= 1;
-    hi.c[b] += 1;
-    return (long long)grad_global(F, hi, a) - grad_global(F, lo, a);
+// vertex-id step of axis a (0 = x, 1 = y, 2 = z in 3D, N = t) in the
+// unpadded vertex numbering
+template <int N>
+__device__ __forceinline__ long long vstride_key(const Field &F, int a) {
+    return a == 0 ? 1LL : a == 1 ? (long long)F.nx : a == N ? (long long)F.nx * F.ny * F.nz
+                                                            : (long long)F.nx * F.ny;
+}
+
+// offset of vertex b + mask m from vertex b (axis N of m is time)
+template <int N>
+__device__ __forceinline__ long long mask_offset(const Field &F, int m) {
+    long long o = (m & 1) + ((m >> 1) & 1) * (long long)F.pitch + ((m >> N) & 1) * vstride(F, 3);
+    if (N == 3) o += ((m >> 2) & 1) * vstride(F, 2);
+    return o;
+}
+
+// Hessian entry H_ab = difference of G_a along axis b with the gradient's
+// boundary rule.  hess_sym returns every HS_ab = H_ab + H_ba at point p
+// (element offset ip) from the distinct samples they use.  Per axis a:
+// lo_a = max(p_a - 1, 0), hi_a = min(p_a + 1, n_a - 1), m_a as above, so
+// G_a = m_a (f[hi_a] - f[lo_a]) and
+//   H_aa = m_a (G_a(p : a -> hi_a) - G_a(p : a -> lo_a)),
+//   H_ab = m_a m_b (f[hi_a, hi_b] - f[lo_a, hi_b] - f[hi_a, lo_b] + f[lo_a, lo_b])  (a != b),
+// the latter symmetric because a step along b leaves m_a, lo_a, hi_a as
+// they are.  With WITH_G, G receives the gradient from the same samples.
+template <int N, bool WITH_G = false>
+__device__ void hess_sym(const Field &F, const Pt &p, long long ip, long long (&HS)[N][N], int32_t *G = nullptr) {
+    long long dlo[N], dhi[N], st[N];
+    int m[N], n[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        n[a] = ext_of(F, a);
+        st[a] = vstride(F, a);
+        dlo[a] = p.c[a] > 0 ? -st[a] : 0;
+        dhi[a] = p.c[a] + 1 < n[a] ? st[a] : 0;
+        m[a] = (p.c[a] == 0 || p.c[a] == n[a] - 1) ? 2 : 1;
+    }
+    const int f0 = qat(F, ip);
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        const int fh = qat(F, ip + dhi[a]), fl = qat(F, ip + dlo[a]);
+        if (WITH_G) G[a] = m[a] * (fh - fl);
+        const int hi = p.c[a] + 1 < n[a] ? p.c[a] + 1 : n[a] - 1;
+        const int lo = p.c[a] > 0 ? p.c[a] - 1 : 0;
+        // G_a at hi_a: samples min(hi_a + 1, n - 1) and max(hi_a - 1, 0)
+        const long long h2 = hi + 1 < n[a] ? dhi[a] + st[a] : dhi[a];
+        const int gh = (hi == n[a] - 1 ? 2 : 1) * (qat(F, ip + h2) - (hi == p.c[a] ? fl : f0));
+        const long long l2 = lo > 0 ? dlo[a] - st[a] : dlo[a];
+        const int gl = (lo == 0 ? 2 : 1) * ((lo == p.c[a] ? fh : f0) - qat(F, ip + l2));
+        HS[a][a] = 2LL * m[a] * ((long long)gh - gl);
+#pragma unroll
+        for (int b = a + 1; b < N; ++b) {
+            const long long x = (long long)qat(F, ip + dhi[a] + dhi[b]) - qat(F, ip + dlo[a] + dhi[b]) -
+                                qat(F, ip + dhi[a] + dlo[b]) + qat(F, ip + dlo[a] + dlo[b]);
+            HS[a][b] = HS[b][a] = 2LL * m[a] * m[b] * x;
+        }
+    }
 }
 
 __device__ __forceinline__ float i128_to_float(__int128 v) {
@@ -462,6 +657,40 @@ __device__ __forceinline__ float i128_to_float(__int128 v) {
     const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
     const float r = __fmaf_rn((float)hi, 18446744073709551616.0f, (float)lo);
     return neg ? -r : r;
+}
+
+// Morse index of the symmetric 2x2 S from an FP32 evaluation, when its signs
+// are certain (same error model as the 3x3 filter below: Sd from weights
+// scaled by a power of two, every entry within e = 16u Ad + 2^-90 of the
+// scaled exact value; the perturbation bound of a product of two entries is
+// M_i M_j - |Sd_i| |Sd_j| with M = |Sd| + e, plus its own rounding).
+// det S < 0: saddle (1); det S > 0: maximum (2) if tr S < 0, else minimum (0).
+__device__ __forceinline__ bool morse_filter2(const float (&Sd)[2][2], const float (&Ad)[2][2], int &morse) {
+    const float u = 5.9604644775390625e-8f;   // 2^-24
+    const float floor_abs = 8.0779356e-28f;   // 2^-90
+    float e[2][2], a[2][2], M[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            e[i][j] = 16.0f * u * Ad[i][j] + floor_abs;
+            a[i][j] = fabsf(Sd[i][j]);
+            M[i][j] = a[i][j] + e[i][j];
+        }
+    const float det = Sd[0][0] * Sd[1][1] - Sd[0][1] * Sd[0][1];
+    const float err_det = (M[0][0] * M[1][1] - a[0][0] * a[1][1]) + (M[0][1] * M[0][1] - a[0][1] * a[0][1]) +
+                          4.0f * u * (M[0][0] * M[1][1] + M[0][1] * M[0][1]);
+    // every comparison is false for a non-finite value: then the exact path
+    if (!(fabsf(det) > 2.0f * err_det)) return false;
+    if (det < 0.0f) {
+        morse = 1;
+        return true;
+    }
+    const float tr = Sd[0][0] + Sd[1][1];
+    const float err_tr = (e[0][0] + e[1][1]) + 2.0f * u * (M[0][0] + M[1][1]);
+    if (!(fabsf(tr) > 2.0f * err_tr)) return false;
+    morse = tr < 0.0f ? 2 : 0;
+    return true;
 }
 
 // Morse index of the symmetric 3x3 S from an FP32 evaluation, when its
@@ -638,13 +867,87 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
     const Pt base = decode_face<N>(F, fid, tt);
     const uint8_t *ch = mesh<N>().face[tt];
     Pt v[N + 1];
+    long long iv[N + 1];
     int32_t V[N + 1][N];
+    long long HS2[N == 2 ? 3 : 1][N][N];   // 2D: every vertex's HS from the same samples as its gradient
+    const long long ib = vindex(F, base);
 #pragma unroll
     for (int k = 0; k <= N; ++k) {
         v[k] = k == 0 ? base : add_mask<N>(base, ch[k - 1]);
+        iv[k] = k == 0 ? ib : ib + mask_offset<N>(F, ch[k - 1]);
+        if constexpr (N == 2) {
+            hess_sym<N, true>(F, v[k], iv[k], HS2[k], V[k]);
+        } else {
 #pragma unroll
-        for (int a = 0; a < N; ++a) V[k][a] = grad_global(F, v[k], a);
+            for (int a = 0; a < N; ++a) V[k][a] = grad_at(F, v[k], iv[k], a);
+        }
     }
+    if constexpr (N == 2) {
+        // |G| <= 2^30: the 2x2 determinants (< 2^61) and their sum fit in int64
+        long long D[3], Dsum = 0;
+#pragma unroll
+        for (int k = 0; k <= 2; ++k) {
+            const int j0 = k == 0 ? 1 : 0, j1 = k == 2 ? 1 : 2;
+            const long long d = (long long)V[j0][0] * V[j1][1] - (long long)V[j0][1] * V[j1][0];
+            D[k] = (k & 1) ? -d : d;
+            Dsum += D[k];
+        }
+        float mu[3];
+        if (Dsum == 0) {
+#pragma unroll
+            for (int k = 0; k <= 2; ++k) mu[k] = 1.0f / 3;
+        } else {
+            const float fd = (float)Dsum;
+#pragma unroll
+            for (int k = 0; k <= 2; ++k) mu[k] = (float)D[k] / fd;
+        }
+        float o[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int k = 1; k <= 2; ++k)
+#pragma unroll
+            for (int a = 0; a <= 2; ++a)
+                if ((ch[k - 1] >> a) & 1) o[a] += mu[k];
+        off = make_float4(o[0], o[1], 0.0f, o[2]);
+        // S = sign(D) sum_k D_k (H_k + H_k^T): FP32 filter, else exact (|w| <
+        // 2^62 and |H + H^T| < 2^34: entries in int128, det S compared in 256 bits)
+        const bool neg = Dsum < 0;
+        long long wmax = 0;
+#pragma unroll
+        for (int k = 0; k <= 2; ++k) wmax = max(wmax, D[k] < 0 ? -D[k] : D[k]);
+        const int wbits = wmax ? 64 - __clzll(wmax) : 1;
+        float Sd[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}}, Ad[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll
+        for (int k = 0; k <= 2; ++k) {
+            const float wd = ldexpf((float)(neg ? -D[k] : D[k]), 1 - wbits), aw = fabsf(wd);
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = a; b < 2; ++b) {
+                    const float hd = (float)HS2[k][a][b];
+                    Sd[a][b] = __fmaf_rn(wd, hd, Sd[a][b]);
+                    Ad[a][b] = __fmaf_rn(aw, fabsf(hd), Ad[a][b]);
+                }
+        }
+        Sd[1][0] = Sd[0][1];
+        Ad[1][0] = Ad[0][1];
+        int m = 0;
+        if (morse_filter2(Sd, Ad, m)) {
+            morse = (int8_t)m;
+            return;
+        }
+        __int128 S00 = 0, S01 = 0, S11 = 0;
+#pragma unroll
+        for (int k = 0; k <= 2; ++k) {
+            const __int128 w = neg ? -(__int128)D[k] : (__int128)D[k];
+            S00 += w * (__int128)HS2[k][0][0];
+            S11 += w * (__int128)HS2[k][1][1];
+            S01 += w * (__int128)HS2[k][0][1];
+        }
+        const int d = cmp_prod128(S00, S11, S01, S01);   // sign(S00 S11 - S01 S01)
+        const __int128 tr = S00 + S11;
+        morse = (int8_t)(d < 0 ? 1 : d > 0 ? (tr < 0 ? 2 : 0) : -1);
+        return;
+    } else {
     __int128 D[N + 1];
     __int128 Dsum = 0;
 #pragma unroll
@@ -683,21 +986,6 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
 
     // S = sign(D) sum_k D_k (H_k + H_k^T), exact
     const int sg = sgn128(Dsum);
-    if (N == 2) {
-        // |D_k| < 2^62 and |H + H^T| < 2^34: entries of S fit in int128;
-        // det S = S00 S11 - S01^2 is compared exactly in 256 bits
-        __int128 S00 = 0, S01 = 0, S11 = 0;
-        for (int k = 0; k <= N; ++k) {
-            const __int128 w = sg < 0 ? -D[k] : D[k];
-            S00 += w * (__int128)(2 * hess_global(F, v[k], 0, 0));
-            S11 += w * (__int128)(2 * hess_global(F, v[k], 1, 1));
-            S01 += w * (__int128)(hess_global(F, v[k], 0, 1) + hess_global(F, v[k], 1, 0));
-        }
-        const int d = cmp_prod128(S00, S11, S01, S01);   // sign(S00 S11 - S01 S01)
-        const __int128 tr = S00 + S11;
-        morse = (int8_t)(d < 0 ? 1 : d > 0 ? (tr < 0 ? 2 : 0) : -1);
-        return;
-    }
     {
         // S exactly in int128 (|w| < 2^93, |h| < 2^34) and in FP32 from
         // weights scaled by one power of two (the index is unchanged by a
@@ -724,12 +1012,13 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
         for (int k = 0; k <= N; ++k) {
             const __int128 w = sg < 0 ? -D[k] : D[k];
             const float wd = ldexpf(i128_to_float(w), 1 - wbits), aw = fabsf(wd);
+            long long HS[N][N];
+            hess_sym<N>(F, v[k], iv[k], HS);
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
                 for (int b = a; b < 3; ++b) {
-                    const long long h = a == b ? 2 * hess_global(F, v[k], a, a)
-                                               : hess_global(F, v[k], a, b) + hess_global(F, v[k], b, a);
+                    const long long h = HS[a][b];
                     Si[a][b] += w * (__int128)h;
                     const float hd = (float)h;
                     Sd[a][b] = __fmaf_rn(wd, hd, Sd[a][b]);
@@ -789,15 +1078,15 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
 #pragma unroll
         for (int b = 0; b < N; ++b) S[a][b] = big_from<BW>(0);
     for (int k = 0; k <= N; ++k) {
-        long long H[N][N];
-        for (int a = 0; a < N; ++a)
-            for (int b = 0; b < N; ++b) H[a][b] = hess_global(F, v[k], a, b);
+        long long HS[N][N];
+        hess_sym<N>(F, v[k], iv[k], HS);
         const __int128 w = sg < 0 ? -D[k] : D[k];
         for (int a = 0; a < N; ++a)
             for (int b = 0; b < N; ++b)
-                S[a][b] = big_add(S[a][b], big_from<BW>(w * (__int128)(H[a][b] + H[b][a])));
+                S[a][b] = big_add(S[a][b], big_from<BW>(w * (__int128)HS[a][b]));
     }
     morse = (int8_t)morse_from_S<N, BW>(S);
+    }   // N == 3
 }
 
 template <int N>
@@ -984,135 +1273,221 @@ __device__ __forceinline__ long long find_cube(const Field &F, const Blocking &B
     return (lo < hi0 && W.surv[lo] == key) ? lo : -1;
 }
 
-// Linking for the streaming variants (Algorithm 1, second loop): the same
-// cells and pairing check as k_link, but a cell's faces lie in two cubes --
-// the cell's base cube (faces without the base vertex's first step dropped)
-// and the cube one step further (the face opposite the base vertex) -- so
-// one search for the other cube's punctured-face mask resolves every side
-// of the cell, and a face's position follows from its cube's offset and mask.
+// index of `key` in the sorted run a[lo, hi), or -1: exponential search out
+// of the guess p (clamped into the run), then binary search of the bracket
+// -- a few probes when the guess is close, never more than about twice a
+// plain binary search
+__device__ __forceinline__ long long gallop_find(const long long *a, long long lo, long long hi, long long p,
+                                                 long long key) {
+    if (lo >= hi) return -1;
+    p = p < lo ? lo : p >= hi ? hi - 1 : p;
+    long long L, R;   // lower_bound(key) lies in [L, R]
+    if (a[p] < key) {
+        L = p + 1;
+        R = hi;
+        for (long long step = 1;; step <<= 1) {
+            const long long q = p + step;
+            if (q >= hi) break;
+            if (a[q] >= key) { R = q; break; }
+            L = q + 1;
+        }
+    } else {
+        L = lo;
+        R = p;
+        for (long long step = 1;; step <<= 1) {
+            const long long q = p - step;
+            if (q < lo) break;
+            if (a[q] < key) { L = q + 1; break; }
+            R = q;
+        }
+    }
+    while (L < R) {
+        const long long mid = (L + R) >> 1;
+        if (a[mid] < key) L = mid + 1;
+        else R = mid;
+    }
+    return (L < hi && a[L] == key) ? L : -1;
+}
+
+// number of cells having face type tt based at b as a side
 template <int N>
-__global__ void __launch_bounds__(NT) k_link_cubes(Field F, Blocking B, Workspace W) {
+__device__ __forceinline__ int face_cells(const Field &F, const Pt &b, int tt) {
+    constexpr int FULL = MeshDims<N>::FULL;
+    const int last = mesh<N>().face[tt][N - 1];
+    if (last == FULL) return 2;                      // inside the cube: both cells in it
+    const int a = __ffs(FULL ^ last) - 1;            // the face lies in the plane x_a = b_a
+    // selects, not a runtime index into b (which would move b to local memory)
+    const int x = a == 0 ? b.c[0] : a == 1 ? b.c[1] : a == N ? b.c[3] : b.c[2];
+    const int ext = a == N ? F.nt : ext_of(F, a);
+    return (x >= 1) + (x + 1 < ext);
+}
+
+// Linking for the streaming variants (Algorithm 1, second loop), one thread
+// per surviving cube: every cell lies in exactly one unit cube, and a cell
+// with a punctured side has one through the cube's base vertex (its sides
+// through b are faces of the cube at b; the opposite side belongs to the next
+// cube along the cell's first step, found in the survivor list).  A cell
+// with exactly two punctured sides joins them; one with any other nonzero
+// count breaks the pairing invariant.  Cells whose sides through b are all
+// unpunctured are not visited: each of them must then have no punctured side
+// at all, which the global count checks -- every punctured face lies in one
+// or two cells (one on the grid boundary), so the cells visited with two
+// punctured sides must number exactly half the sum of those counts.
+template <int N>
+__global__ void __launch_bounds__(NT, 4) k_link_survivors(Field F, Blocking B, Workspace W) {
     constexpr int D = N + 1;
     constexpr int FULL = (1 << D) - 1;
-    constexpr int T = MeshDims<N>::T;
+    constexpr int C = MeshDims<N>::C;
+    __shared__ unsigned long long red[2][NT / 32];
     if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
+    const long long ns = (long long)W.ctr->survivors;
     const long long P = W.ctr->punctures;
     unsigned *status = &W.ctr->status;
-    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
-        const long long fid = W.face[i];
-        int tt;
-        const Pt base = decode_face<N>(F, fid, tt);
-        const long long s_own = W.staging[i];
-        const unsigned long long mask_own = W.surv_mask[s_own];
-        int m[N];
-        for (int k = 0; k < N; ++k) m[k] = mesh<N>().face[tt][k];
-        Pt cb[2];
-        int cm[2][D];
-        int ncell = 0;
-        if (m[N - 1] == FULL) {
-            int prev = 0;
-            for (int j = 0; j < N; ++j) {
-                const int step = m[j] ^ prev;
-                if (__popc(step) == 2) {
-                    for (int a = 0; a < D; ++a) {
-                        if (!((step >> a) & 1)) continue;
-                        for (int q = 0; q < j; ++q) cm[ncell][q] = m[q];
-                        cm[ncell][j] = prev | (1 << a);
-                        for (int q = j; q < N; ++q) cm[ncell][q + 1] = m[q];
-                        cb[ncell] = base;
-                        ++ncell;
-                    }
-                    break;
-                }
-                prev = m[j];
+    unsigned long long pairs = 0, incid = 0;
+    // one item per (surviving cube, first-step axis a): the cells of the cube
+    // that step first along a, all of which share the next cube along a.
+    // Items are axis-major, so a warp's lanes take the same branch (a search
+    // for the next cube along y, z or t; none along x).
+    for (long long it = blockIdx.x * (long long)NT + threadIdx.x; it < ns * D; it += (long long)gridDim.x * NT) {
+        const int a = (int)(it / ns);
+        const long long s = it - (long long)a * ns;
+        const unsigned long long mo = W.surv_mask[s];
+        if (!mo || (a != 0 && !(mo & cells<N>().own_axis[a]))) continue;
+        const long long g = W.surv[s];
+        const Pt b = decode_vertex(F, g);
+        if (a == 0) {   // the item of axis 0 also counts the cube's face incidences
+            for (unsigned long long r = mo; r; r &= r - 1) incid += face_cells<N>(F, b, __ffsll((long long)r) - 1);
+            if (!(mo & cells<N>().own_axis[0])) continue;
+        }
+        int inside = 0;
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            const int slot = q == N ? 3 : q;
+            const int ext = q == N ? F.nt : ext_of(F, q);
+            if (b.c[slot] + 1 < ext) inside |= 1 << q;
+        }
+        if (inside != FULL) continue;                // a boundary cube holds no cell
+        const long long seg = segment_of_coords(b.c[1], b.c[2], b.c[3], F, B);
+        const long long pos = W.seg_off[seg] + W.surv_off[s];
+        // the next cube along axis a: its mask and first puncture's position
+        unsigned long long mf = 0;
+        long long pf = 0;
+        if (a == 0) {
+            // the next vertex id: the next survivor of the segment, if any
+            const long long e = W.seg_sstage[seg] + W.seg_scnt[seg];
+            if (s + 1 < e && W.surv[s + 1] == g + 1) {
+                mf = W.surv_mask[s + 1];
+                pf = pos + __popcll(mo);
             }
         } else {
-            const int a = __ffs(FULL ^ m[N - 1]) - 1;
-            const int ca = a == N ? 3 : a;
-            const int ext = a == N ? F.nt : (a == 0 ? F.nx : a == 1 ? F.ny : F.nz);
-            if (base.c[ca] >= 1) {
-                cb[ncell] = base;
-                cb[ncell].c[ca] -= 1;
-                cm[ncell][0] = 1 << a;
-                for (int q = 0; q < N; ++q) cm[ncell][q + 1] = m[q] | (1 << a);
-                ++ncell;
-            }
-            if (base.c[ca] + 1 < ext) {
-                cb[ncell] = base;
-                for (int q = 0; q < N; ++q) cm[ncell][q] = m[q];
-                cm[ncell][N] = FULL;
-                ++ncell;
+            Pt q = b;   // b + e_a, without a runtime index into q
+            q.c[1] += a == 1;
+            q.c[2] += N == 3 && a == 2;
+            q.c[3] += a == N;
+            const long long sq = segment_of_coords(q.c[1], q.c[2], q.c[3], F, B);
+            const long long key = g + vstride_key<N>(F, a);
+            const long long lo = W.seg_sstage[sq], n = W.seg_scnt[sq];
+            // guess: the next row of the same segment lies about a row's
+            // share of the segment further on; another segment (next z, t
+            // or y-block) holds the cube at about the same relative rank
+            const long long own_lo = W.seg_sstage[seg], own_n = W.seg_scnt[seg];
+            const long long guess = sq == seg ? s + (own_n + B.ry - 1) / B.ry
+                                              : lo + (own_n ? (s - own_lo) * n / own_n : 0);
+            const long long sf = gallop_find(W.surv, sq == seg ? s + 1 : lo, lo + n, guess, key);
+            if (sf >= 0) {
+                mf = W.surv_mask[sf];
+                pf = W.seg_off[sq] + W.surv_off[sf];
             }
         }
-        for (int c = 0; c < ncell; ++c) {
-            // the cell's two cubes: base cb and cb + first step; one is ours
-            const Pt far = add_mask<N>(cb[c], cm[c][0]);
-            const bool own_is_base = cb[c].c[0] == base.c[0] && cb[c].c[1] == base.c[1] &&
-                                     cb[c].c[2] == base.c[2] && cb[c].c[3] == base.c[3];
-            const Pt other = own_is_base ? far : cb[c];
-            const long long s_oth = find_cube(F, B, W, other);
-            const unsigned long long mask_oth = s_oth >= 0 ? W.surv_mask[s_oth] : 0ull;
-            const long long seg_oth = segment_of_coords(other.c[1], other.c[2], other.c[3], F, B);
-            int hits = 0;
-            long long partner = -1;
-            for (int k = 0; k <= D; ++k) {
-                int sm[N];
-                bool in_far;
-                if (k == 0) {
-                    for (int q = 0; q < N; ++q) sm[q] = cm[c][q + 1] ^ cm[c][0];
-                    in_far = true;
-                } else if (k == D) {
-                    for (int q = 0; q < N; ++q) sm[q] = cm[c][q];
-                    in_far = false;
-                } else {
-                    int w = 0;
-                    for (int q = 0; q < D; ++q)
-                        if (q != k - 1) sm[w++] = cm[c][q];
-                    in_far = false;
-                }
-                const int ft = mesh<N>().lookup[chain_key<N>(sm)];
-                const bool in_own = in_far != own_is_base;
-                if (in_own && ft == tt) continue;              // the face itself
-                const unsigned long long mk = in_own ? mask_own : mask_oth;
-                if (!((mk >> ft) & 1)) continue;
-                ++hits;
-                const long long sc = in_own ? s_own : s_oth;
-                const long long seg = in_own ? segment_of_coords(base.c[1], base.c[2], base.c[3], F, B) : seg_oth;
-                partner = W.seg_off[seg] + W.surv_off[sc] + __popcll(mk & ((1ull << ft) - 1ull));
-            }
-            if (hits != 1) {
+        constexpr int PER = C / D;
+        for (int c = a * PER; c < (a + 1) * PER; ++c) {
+            const unsigned long long in_own = mo & cells<N>().own[c];
+            if (!in_own) continue;
+            const int ft = cells<N>().far[c];
+            const bool far_hit = (mf >> ft) & 1ull;
+            const int n = __popcll(in_own) + (far_hit ? 1 : 0);
+            if (n != 2) {
                 atomicOr(status, ST_PAIRING);
                 continue;
             }
-            // both ends see the pair; one union suffices
-            if (partner > i) uf_unite(W.parent, (int)i, (int)partner, status);
+            const int t0 = __ffsll((long long)in_own) - 1;
+            const long long i = pos + __popcll(mo & ((1ull << t0) - 1ull));
+            long long j;
+            if (far_hit) {
+                j = pf + __popcll(mf & ((1ull << ft) - 1ull));
+            } else {
+                const int t1 = __ffsll((long long)(in_own & (in_own - 1))) - 1;
+                j = pos + __popcll(mo & ((1ull << t1) - 1ull));
+            }
+            if (i < 0 || j < 0 || i >= P || j >= P) {   // only after a failed scan (flagged)
+                atomicOr(status, ST_PAIRING);
+                continue;
+            }
+            uf_unite(W.parent, (int)i, (int)j, status);
+            ++pairs;
         }
+    }
+    // block totals of the two counts, then one atomic each
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        incid += __shfl_xor_sync(0xffffffffu, incid, o);
+    }
+    if (lane == 0) { red[0][warp] = pairs; red[1][warp] = incid; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long p = 0, q = 0;
+        for (int w = 0; w < NT / 32; ++w) { p += red[0][w]; q += red[1][w]; }
+        if (p) atomicAdd(&W.ctr->pairs, p);
+        if (q) atomicAdd(&W.ctr->incid, q);
     }
 }
 
 template <int N>
-__global__ void __launch_bounds__(NT) k_label(Field F, Workspace W) {
+__global__ void __launch_bounds__(NT) k_label(Field F, Workspace W, int check_cells) {
+    // a block's records are built in shared memory and stored as one
+    // contiguous run of 16-byte words (a record is 56 bytes; a run starts at
+    // a multiple of NT records, so at a 16-byte boundary)
+    static_assert(sizeof(ftk_cp) == 56 && (NT * sizeof(ftk_cp)) % 16 == 0, "record layout");
+    __shared__ __align__(16) ftk_cp recs[NT];
     if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
     const long long P = W.ctr->punctures;
     unsigned *status = &W.ctr->status;
-    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
-        const int r = uf_find(W.parent, (int)i, status);
-        const long long fid = W.face[i];
-        const long long lab = W.face[r];
-        W.label[i] = lab;
-        int tt;
-        const Pt b = decode_face<N>(F, fid, tt);
-        ftk_cp rec;
-        rec.face_id = fid;
-        rec.label = lab;
-        rec.base[0] = b.c[0]; rec.base[1] = b.c[1]; rec.base[2] = b.c[2]; rec.base[3] = b.c[3];
-        const float4 o = W.off[i];
-        rec.off[0] = o.x; rec.off[1] = o.y; rec.off[2] = o.z; rec.off[3] = o.w;
-        rec.morse_index = W.morse[i];
-        rec.ordinal = (mesh<N>().face[tt][N - 1] & MeshDims<N>::TBIT) ? 0 : 1;
-        rec.ndim = (uint8_t)N;
-        for (int q = 0; q < 5; ++q) rec.reserved[q] = 0;
-        W.packed[i] = rec;
+    // every punctured side of a cell linked exactly once (see k_link_survivors)
+    if (check_cells && blockIdx.x == 0 && threadIdx.x == 0 && 2 * W.ctr->pairs != W.ctr->incid)
+        atomicOr(status, ST_PAIRING);
+    for (long long i0 = blockIdx.x * (long long)NT; i0 < P; i0 += (long long)gridDim.x * NT) {
+        const long long i = i0 + threadIdx.x;
+        if (i < P) {
+            const int r = uf_find(W.parent, (int)i, status);
+            const long long fid = W.face[i];
+            const long long lab = W.face[r];
+            W.label[i] = lab;
+            int tt;
+            const Pt b = decode_face<N>(F, fid, tt);
+            ftk_cp &rec = recs[threadIdx.x];
+            rec.face_id = fid;
+            rec.label = lab;
+            rec.base[0] = b.c[0]; rec.base[1] = b.c[1]; rec.base[2] = b.c[2]; rec.base[3] = b.c[3];
+            const float4 o = W.off[i];
+            rec.off[0] = o.x; rec.off[1] = o.y; rec.off[2] = o.z; rec.off[3] = o.w;
+            rec.morse_index = W.morse[i];
+            rec.ordinal = (mesh<N>().face[tt][N - 1] & MeshDims<N>::TBIT) ? 0 : 1;
+            rec.ndim = (uint8_t)N;
+            for (int q = 0; q < 5; ++q) rec.reserved[q] = 0;
+        }
+        __syncthreads();
+        const long long n = P - i0 < NT ? P - i0 : NT;
+        const int nbytes = (int)n * (int)sizeof(ftk_cp);
+        const uint4 *src = reinterpret_cast<const uint4 *>(recs);
+        uint4 *dst = reinterpret_cast<uint4 *>(W.packed + i0);
+        for (int k = threadIdx.x; k < nbytes / 16; k += NT) dst[k] = src[k];
+        if ((nbytes & 15) && threadIdx.x == 0) {   // odd count: the last 8 bytes
+            const int k = nbytes / 8 - 1;
+            reinterpret_cast<unsigned long long *>(W.packed + i0)[k] = reinterpret_cast<const unsigned long long *>(recs)[k];
+        }
+        __syncthreads();
     }
 }
 
@@ -1491,6 +1866,7 @@ __device__ unsigned long long eval_cube(const Field &F, long long g) {
         if (b.c[slot] + 1 < ext) inside |= 1 << a;
     }
     int32_t Gc[NCRN][N];
+    const long long ib = vindex(F, b);
 #pragma unroll
     for (int c = 0; c < NCRN; ++c) {
         if (c & ~inside) {
@@ -1499,8 +1875,9 @@ __device__ unsigned long long eval_cube(const Field &F, long long g) {
             continue;
         }
         const Pt p = add_mask<N>(b, c);
+        const long long ip = ib + mask_offset<N>(F, c);
 #pragma unroll
-        for (int r = 0; r < N; ++r) Gc[c][r] = grad_global(F, p, r);
+        for (int r = 0; r < N; ++r) Gc[c][r] = grad_at(F, p, ip, r);
     }
     unsigned long long m = 0;
     for (int tt = 0; tt < T; ++tt) {
@@ -1558,8 +1935,9 @@ __global__ void __launch_bounds__(NT) k_survive_eval(Field F, Workspace W) {
                 for (int r = 0; r < N; ++r) Gs[warp][lane][r] = 0;
             } else {
                 const Pt p = add_mask<N>(b, lane);
+                const long long ip = vindex(F, b) + mask_offset<N>(F, lane);
 #pragma unroll
-                for (int r = 0; r < N; ++r) Gs[warp][lane][r] = grad_global(F, p, r);
+                for (int r = 0; r < N; ++r) Gs[warp][lane][r] = grad_at(F, p, ip, r);
             }
         }
         __syncwarp();
@@ -1588,29 +1966,48 @@ __global__ void __launch_bounds__(NT) k_survive_eval(Field F, Workspace W) {
     }
 }
 
-// one warp per segment: offsets of the survivors' punctures within the
-// segment (exclusive scan of the mask popcounts) and the segment total
+// Offsets of the punctured faces over the survivor list: surv_off[s] = number
+// of punctures of the survivors before s in list order (every segment's
+// survivors are one contiguous run of the list, so differences give the
+// within-segment offsets and the segment totals).  Blocks claim tiles of
+// LB_TILE survivors in order; a thread sums the popcounts of LB_TILE / NT
+// consecutive masks.
 __global__ void __launch_bounds__(NT) k_survive_scan(Workspace W) {
+    constexpr int PER = LB_TILE / NT;
+    __shared__ long long red[NT / 32 + 1];
+    __shared__ long long sh[2];
     if (W.ctr->status & ST_SOVERFLOW) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * (NT / 32);
-    for (long long seg = (long long)blockIdx.x * (NT / 32) + warp; seg < W.nseg; seg += stride) {
-        const int n = W.seg_scnt[seg];
-        const long long base = W.seg_sstage[seg];
-        int run = 0;
-        for (int k0 = 0; k0 < n; k0 += 32) {
-            const int k = k0 + lane;
-            const int c = k < n ? __popcll(W.surv_mask[base + k]) : 0;
-            int incl = c;
+    const long long ns = (long long)W.ctr->survivors;
+    while (true) {
+        if (threadIdx.x == 0) sh[1] = (long long)atomicAdd(&W.ctr->tiles, 1ull);
+        __syncthreads();
+        const long long t = sh[1];
+        if (t * LB_TILE >= ns) break;
+        const long long s0 = t * LB_TILE + (long long)threadIdx.x * PER;
+        int c[PER];
+        int loc = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (k < n) W.surv_off[base + k] = run + incl - c;
-            run += __shfl_sync(0xffffffffu, incl, 31);
+        for (int k = 0; k < PER; ++k) {
+            c[k] = s0 + k < ns ? __popcll(W.surv_mask[s0 + k]) : 0;
+            loc += c[k];
         }
-        if (lane == 0) W.seg_cnt[seg] = run;
+        long long tot;
+        long long ex = block_excl_scan<long long>(loc, red, tot);
+        if (threadIdx.x < 32) {
+            const long long before = warp_lookback(W.tile, t, tot, &W.ctr->status);
+            if (threadIdx.x == 0) {
+                sh[0] = before;
+                if ((t + 1) * LB_TILE >= ns) W.ctr->surv_total = before + tot;
+            }
+        }
+        __syncthreads();
+        ex += sh[0];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            if (s0 + k < ns) W.surv_off[s0 + k] = (int)(ex < INT_MAX ? ex : INT_MAX);
+            ex += c[k];
+        }
+        __syncthreads();
     }
 }
 
@@ -1618,19 +2015,27 @@ __global__ void __launch_bounds__(NT) k_survive_scan(Workspace W) {
 template <int N>
 __global__ void __launch_bounds__(NT) k_emit(Field F, Blocking B, Workspace W) {
     constexpr int T = MeshDims<N>::T;
+    // the segment scan has finished: clear its tile states for the next run
+    const long long nst = (W.nseg + SEG_TILE - 1) / SEG_TILE;
+    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < nst; t += (long long)gridDim.x * NT)
+        W.seg_tile[t] = 0ull;
     if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
     const unsigned long long ns = W.ctr->survivors;
+    const long long P = W.ctr->punctures;
     for (long long s = blockIdx.x * (long long)NT + threadIdx.x; s < (long long)ns; s += (long long)gridDim.x * NT) {
         unsigned long long m = W.surv_mask[s];
         if (!m) continue;
         const long long g = W.surv[s];
         long long i = W.seg_off[segment_of(g, F, B)] + W.surv_off[s];
+        if (i < 0 || i + __popcll(m) > P) {   // only after a failed scan (flagged)
+            atomicOr(&W.ctr->status, ST_PAIRING);
+            continue;
+        }
         while (m) {
             const int tt = __ffsll((long long)m) - 1;
             m &= m - 1;
             W.face[i] = g * T + tt;
             W.parent[i] = (int)i;
-            W.staging[i] = s;          // the puncture's cube, for the link step
             ++i;
         }
     }
@@ -1686,6 +2091,23 @@ static int sparse_grid() {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         g = (sms > 0 ? sms : 148) * 4;
     }
+    return g;
+}
+
+// grid of a latency-bound grid-stride kernel: every block it can keep
+// resident on every SM (more loads in flight than sparse_grid's 4 per SM)
+template <auto K>
+static int resident_grid() {
+    static const int g = [] {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K, NT, 0) != cudaSuccess || per < 1) {
+            cudaGetLastError();
+            per = 4;
+        }
+        return (sms > 0 ? sms : 148) * per;
+    }();
     return g;
 }
 
@@ -2102,7 +2524,7 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
     if (ev) cudaEventRecord(ev[1], s);
     const bool stream = variant != VAR_TILE;
     if (stream) {
-        if constexpr (N == 2) k_survive_eval_thread<N><<<sg, NT, 0, s>>>(F, W);
+        if constexpr (N == 2) k_survive_eval_thread<N><<<resident_grid<k_survive_eval_thread<N>>(), NT, 0, s>>>(F, W);
         else k_survive_eval<N><<<sg * 2, NT, 0, s>>>(F, W);
         k_survive_scan<<<sg, NT, 0, s>>>(W);
     }
@@ -2110,25 +2532,26 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
         cudaError_t e2 = cudaGetLastError();
         if (e2 != cudaSuccess) { g_launch_stage = "detect/survive"; return e2; }
     }
-    k_scan<<<1, NT, 0, s>>>(W, stream ? 1 : 0);
+    if (stream) k_seg_scan<<<(unsigned)std::min<long long>(sg, (W.nseg + SEG_TILE - 1) / SEG_TILE), NT, 0, s>>>(W);
+    else k_scan<<<1, NT, 0, s>>>(W);
     if (ev) cudaEventRecord(ev[2], s);
     if (stream) {
-        k_emit<N><<<sg, NT, 0, s>>>(F, B, W);
+        k_emit<N><<<resident_grid<k_emit<N>>(), NT, 0, s>>>(F, B, W);
         // few, long-running threads in 3D: small blocks spread them over every SM
         if constexpr (N == 3) {
             k_locate<N><<<sg * 2, 64, 0, s>>>(F, W);
             k_classify_exact<N><<<sg, NT, 0, s>>>(F, W);
         } else {
-            k_locate<N><<<sg, NT, 0, s>>>(F, W);
+            k_locate<N><<<resident_grid<k_locate<N>>(), NT, 0, s>>>(F, W);
         }
     } else {
         k_finalize<N><<<sg, NT, 0, s>>>(F, B, W);
     }
     if (ev) cudaEventRecord(ev[3], s);
-    if (stream) k_link_cubes<N><<<sg, NT, 0, s>>>(F, B, W);
+    if (stream) k_link_survivors<N><<<resident_grid<k_link_survivors<N>>(), NT, 0, s>>>(F, B, W);
     else k_link<N><<<sg, NT, 0, s>>>(F, B, W);
     if (ev) cudaEventRecord(ev[4], s);
-    k_label<N><<<sg, NT, 0, s>>>(F, W);
+    k_label<N><<<resident_grid<k_label<N>>(), NT, 0, s>>>(F, W, stream ? 1 : 0);
     if (ev) cudaEventRecord(ev[5], s);
     cudaError_t e3 = cudaGetLastError();
     if (e3 != cudaSuccess) g_launch_stage = "scan..label";

@@ -24,6 +24,11 @@ struct RunCounters {
     long long punctures;           // final count P (set by the scan kernel)
     unsigned long long survivors;  // spacetime cubes that survived the sign cull
     unsigned long long pending;    // 3D punctures left to the exact classification
+    unsigned long long tiles;      // survivor tiles handed out (survivor scan)
+    unsigned long long seg_tiles;  // segment tiles handed out (segment scan)
+    long long surv_total;          // punctures over every surviving cube
+    unsigned long long pairs;      // cells linked (two punctured sides)
+    unsigned long long incid;      // sum over punctured faces of their cell count
 };
 
 // Division by a fixed divisor d for numerators n < 2^31: with
@@ -82,8 +87,7 @@ struct Workspace {
     int *seg_cnt;            // [nseg] punctures per segment
     long long *seg_stage;    // [nseg] offset of the segment's run in staging
     long long *seg_off;      // [nseg] exclusive scan of seg_cnt
-    long long *staging;      // [cap] tiled variant: face ids, per-segment runs;
-                             //       streaming variants: surviving cube of each puncture
+    long long *staging;      // [cap] tiled variant: face ids, per-segment runs
     long long *face;         // [cap] face ids sorted
     int *parent;             // [cap] union-find
     float4 *off;             // [cap] in-cell offsets x, y, z, t
@@ -95,11 +99,16 @@ struct Workspace {
     // streaming variant: surviving cubes, evaluated after the dense pass
     long long *surv;                // [scap] vertex id of each surviving cube, per-segment runs
     unsigned long long *surv_mask;  // [scap] punctured face types of the cube
-    int *surv_off;                  // [scap] first puncture of the cube within its segment
+    int *surv_off;                  // [scap] punctures of the survivors before it in list order
     int *seg_scnt;                  // [nseg] survivors per segment
     long long *seg_sstage;          // [nseg] start of the segment's run in surv
+    unsigned long long *tile;       // [scap / LB_TILE] look-back state of the survivor scan
+    unsigned long long *seg_tile;   // [nseg / SEG_TILE] look-back state of the segment scan
     long long scap;
 };
+
+constexpr int LB_TILE = 2048;       // survivors per tile of the survivor scan
+constexpr int SEG_TILE = 2048;      // segments per tile of the segment scan
 
 // segment = (t, z, y-block): a contiguous run of face ids
 __host__ __device__ inline long long segment_of_coords(int y, int z, int t, const Field &F, const Blocking &B) {
