@@ -592,14 +592,6 @@ __device__ __forceinline__ int grad_at(const Field &F, const Pt &p, long long ip
     return m * (qat(F, hi) - qat(F, lo));
 }
 
-// vertex-id step of axis a (0 = x, 1 = y, 2 = z in 3D, N = t) in the
-// unpadded vertex numbering
-template <int N>
-__device__ __forceinline__ long long vstride_key(const Field &F, int a) {
-    return a == 0 ? 1LL : a == 1 ? (long long)F.nx : a == N ? (long long)F.nx * F.ny * F.nz
-                                                            : (long long)F.nx * F.ny;
-}
-
 // offset of vertex b + mask m from vertex b (axis N of m is time)
 template <int N>
 __device__ __forceinline__ long long mask_offset(const Field &F, int m) {
@@ -1273,42 +1265,6 @@ __device__ __forceinline__ long long find_cube(const Field &F, const Blocking &B
     return (lo < hi0 && W.surv[lo] == key) ? lo : -1;
 }
 
-// index of `key` in the sorted run a[lo, hi), or -1: exponential search out
-// of the guess p (clamped into the run), then binary search of the bracket
-// -- a few probes when the guess is close, never more than about twice a
-// plain binary search
-__device__ __forceinline__ long long gallop_find(const long long *a, long long lo, long long hi, long long p,
-                                                 long long key) {
-    if (lo >= hi) return -1;
-    p = p < lo ? lo : p >= hi ? hi - 1 : p;
-    long long L, R;   // lower_bound(key) lies in [L, R]
-    if (a[p] < key) {
-        L = p + 1;
-        R = hi;
-        for (long long step = 1;; step <<= 1) {
-            const long long q = p + step;
-            if (q >= hi) break;
-            if (a[q] >= key) { R = q; break; }
-            L = q + 1;
-        }
-    } else {
-        L = lo;
-        R = p;
-        for (long long step = 1;; step <<= 1) {
-            const long long q = p - step;
-            if (q < lo) break;
-            if (a[q] < key) { L = q + 1; break; }
-            R = q;
-        }
-    }
-    while (L < R) {
-        const long long mid = (L + R) >> 1;
-        if (a[mid] < key) L = mid + 1;
-        else R = mid;
-    }
-    return (L < hi && a[L] == key) ? L : -1;
-}
-
 // number of cells having face type tt based at b as a side
 template <int N>
 __device__ __forceinline__ int face_cells(const Field &F, const Pt &b, int tt) {
@@ -1334,7 +1290,7 @@ __device__ __forceinline__ int face_cells(const Field &F, const Pt &b, int tt) {
 // or two cells (one on the grid boundary), so the cells visited with two
 // punctured sides must number exactly half the sum of those counts.
 template <int N>
-__global__ void __launch_bounds__(NT, 4) k_link_survivors(Field F, Blocking B, Workspace W) {
+__global__ void __launch_bounds__(NT) k_link_survivors(Field F, Blocking B, Workspace W) {
     constexpr int D = N + 1;
     constexpr int FULL = (1 << D) - 1;
     constexpr int C = MeshDims<N>::C;
@@ -1384,19 +1340,10 @@ __global__ void __launch_bounds__(NT, 4) k_link_survivors(Field F, Blocking B, W
             q.c[1] += a == 1;
             q.c[2] += N == 3 && a == 2;
             q.c[3] += a == N;
-            const long long sq = segment_of_coords(q.c[1], q.c[2], q.c[3], F, B);
-            const long long key = g + vstride_key<N>(F, a);
-            const long long lo = W.seg_sstage[sq], n = W.seg_scnt[sq];
-            // guess: the next row of the same segment lies about a row's
-            // share of the segment further on; another segment (next z, t
-            // or y-block) holds the cube at about the same relative rank
-            const long long own_lo = W.seg_sstage[seg], own_n = W.seg_scnt[seg];
-            const long long guess = sq == seg ? s + (own_n + B.ry - 1) / B.ry
-                                              : lo + (own_n ? (s - own_lo) * n / own_n : 0);
-            const long long sf = gallop_find(W.surv, sq == seg ? s + 1 : lo, lo + n, guess, key);
+            const long long sf = find_cube(F, B, W, q);
             if (sf >= 0) {
                 mf = W.surv_mask[sf];
-                pf = W.seg_off[sq] + W.surv_off[sf];
+                pf = W.seg_off[segment_of_coords(q.c[1], q.c[2], q.c[3], F, B)] + W.surv_off[sf];
             }
         }
         constexpr int PER = C / D;
@@ -1617,7 +1564,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
             bool ok = true;
             for (int j = 0; j < J; ++j) {
                 const int slot = j % NS2;
-                if (j >= NS2 && !mbar_wait(&empty[slot], ((j / NS2) + 1) & 1)) {
+                if (j >= NS2 && !mbar_wait(&empty[slot], ((j / NS2) + 1) & 1, 64)) {
                     ok = false;
                     break;
                 }
@@ -1641,7 +1588,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
         // the warp); pass 1 counts, pass 2 writes in bitmap order
         for (int q = 0; q < nslab; ++q) {
             const int b = q & 1;
-            if (!__all_sync(0xffffffffu, mbar_wait(&done[b], (q >> 1) & 1))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&done[b], (q >> 1) & 1, 256))) {
                 if (lane == 0) atomicOr(status, ST_TIMEOUT);
                 return;
             }
@@ -1679,9 +1626,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     const int xl = max(xa - 1, 0);
     const int xr1 = min(xa + CX, nx - 1);
     const int xr2 = min(xa + CX + 1, nx - 1);
-    const bool dbl0 = x0 == 0;                             // one-sided difference at x = 0
-    const bool dbl7 = ncol == 8 && x0 + 8 == nx;           // ... at x = nx-1 (column 7)
-    const bool dbl3 = ncol == 4;                           // ... at x = nx-1 (column 3)
+    const bool dbl7 = ncol == 8 && x0 + 8 == nx;           // column 7 is x = nx-1
+    const bool dbl3 = ncol == 4;                           // column 3 is x = nx-1
     const float scale = F.scale;
     uint32_t bad = 0, dummy = 0;
     // cube-row words of the previous slice, one smem column per thread
@@ -1699,9 +1645,104 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
 #pragma unroll
     for (int k = 0; k < 11; ++k) fa[k] = fb[k] = fc[k] = MAGIC_BITS;
     uint32_t pprev = 0;
+    // fast encoding: AND and OR of every sample read, checked against the
+    // encoding's range once at the end
+    uint32_t qa_and = 0xffffffffu, qa_or = 0u;
     int j = 0;
     int nsv = 0;     // survivors this thread found in the current slab
     bool ok = true;
+
+    // Streamed row vi of slice sl: wait for its ring slot, quantise it into
+    // `cur`, and with the two rows before it (r0 = row u-1, r1 = row u) form
+    // G row u = y0 - 2 + vi and the cube rows it completes.  The caller
+    // rotates the three row buffers through the arguments, so no row is
+    // copied.  Only the signs of G matter here: the one-sided difference at
+    // a grid edge (clamped rows and columns) has the sign of the doubled
+    // difference the exact stages use.
+    auto row = [&](int vi, int sl, uint32_t *bq, const uint32_t (&r0)[11], const uint32_t (&r1)[11],
+                   uint32_t (&cur)[11]) {
+        const int slot = j % NS2;
+        if (ok && !mbar_wait(&full[slot], (j / NS2) & 1)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);   // keep the warp converged
+        if (ok) {
+            const float *r = ring + (size_t)slot * nx;
+            const float4 c0 = *reinterpret_cast<const float4 *>(r + xa);
+            const float4 c1 = *reinterpret_cast<const float4 *>(r + xb);
+            cur[1] = qbits<EXACT>(c0.x, scale, bad);
+            cur[2] = qbits<EXACT>(c0.y, scale, bad);
+            cur[3] = qbits<EXACT>(c0.z, scale, bad);
+            cur[4] = qbits<EXACT>(c0.w, scale, bad);
+            cur[5] = qbits<EXACT>(c1.x, scale, bad);
+            cur[6] = qbits<EXACT>(c1.y, scale, bad);
+            cur[7] = qbits<EXACT>(c1.z, scale, bad);
+            cur[8] = qbits<EXACT>(c1.w, scale, bad);
+            if (ncol == 4) {
+                // columns x0+4.. do not exist: clamp to column nx-1
+                cur[5] = cur[6] = cur[7] = cur[8] = cur[4];
+            }
+            cur[0] = qbits<EXACT>(r[xl], scale, dummy);
+            cur[9] = qbits<EXACT>(r[xr1], scale, dummy);
+            cur[10] = qbits<EXACT>(r[xr2], scale, dummy);
+            if (!EXACT) {
+                // every sample read is a sample of the field (idle threads
+                // read column 0): all must lie in the fast rounding range
+                qa_and &= cur[1] & cur[2] & cur[3] & cur[4] & cur[5] & cur[6] & cur[7] & cur[8];
+                qa_or |= cur[1] | cur[2] | cur[3] | cur[4] | cur[5] | cur[6] | cur[7] | cur[8];
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+        ++j;
+        const int u = y0 - 2 + vi;
+        if (vi >= 2 && u <= ny - 1) {
+            uint32_t gx[9], gy[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                gx[k] = r1[k + 2] - r1[k];
+                gy[k] = cur[k + 1] - r0[k + 1];
+            }
+            if (dbl7) { gx[8] = gx[7]; gy[8] = gy[7]; }      // no column x0+8: duplicate
+            if (dbl3) { gx[4] = gx[3]; gy[4] = gy[3]; }      // no column x0+4
+            // bit 31 of each (wrapped) difference is the sign of G:
+            // w = sign(G_x[k]) at bit k, sign(G_y[k]) at bit 16 + k
+            uint32_t w = 0;
+#pragma unroll
+            for (int k = 8; k >= 0; --k) w = __funnelshift_l(gy[k], w, 1);
+            w <<= 7;
+#pragma unroll
+            for (int k = 8; k >= 0; --k) w = __funnelshift_l(gx[k], w, 1);
+            const uint32_t p = pair_word(w);
+            // cube row c = u-1 (G rows u-1, u); at the top edge cube row u alone
+            if (vi >= 3) {
+                const int i = vi - 3;
+                const uint32_t sq = combine(pprev, p);
+                if (sl > 0) {
+                    const uint32_t sv8 = survivors8(combine(sq, sst[i * NC])) & vmask;
+                    if (sv8) {
+                        const int idx = i * nx + x0;
+                        atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
+                        nsv += __popc(sv8);
+                        if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
+                    }
+                }
+                sst[i * NC] = sq;
+            }
+            if (u == ny - 1 && vi - 2 < RY2) {
+                const int i = vi - 2;
+                if (sl > 0) {
+                    const uint32_t sv8 = survivors8(combine(p, sst[i * NC])) & vmask;
+                    if (sv8) {
+                        const int idx = i * nx + x0;
+                        atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
+                        nsv += __popc(sv8);
+                        if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
+                    }
+                }
+                sst[i * NC] = p;
+            }
+            pprev = p;
+        }
+    };
 
     for (int sl = sl0; sl < nsl && ok; ++sl) {
         // slice sl > 0 completes slab q = sl-1, whose bits go to buffer q & 1:
@@ -1710,101 +1751,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
         uint32_t *bq = bm + (q & 1) * L.bmw;
         if (sl > 0 && q >= 2 && !mbar_wait(&freed[q & 1], ((q >> 1) - 1) & 1)) ok = false;
         ok = __all_sync(0xffffffffu, ok);
-#pragma unroll 3
-        for (int vi = 0; vi < RS; ++vi) {
-            const int slot = j % NS2;
-            if (ok && !mbar_wait(&full[slot], (j / NS2) & 1)) ok = false;
-            ok = __all_sync(0xffffffffu, ok);   // keep the warp converged
-            if (ok) {
-                const float *r = ring + (size_t)slot * nx;
-                const float4 c0 = *reinterpret_cast<const float4 *>(r + xa);
-                const float4 c1 = *reinterpret_cast<const float4 *>(r + xb);
-                fc[1] = qbits<EXACT>(c0.x, scale, bad);
-                fc[2] = qbits<EXACT>(c0.y, scale, bad);
-                fc[3] = qbits<EXACT>(c0.z, scale, bad);
-                fc[4] = qbits<EXACT>(c0.w, scale, bad);
-                fc[5] = qbits<EXACT>(c1.x, scale, bad);
-                fc[6] = qbits<EXACT>(c1.y, scale, bad);
-                fc[7] = qbits<EXACT>(c1.z, scale, bad);
-                fc[8] = qbits<EXACT>(c1.w, scale, bad);
-                if (ncol == 4) {
-                    // columns x0+4.. do not exist: clamp to column nx-1
-                    fc[5] = fc[6] = fc[7] = fc[8] = fc[4];
-                }
-                fc[0] = qbits<EXACT>(r[xl], scale, dummy);
-                fc[9] = qbits<EXACT>(r[xr1], scale, dummy);
-                fc[10] = qbits<EXACT>(r[xr2], scale, dummy);
-                if (!EXACT) {
-                    // every own sample must lie in the fast rounding range
-                    const uint32_t a = fc[1] & fc[2] & fc[3] & fc[4] & fc[5] & fc[6] & fc[7] & fc[8];
-                    const uint32_t o = fc[1] | fc[2] | fc[3] | fc[4] | fc[5] | fc[6] | fc[7] | fc[8];
-                    bad |= act ? ((a ^ MAGIC_BITS) | (o ^ MAGIC_BITS)) & 0xFF800000u : 0u;
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[slot]);
-            }
-            ++j;
-            // G row u = y0 - 2 + vi (rows u-1, u, u+1 are fa, fb, fc, clamped)
-            const int u = y0 - 2 + vi;
-            if (vi >= 2 && u <= ny - 1) {
-                uint32_t gx[9], gy[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    gx[k] = fb[k + 2] - fb[k];
-                    gy[k] = fc[k + 1] - fa[k + 1];
-                }
-                if (u == 0 || u == ny - 1) {
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) gy[k] <<= 1;
-                }
-                gx[0] = dbl0 ? gx[0] << 1 : gx[0];
-                gx[7] = dbl7 ? gx[7] << 1 : gx[7];
-                gx[3] = dbl3 ? gx[3] << 1 : gx[3];
-                if (dbl7) { gx[8] = gx[7]; gy[8] = gy[7]; }      // no column x0+8: duplicate
-                if (dbl3) { gx[4] = gx[3]; gy[4] = gy[3]; }      // no column x0+4
-                // bit 31 of each (wrapped) difference is the sign of G
-                uint32_t w = 0;
-#pragma unroll
-                for (int k = 8; k >= 0; --k) w = __funnelshift_l(gy[k], w, 1);
-                w <<= 7;
-#pragma unroll
-                for (int k = 8; k >= 0; --k) w = __funnelshift_l(gx[k], w, 1);
-                const uint32_t p = pair_word(w);
-                // cube row c = u-1 (G rows u-1, u); at the top edge cube row u alone
-                if (vi >= 3) {
-                    const int i = vi >= 3 ? vi - 3 : 0;
-                    const uint32_t sq = combine(pprev, p);
-                    if (sl > 0) {
-                        const uint32_t sv8 = survivors8(combine(sq, sst[i * NC])) & vmask;
-                        if (sv8) {
-                            const int idx = i * nx + x0;
-                            atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
-                            nsv += __popc(sv8);
-                            if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
-                        }
-                    }
-                    sst[i * NC] = sq;
-                }
-                if (u == ny - 1 && vi >= 2 && vi - 2 < RY2) {
-                    const int i = vi >= 2 ? vi - 2 : 0;
-                    if (sl > 0) {
-                        const uint32_t sv8 = survivors8(combine(p, sst[i * NC])) & vmask;
-                        if (sv8) {
-                            const int idx = i * nx + x0;
-                            atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
-                            nsv += __popc(sv8);
-                            if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
-                        }
-                    }
-                    sst[i * NC] = p;
-                }
-                pprev = p;
-            }
-#pragma unroll
-            for (int k = 0; k < 11; ++k) {
-                fa[k] = fb[k];
-                fb[k] = fc[k];
-            }
+        // rows in threes, the buffers rotating (fa, fb, fc) -> (fb, fc, fa) -> (fc, fa, fb)
+#pragma unroll 1
+        for (int vi = 0; vi < RS; vi += 3) {
+            row(vi, sl, bq, fa, fb, fc);
+            if (vi + 1 < RS) row(vi + 1, sl, bq, fb, fc, fa);
+            if (vi + 2 < RS) row(vi + 2, sl, bq, fc, fa, fb);
         }
         if (sl > 0) {
             const int n = __reduce_add_sync(0xffffffffu, nsv);
@@ -1845,6 +1797,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
         for (int i = 0; i < RY2; ++i) B.st_out[st_base + (long long)i * NC] = sst[i * NC];
     }
     if (!ok) atomicOr(status, ST_TIMEOUT);
+    if (!EXACT) bad |= ((qa_and ^ MAGIC_BITS) | (qa_or ^ MAGIC_BITS)) & 0xFF800000u;
     if (bad & (EXACT ? 1u : 0xFF800000u)) atomicOr(status, EXACT ? ST_RANGE : ST_WIDE);
 }
 
@@ -1852,6 +1805,22 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
 // Surviving cubes of the streaming variant: exact evaluation, ordered output
 // ----------------------------------------------------------------------------
 // bit tt of the result set iff face type tt based at vertex g is punctured
+// mask k of the chain of 2D face type tt, evaluated at compile time
+__host__ __device__ constexpr int face2_mask(int tt, int k) { return MeshTables<2>().face[tt][k]; }
+
+// the 12 face types of a 2D cube, unrolled at compile time
+template <int TT>
+__device__ __forceinline__ void eval_faces2(const int32_t (&Gc)[8][2], int inside, unsigned long long &m) {
+    if constexpr (TT < MeshDims<2>::T) {
+        constexpr int c1 = face2_mask(TT, 0), c2 = face2_mask(TT, 1);
+        if (!(c2 & ~inside)) {   // else the face leaves the grid
+            const int32_t V[3][2] = {{Gc[0][0], Gc[0][1]}, {Gc[c1][0], Gc[c1][1]}, {Gc[c2][0], Gc[c2][1]}};
+            if (face_punctured<2>(V)) m |= 1ull << TT;
+        }
+        eval_faces2<TT + 1>(Gc, inside, m);
+    }
+}
+
 template <int N>
 __device__ unsigned long long eval_cube(const Field &F, long long g) {
     constexpr int D = N + 1;
@@ -1880,17 +1849,22 @@ __device__ unsigned long long eval_cube(const Field &F, long long g) {
         for (int r = 0; r < N; ++r) Gc[c][r] = grad_at(F, p, ip, r);
     }
     unsigned long long m = 0;
-    for (int tt = 0; tt < T; ++tt) {
-        const uint8_t *ch = mesh<N>().face[tt];
-        if (ch[N - 1] & ~inside) continue;   // the face leaves the grid
-        int32_t V[N + 1][N];
+    if constexpr (N == 2) {
+        // face chains as compile-time constants: Gc stays in registers
+        eval_faces2<0>(Gc, inside, m);
+    } else {
+        for (int tt = 0; tt < T; ++tt) {
+            const uint8_t *ch = mesh<N>().face[tt];
+            if (ch[N - 1] & ~inside) continue;   // the face leaves the grid
+            int32_t V[N + 1][N];
 #pragma unroll
-        for (int k = 0; k <= N; ++k) {
-            const int c = k == 0 ? 0 : ch[k - 1];
+            for (int k = 0; k <= N; ++k) {
+                const int c = k == 0 ? 0 : ch[k - 1];
 #pragma unroll
-            for (int r = 0; r < N; ++r) V[k][r] = Gc[c][r];
+                for (int r = 0; r < N; ++r) V[k][r] = Gc[c][r];
+            }
+            if (face_punctured<N>(V)) m |= 1ull << tt;
         }
-        if (face_punctured<N>(V)) m |= 1ull << tt;
     }
     return m;
 }

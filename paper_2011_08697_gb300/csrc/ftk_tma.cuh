@@ -37,12 +37,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait on a phase; false if it did not complete within WAIT_CYCLES
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// bounded wait on a phase; false if it did not complete within WAIT_CYCLES.
+// Warps off the critical path (producer, compactor) back off with a sleep
+// between polls (sleep_ns > 0), leaving the issue slots to the consumers.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned sleep_ns = 0) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
+    while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > WAIT_CYCLES) return false;
+        if (sleep_ns) __nanosleep(sleep_ns);
+    }
     return true;
 }
 __device__ __forceinline__ void tma_row(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
