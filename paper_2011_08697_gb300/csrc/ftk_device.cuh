@@ -17,6 +17,7 @@
 //  * BigInt<W>: fixed-width two's-complement integers for the exact Morse
 //    classification (products up to ~2^390 in 3D).
 #pragma once
+#include <cmath>
 #include <cstdint>
 
 namespace ftk {
@@ -135,6 +136,163 @@ __host__ __device__ constexpr int chain_key(const int (&m)[N]) {
     int key = 0;
     for (int i = 0; i < N; ++i) key |= m[i] << (4 * i);
     return key;
+}
+
+// ----------------------------------------------------------------------------
+// Floating-point filters of the Morse classification (host and device, so
+// that the CPU tests can check them against exact arithmetic)
+// ----------------------------------------------------------------------------
+// fused multiply-add rounded once to nearest, on either side
+__host__ __device__ inline float fma_rn(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return std::fmaf(a, b, c);
+#endif
+}
+
+// bit length of |w| (1 for w = 0): the scale 2^(1 - bits) maps the largest
+// weight into [1, 2)
+__host__ __device__ inline int i128_bits(__int128 w) {
+    const unsigned __int128 u = w < 0 ? (unsigned __int128)(-w) : (unsigned __int128)w;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+#ifdef __CUDA_ARCH__
+    return hi ? 128 - __clzll((long long)hi) : (lo ? 64 - __clzll((long long)lo) : 1);
+#else
+    return hi ? 128 - __builtin_clzll(hi) : (lo ? 64 - __builtin_clzll(lo) : 1);
+#endif
+}
+
+__host__ __device__ inline float i128_to_float(__int128 v) {
+    const bool neg = v < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    const float r = fma_rn((float)hi, 18446744073709551616.0f, (float)lo);
+    return neg ? -r : r;
+}
+
+// Morse index of the symmetric 2x2 S from an FP32 evaluation, when its signs
+// are certain (same error model as the 3x3 filter below: Sd from weights
+// scaled by a power of two, every entry within e = 16u Ad + 2^-90 of the
+// scaled exact value; the perturbation bound of a product of two entries is
+// M_i M_j - |Sd_i| |Sd_j| with M = |Sd| + e, plus its own rounding).
+// det S < 0: saddle (1); det S > 0: maximum (2) if tr S < 0, else minimum (0).
+__host__ __device__ inline bool morse_filter2(const float (&Sd)[2][2], const float (&Ad)[2][2], int &morse) {
+    const float u = 5.9604644775390625e-8f;   // 2^-24
+    const float floor_abs = 8.0779356e-28f;   // 2^-90
+    float e[2][2], a[2][2], M[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            e[i][j] = 16.0f * u * Ad[i][j] + floor_abs;
+            a[i][j] = fabsf(Sd[i][j]);
+            M[i][j] = a[i][j] + e[i][j];
+        }
+    const float det = Sd[0][0] * Sd[1][1] - Sd[0][1] * Sd[0][1];
+    const float err_det = (M[0][0] * M[1][1] - a[0][0] * a[1][1]) + (M[0][1] * M[0][1] - a[0][1] * a[0][1]) +
+                          4.0f * u * (M[0][0] * M[1][1] + M[0][1] * M[0][1]);
+    // every comparison is false for a non-finite value: then the exact path
+    if (!(fabsf(det) > 2.0f * err_det)) return false;
+    if (det < 0.0f) {
+        morse = 1;
+        return true;
+    }
+    const float tr = Sd[0][0] + Sd[1][1];
+    const float err_tr = (e[0][0] + e[1][1]) + 2.0f * u * (M[0][0] + M[1][1]);
+    if (!(fabsf(tr) > 2.0f * err_tr)) return false;
+    morse = tr < 0.0f ? 2 : 0;
+    return true;
+}
+
+// Morse index of the symmetric 3x3 S from an FP32 evaluation, when its
+// signs are certain (the index is unchanged by a positive scale of S, so the
+// weights come in scaled by a power of two into [1, 2) for the largest).
+// Sd = S evaluated in FP32 from the scaled weights and the exact int64
+// Hessian sums: conversion, product and a 4-term sum stay within
+// 9u sum_k |w_k h_k| of the exact scaled entry, u = 2^-24; denormal
+// rounding adds at most 2^-100 absolutely.  Ad = sum_k |w_k h_k| in FP32.
+// With e = 16u Ad + 2^-90 bounding each entry's error and M = |Sd| + e
+// bounding each exact entry, the errors of tr, m2 and det are bounded by the
+// change of each monomial under the entry perturbations (prod M - prod |Sd|)
+// plus the rounding of their evaluation.  Returns false (the caller decides
+// exactly) unless every invariant exceeds twice its bound.
+__host__ __device__ inline bool morse_filter3(const float (&Sd)[3][3], const float (&Ad)[3][3], int &morse) {
+    const float u = 5.9604644775390625e-8f;   // 2^-24
+    const float floor_abs = 8.0779356e-28f;   // 2^-90
+    float e[3][3], M[3][3], a[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            e[i][j] = 16.0f * u * Ad[i][j] + floor_abs;
+            a[i][j] = fabsf(Sd[i][j]);
+            M[i][j] = a[i][j] + e[i][j];
+        }
+    const float tr = Sd[0][0] + Sd[1][1] + Sd[2][2];
+    const float err_tr = (e[0][0] + e[1][1] + e[2][2]) + 4.0f * u * (M[0][0] + M[1][1] + M[2][2]);
+    float m2 = 0.0f, err_m2 = 0.0f, mag_m2 = 0.0f;
+    const int P[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int i = P[q][0], j = P[q][1];
+        m2 += Sd[i][i] * Sd[j][j] - Sd[i][j] * Sd[i][j];
+        err_m2 += (M[i][i] * M[j][j] - a[i][i] * a[j][j]) + (M[i][j] * M[i][j] - a[i][j] * a[i][j]);
+        mag_m2 += M[i][i] * M[j][j] + M[i][j] * M[i][j];
+    }
+    err_m2 += 8.0f * u * mag_m2;
+    const float c0 = Sd[1][1] * Sd[2][2] - Sd[1][2] * Sd[2][1];
+    const float c1 = Sd[1][0] * Sd[2][2] - Sd[1][2] * Sd[2][0];
+    const float c2 = Sd[1][0] * Sd[2][1] - Sd[1][1] * Sd[2][0];
+    const float det = Sd[0][0] * c0 - Sd[0][1] * c1 + Sd[0][2] * c2;
+    // the six monomials of det: perturbation bound and magnitude
+    const int pm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    float err_det = 0.0f, mag_det = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float Mp = M[0][pm[q][0]] * M[1][pm[q][1]] * M[2][pm[q][2]];
+        const float ap = a[0][pm[q][0]] * a[1][pm[q][1]] * a[2][pm[q][2]];
+        err_det += Mp - ap;
+        mag_det += Mp;
+    }
+    err_det += 12.0f * u * mag_det;
+    // every comparison is false for a non-finite value: then the exact path
+    if (!(fabsf(tr) > 2.0f * err_tr && fabsf(m2) > 2.0f * err_m2 && fabsf(det) > 2.0f * err_det)) return false;
+    const int s[3] = {tr > 0.0f ? 1 : -1, m2 > 0.0f ? 1 : -1, det > 0.0f ? 1 : -1};
+    int prev = 1, changes = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (s[i] != prev) ++changes;
+        prev = s[i];
+    }
+    morse = changes;
+    return true;
+}
+
+// one vertex's term of S in FP32: Sd += wd HS, Ad += |wd| |HS| (upper
+// triangle), wd = the vertex's weight scaled by a power of two
+template <int N>
+__host__ __device__ inline void s_fp32_step(float wd, const long long (&HS)[N][N], float (&Sd)[N][N],
+                                            float (&Ad)[N][N]) {
+    const float aw = fabsf(wd);
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = a; b < N; ++b) {
+            const float hd = (float)HS[a][b];
+            Sd[a][b] = fma_rn(wd, hd, Sd[a][b]);
+            Ad[a][b] = fma_rn(aw, fabsf(hd), Ad[a][b]);
+        }
+}
+template <int N>
+__host__ __device__ inline void s_fp32_symmetrise(float (&Sd)[N][N], float (&Ad)[N][N]) {
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = 0; b < a; ++b) {
+            Sd[a][b] = Sd[b][a];
+            Ad[a][b] = Ad[b][a];
+        }
 }
 
 // ----------------------------------------------------------------------------

@@ -33,6 +33,7 @@
 //   k_label      as above.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 
 #include "ftk_device.cuh"
@@ -643,111 +644,6 @@ __device__ void hess_sym(const Field &F, const Pt &p, long long ip, long long (&
     }
 }
 
-__device__ __forceinline__ float i128_to_float(__int128 v) {
-    const bool neg = v < 0;
-    const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
-    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
-    const float r = __fmaf_rn((float)hi, 18446744073709551616.0f, (float)lo);
-    return neg ? -r : r;
-}
-
-// Morse index of the symmetric 2x2 S from an FP32 evaluation, when its signs
-// are certain (same error model as the 3x3 filter below: Sd from weights
-// scaled by a power of two, every entry within e = 16u Ad + 2^-90 of the
-// scaled exact value; the perturbation bound of a product of two entries is
-// M_i M_j - |Sd_i| |Sd_j| with M = |Sd| + e, plus its own rounding).
-// det S < 0: saddle (1); det S > 0: maximum (2) if tr S < 0, else minimum (0).
-__device__ __forceinline__ bool morse_filter2(const float (&Sd)[2][2], const float (&Ad)[2][2], int &morse) {
-    const float u = 5.9604644775390625e-8f;   // 2^-24
-    const float floor_abs = 8.0779356e-28f;   // 2^-90
-    float e[2][2], a[2][2], M[2][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            e[i][j] = 16.0f * u * Ad[i][j] + floor_abs;
-            a[i][j] = fabsf(Sd[i][j]);
-            M[i][j] = a[i][j] + e[i][j];
-        }
-    const float det = Sd[0][0] * Sd[1][1] - Sd[0][1] * Sd[0][1];
-    const float err_det = (M[0][0] * M[1][1] - a[0][0] * a[1][1]) + (M[0][1] * M[0][1] - a[0][1] * a[0][1]) +
-                          4.0f * u * (M[0][0] * M[1][1] + M[0][1] * M[0][1]);
-    // every comparison is false for a non-finite value: then the exact path
-    if (!(fabsf(det) > 2.0f * err_det)) return false;
-    if (det < 0.0f) {
-        morse = 1;
-        return true;
-    }
-    const float tr = Sd[0][0] + Sd[1][1];
-    const float err_tr = (e[0][0] + e[1][1]) + 2.0f * u * (M[0][0] + M[1][1]);
-    if (!(fabsf(tr) > 2.0f * err_tr)) return false;
-    morse = tr < 0.0f ? 2 : 0;
-    return true;
-}
-
-// Morse index of the symmetric 3x3 S from an FP32 evaluation, when its
-// signs are certain (the index is unchanged by a positive scale of S, so the
-// weights come in scaled by a power of two into [1, 2) for the largest).
-// Sd = S evaluated in FP32 from the scaled weights and the exact int64
-// Hessian sums: conversion, product and a 4-term sum stay within
-// 9u sum_k |w_k h_k| of the exact scaled entry, u = 2^-24; denormal
-// rounding adds at most 2^-100 absolutely.  Ad = sum_k |w_k h_k| in FP32.
-// With e = 16u Ad + 2^-90 bounding each entry's error and M = |Sd| + e
-// bounding each exact entry, the errors of tr, m2 and det are bounded by the
-// change of each monomial under the entry perturbations (prod M - prod |Sd|)
-// plus the rounding of their evaluation.  Returns false (the caller decides
-// exactly) unless every invariant exceeds twice its bound.
-__device__ __forceinline__ bool morse_filter3(const float (&Sd)[3][3], const float (&Ad)[3][3], int &morse) {
-    const float u = 5.9604644775390625e-8f;   // 2^-24
-    const float floor_abs = 8.0779356e-28f;   // 2^-90
-    float e[3][3], M[3][3], a[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            e[i][j] = 16.0f * u * Ad[i][j] + floor_abs;
-            a[i][j] = fabsf(Sd[i][j]);
-            M[i][j] = a[i][j] + e[i][j];
-        }
-    const float tr = Sd[0][0] + Sd[1][1] + Sd[2][2];
-    const float err_tr = (e[0][0] + e[1][1] + e[2][2]) + 4.0f * u * (M[0][0] + M[1][1] + M[2][2]);
-    float m2 = 0.0f, err_m2 = 0.0f, mag_m2 = 0.0f;
-    const int P[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int i = P[q][0], j = P[q][1];
-        m2 += Sd[i][i] * Sd[j][j] - Sd[i][j] * Sd[i][j];
-        err_m2 += (M[i][i] * M[j][j] - a[i][i] * a[j][j]) + (M[i][j] * M[i][j] - a[i][j] * a[i][j]);
-        mag_m2 += M[i][i] * M[j][j] + M[i][j] * M[i][j];
-    }
-    err_m2 += 8.0f * u * mag_m2;
-    const float c0 = Sd[1][1] * Sd[2][2] - Sd[1][2] * Sd[2][1];
-    const float c1 = Sd[1][0] * Sd[2][2] - Sd[1][2] * Sd[2][0];
-    const float c2 = Sd[1][0] * Sd[2][1] - Sd[1][1] * Sd[2][0];
-    const float det = Sd[0][0] * c0 - Sd[0][1] * c1 + Sd[0][2] * c2;
-    // the six monomials of det: perturbation bound and magnitude
-    const int pm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-    float err_det = 0.0f, mag_det = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const float Mp = M[0][pm[q][0]] * M[1][pm[q][1]] * M[2][pm[q][2]];
-        const float ap = a[0][pm[q][0]] * a[1][pm[q][1]] * a[2][pm[q][2]];
-        err_det += Mp - ap;
-        mag_det += Mp;
-    }
-    err_det += 12.0f * u * mag_det;
-    // every comparison is false for a non-finite value: then the exact path
-    if (!(fabsf(tr) > 2.0f * err_tr && fabsf(m2) > 2.0f * err_m2 && fabsf(det) > 2.0f * err_det)) return false;
-    const int s[3] = {tr > 0.0f ? 1 : -1, m2 > 0.0f ? 1 : -1, det > 0.0f ? 1 : -1};
-    int prev = 1, changes = 0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        if (s[i] != prev) ++changes;
-        prev = s[i];
-    }
-    morse = changes;
-    return true;
-}
 
 // coordinates (x, y, z, t) of vertex id g
 __device__ __forceinline__ Pt decode_vertex(const Field &F, long long g) {
@@ -906,22 +802,12 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
         long long wmax = 0;
 #pragma unroll
         for (int k = 0; k <= 2; ++k) wmax = max(wmax, D[k] < 0 ? -D[k] : D[k]);
-        const int wbits = wmax ? 64 - __clzll(wmax) : 1;
+        const int wbits = i128_bits(wmax);
         float Sd[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}}, Ad[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
 #pragma unroll
-        for (int k = 0; k <= 2; ++k) {
-            const float wd = ldexpf((float)(neg ? -D[k] : D[k]), 1 - wbits), aw = fabsf(wd);
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = a; b < 2; ++b) {
-                    const float hd = (float)HS2[k][a][b];
-                    Sd[a][b] = __fmaf_rn(wd, hd, Sd[a][b]);
-                    Ad[a][b] = __fmaf_rn(aw, fabsf(hd), Ad[a][b]);
-                }
-        }
-        Sd[1][0] = Sd[0][1];
-        Ad[1][0] = Ad[0][1];
+        for (int k = 0; k <= 2; ++k)
+            s_fp32_step<2>(ldexpf(i128_to_float(neg ? -D[k] : D[k]), 1 - wbits), HS2[k], Sd, Ad);
+        s_fp32_symmetrise<2>(Sd, Ad);
         int m = 0;
         if (morse_filter2(Sd, Ad, m)) {
             morse = (int8_t)m;
@@ -990,8 +876,7 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
             const __int128 w = D[k] < 0 ? -D[k] : D[k];
             if (w > wmax) wmax = w;
         }
-        const unsigned long long whi = (unsigned long long)(wmax >> 64), wlo = (unsigned long long)wmax;
-        const int wbits = whi ? 128 - __clzll((long long)whi) : (wlo ? 64 - __clzll((long long)wlo) : 1);
+        const int wbits = i128_bits(wmax);
         __int128 Si[3][3];
         float Sd[3][3], Ad[3][3];
 #pragma unroll
@@ -1003,28 +888,19 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
             }
         for (int k = 0; k <= N; ++k) {
             const __int128 w = sg < 0 ? -D[k] : D[k];
-            const float wd = ldexpf(i128_to_float(w), 1 - wbits), aw = fabsf(wd);
             long long HS[N][N];
             hess_sym<N>(F, v[k], iv[k], HS);
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
-                for (int b = a; b < 3; ++b) {
-                    const long long h = HS[a][b];
-                    Si[a][b] += w * (__int128)h;
-                    const float hd = (float)h;
-                    Sd[a][b] = __fmaf_rn(wd, hd, Sd[a][b]);
-                    Ad[a][b] = __fmaf_rn(aw, fabsf(hd), Ad[a][b]);
-                }
+                for (int b = a; b < 3; ++b) Si[a][b] += w * (__int128)HS[a][b];
+            s_fp32_step<3>(ldexpf(i128_to_float(w), 1 - wbits), HS, Sd, Ad);
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < a; ++b) {
-                Si[a][b] = Si[b][a];
-                Sd[a][b] = Sd[b][a];
-                Ad[a][b] = Ad[b][a];
-            }
+            for (int b = 0; b < a; ++b) Si[a][b] = Si[b][a];
+        s_fp32_symmetrise<3>(Sd, Ad);
         const __int128 LIM = (__int128)1 << 40;
         // the int128 sums cannot wrap: 4 terms of |w| < 2^wbits, |h| < 2^35
         bool small = wbits <= 88;
@@ -2454,6 +2330,13 @@ template <int N>
 static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, const Workspace &W, cudaStream_t s,
                               cudaEvent_t *ev) {
     const int sg = sparse_grid();
+    // grid of a grid-stride kernel: at most `limit` blocks, and no more than
+    // its work bound (the capacity of the list it walks) needs -- small
+    // fields (batches, streamed slabs) launch few blocks
+    auto gsize = [](int limit, long long items, int per_block) -> unsigned {
+        const long long need = (items + per_block - 1) / per_block;
+        return (unsigned)std::max<long long>(1, std::min<long long>(limit, need));
+    };
     if (ev) cudaEventRecord(ev[0], s);
     // kernel attributes are set outside stream capture (a first, uncaptured
     // launch of the same shape always precedes a captured one)
@@ -2498,9 +2381,10 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
     if (ev) cudaEventRecord(ev[1], s);
     const bool stream = variant != VAR_TILE;
     if (stream) {
-        if constexpr (N == 2) k_survive_eval_thread<N><<<resident_grid<k_survive_eval_thread<N>>(), NT, 0, s>>>(F, W);
-        else k_survive_eval<N><<<sg * 2, NT, 0, s>>>(F, W);
-        k_survive_scan<<<sg, NT, 0, s>>>(W);
+        if constexpr (N == 2)
+            k_survive_eval_thread<N><<<gsize(resident_grid<k_survive_eval_thread<N>>(), W.scap, NT), NT, 0, s>>>(F, W);
+        else k_survive_eval<N><<<gsize(sg * 2, W.scap, NT / 32), NT, 0, s>>>(F, W);
+        k_survive_scan<<<gsize(sg, W.scap, LB_TILE), NT, 0, s>>>(W);
     }
     {
         cudaError_t e2 = cudaGetLastError();
@@ -2510,22 +2394,22 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
     else k_scan<<<1, NT, 0, s>>>(W);
     if (ev) cudaEventRecord(ev[2], s);
     if (stream) {
-        k_emit<N><<<resident_grid<k_emit<N>>(), NT, 0, s>>>(F, B, W);
+        k_emit<N><<<gsize(resident_grid<k_emit<N>>(), W.scap, NT), NT, 0, s>>>(F, B, W);
         // few, long-running threads in 3D: small blocks spread them over every SM
         if constexpr (N == 3) {
-            k_locate<N><<<sg * 2, 64, 0, s>>>(F, W);
-            k_classify_exact<N><<<sg, NT, 0, s>>>(F, W);
+            k_locate<N><<<gsize(sg * 2, W.cap, 64), 64, 0, s>>>(F, W);
+            k_classify_exact<N><<<gsize(sg, W.cap, NT), NT, 0, s>>>(F, W);
         } else {
-            k_locate<N><<<resident_grid<k_locate<N>>(), NT, 0, s>>>(F, W);
+            k_locate<N><<<gsize(resident_grid<k_locate<N>>(), W.cap, NT), NT, 0, s>>>(F, W);
         }
     } else {
         k_finalize<N><<<sg, NT, 0, s>>>(F, B, W);
     }
     if (ev) cudaEventRecord(ev[3], s);
-    if (stream) k_link_survivors<N><<<resident_grid<k_link_survivors<N>>(), NT, 0, s>>>(F, B, W);
+    if (stream) k_link_survivors<N><<<gsize(resident_grid<k_link_survivors<N>>(), W.scap * (N + 1), NT), NT, 0, s>>>(F, B, W);
     else k_link<N><<<sg, NT, 0, s>>>(F, B, W);
     if (ev) cudaEventRecord(ev[4], s);
-    k_label<N><<<resident_grid<k_label<N>>(), NT, 0, s>>>(F, W, stream ? 1 : 0);
+    k_label<N><<<gsize(resident_grid<k_label<N>>(), W.cap, NT), NT, 0, s>>>(F, W, stream ? 1 : 0);
     if (ev) cudaEventRecord(ev[5], s);
     cudaError_t e3 = cudaGetLastError();
     if (e3 != cudaSuccess) g_launch_stage = "scan..label";
