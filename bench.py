@@ -165,11 +165,14 @@ def measured_peak_hbm():
 
 def profiled_traffic(wl: str):
     """DRAM bytes per detect launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    taken on the current kernel source (else None): the hash covers the
+    kernel file's device code, everything before its host-side marker."""
     import hashlib
-    src_file = "ftk_detect3.cu" if wl == "blobs3d" else "ftk_kernels.cu"
+    src_file = "ftk_detect3.cu" if wl == "blobs3d" else "ftk_detect2.cu"
     src = os.path.join(ROOT, "paper_2011_08697_gb300", "csrc", src_file)
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    text = open(src, "rb").read()
+    mark = text.find(b"// ---- host side: launch configuration ----")
+    sha = hashlib.sha256(text if mark < 0 else text[:mark]).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", f"detect_{wl}_traffic.txt")
     if not os.path.exists(path):
         return None

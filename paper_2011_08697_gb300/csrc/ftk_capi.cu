@@ -92,9 +92,7 @@ ftk_status alloc_survivors(Workspace &W, long long scap) {
     if (cudaMalloc(&W.surv, scap * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&W.surv_mask, scap * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&W.surv_off, scap * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&W.tile, ntile * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(W.tile, 0, ntile * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess) {   // the plan's streams do not wait on the legacy stream
+        cudaMalloc(&W.tile, ntile * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         return fail(FTK_ERR_NOMEM, "device allocation of the survivor arrays failed");
     }
@@ -510,9 +508,7 @@ ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_
         const long long nst = (W.nseg + SEG_TILE - 1) / SEG_TILE;
         if (cudaMalloc(&W.seg_scnt, W.nseg * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&W.seg_sstage, W.nseg * sizeof(long long)) != cudaSuccess ||
-            cudaMalloc(&W.seg_tile, nst * sizeof(unsigned long long)) != cudaSuccess ||
-            cudaMemset(W.seg_tile, 0, nst * sizeof(unsigned long long)) != cudaSuccess ||
-            cudaDeviceSynchronize() != cudaSuccess) {
+            cudaMalloc(&W.seg_tile, nst * sizeof(unsigned long long)) != cudaSuccess) {
             cudaGetLastError();
             s = fail(FTK_ERR_NOMEM, "device allocation failed");
         } else {

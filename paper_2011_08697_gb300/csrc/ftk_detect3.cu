@@ -445,6 +445,7 @@ void *s3_kernel() { return (void *)k_detect3_stream<EXACT>; }
 
 }  // namespace
 
+// ---- host side: launch configuration ----
 size_t stream3_smem_bytes(int nx, const Blocking &B) { return (size_t)s3_layout(nx, B.ry, B.rz).total; }
 int stream3_threads() { return S3_THREADS; }
 
@@ -452,9 +453,7 @@ int stream3_ctas_per_sm(int nx, const Blocking &B) {
     int n = 0;
     const size_t smem = stream3_smem_bytes(nx, B);
     const void *k = s3_kernel<false>();
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < smem)
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_cap(k, smem, false);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, S3_THREADS, smem);
     return n > 0 ? n : 1;
 }
@@ -464,16 +463,10 @@ cudaError_t launch_detect3(int variant, const Field &F, const Blocking &B, const
     const bool exact = variant == VAR_STREAM3_EXACT;
     const void *k = exact ? s3_kernel<true>() : s3_kernel<false>();
     const size_t smem = stream3_smem_bytes(F.pitch, B);
-    // the attribute only ever grows: a captured graph may replay a larger
-    // launch after a smaller one was configured
-    static size_t configured[2] = {0, 0};
-    size_t &cfg = configured[exact ? 1 : 0];
-    if (smem > cfg) {
-        if (capturing) return cudaErrorInvalidValue;   // configured by the first, uncaptured launch
-        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        cfg = smem;
-    }
+    // the cap only ever grows: a captured graph may replay a larger launch
+    // after a smaller one was configured
+    const cudaError_t e = raise_smem_cap(k, smem, capturing);
+    if (e != cudaSuccess) return e;
     const unsigned units = (unsigned)((long long)B.ntc * B.nzb * B.nyb);
     Field Fa = F;
     Blocking Ba = B;

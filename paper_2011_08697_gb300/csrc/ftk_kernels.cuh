@@ -139,6 +139,7 @@ constexpr int STREAM3_MAX_NX = 512;   // widest row the 3D streaming kernel take
 inline int exact_variant(int v) {
     return v == VAR_STREAM2 ? VAR_STREAM2_EXACT : v == VAR_STREAM3 ? VAR_STREAM3_EXACT : v;
 }
+constexpr float RANGE_LIMIT = 268435456.0f;   // 2^28: the exact quantisation's range of |f 2^S|
 constexpr int STREAM2_ROWS = 16;      // cube rows per unit of the streaming kernel
 constexpr int STREAM2_MAX_NX = 2048;  // widest row the streaming kernel takes
 
@@ -154,6 +155,14 @@ size_t stream3_smem_bytes(int nx, const Blocking &B);
 int stream3_threads();
 int stream3_ctas_per_sm(int nx, const Blocking &B);
 cudaError_t launch_detect3(int variant, const Field &F, const Blocking &B, const Workspace &W, cudaStream_t s,
+                           bool capturing);
+// Raises a kernel's dynamic shared-memory cap to at least `smem` bytes and
+// never lowers it (thread-safe: plans on several host threads share the
+// kernels).  Inside a stream capture a needed raise is an error instead:
+// the first, uncaptured launch of each shape configures it.
+cudaError_t raise_smem_cap(const void *kernel, size_t smem, bool capturing);
+// 2D streaming kernel launch (ftk_detect2.cu; same attribute rule)
+cudaError_t launch_detect2(int variant, const Field &F, const Blocking &B, const Workspace &W, cudaStream_t s,
                            bool capturing);
 // rows of nx floats at src (any alignment) -> rows of pitch floats at dst,
 // columns nx..pitch-1 repeating column nx-1
