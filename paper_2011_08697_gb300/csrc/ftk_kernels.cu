@@ -2,8 +2,8 @@
 //
 // Two forms of paper Algorithm 1 (left column, with Sec. 4.1 / 4.3).
 //
-// Streaming variants (the default; the dense pass is in k_detect2_stream
-// here and k_detect3_stream in ftk_detect3.cu):
+// Streaming variants (the default; the dense pass is k_detect2_stream in
+// ftk_detect2.cu and k_detect3_stream in ftk_detect3.cu):
 //   detect       dense, HBM-bound: stream the field once, quantise
 //                F = rint(f 2^S), integer central-difference gradient, and
 //                cull every spacetime cube exactly -- a gradient component
@@ -999,17 +999,6 @@ __device__ __forceinline__ void uf_unite(int *parent, int a, int b, unsigned *st
         a = old;
     }
     atomicOr(status, ST_TIMEOUT);
-}
-
-__device__ __forceinline__ long long find_face(const long long *face, long long P, long long key) {
-    long long lo = 0, hi = P;
-    while (lo < hi) {
-        const long long mid = (lo + hi) >> 1;
-        const long long v = face[mid];
-        if (v < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return (lo < P && face[lo] == key) ? lo : -1;
 }
 
 template <int N>
