@@ -1587,14 +1587,14 @@ size_t detect_smem_bytes(int ndim, const Field &F, const Blocking &B) {
     return (size_t)L.total;
 }
 
+// four blocks per SM (initialised once, thread-safe)
 static int sparse_grid() {
-    static int g = 0;
-    if (!g) {
+    static const int g = [] {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        g = (sms > 0 ? sms : 148) * 4;
-    }
+        return (sms > 0 ? sms : 148) * 4;
+    }();
     return g;
 }
 
