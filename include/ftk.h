@@ -140,8 +140,11 @@ ftk_status ftk_plan_execute(ftk_plan *plan, const float *f, void *cuda_stream);
 ftk_status ftk_plan_count(ftk_plan *plan, int64_t *count);
 ftk_status ftk_plan_download(ftk_plan *plan, ftk_result **out);
 ftk_status ftk_plan_device_view(ftk_plan *plan, ftk_device_view *view);
-/* Per-stage device times (ms) of the last synchronised execute, in the order
- * detect, scan, finalize, link, label; n = number of entries written. */
+/* Per-stage device times (ms) of the last synchronised execute (plan created
+ * with FTK_FLAG_STAGE_TIMES), five entries: dense detect; survivor
+ * evaluation and the scans (tiled variant: the segment scan); placement,
+ * location and classification (tiled: finalize); linking; labels and
+ * records.  n = number of entries written. */
 ftk_status ftk_plan_stage_times(ftk_plan *plan, float *ms, int cap, int *n);
 ftk_status ftk_plan_destroy(ftk_plan *plan);
 
