@@ -59,9 +59,15 @@ _lib = None
 
 
 def build_clib(force: bool = False) -> str:
-    """Compile ftk_oracle.c into libftk_oracle.so next to it (gcc, -O2)."""
+    """Compile ftk_oracle.c into libftk_oracle.so next to it (gcc, -O2, with
+    OpenMP when the compiler has it; the scan then runs on several threads)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", _SO])
+        tmp = _SO + f".{os.getpid()}.tmp"
+        base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], stdout=subprocess.DEVNULL,
+                          stderr=subprocess.DEVNULL).returncode != 0:
+            subprocess.check_call(base)
+        os.replace(tmp, _SO)
     return _SO
 
 
@@ -80,6 +86,13 @@ def clib():
         lib.oracle_scan.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, i32p,
                                     ctypes.c_int64, ctypes.c_int64, i64p, ctypes.c_int64]
         lib.oracle_scan.restype = ctypes.c_int64
+        lib.oracle_scan_mt.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, i32p,
+                                       ctypes.c_int64, ctypes.c_int64, i64p, ctypes.c_int64, ctypes.c_int]
+        lib.oracle_scan_mt.restype = ctypes.c_int64
+        lib.oracle_max_threads.argtypes = []
+        lib.oracle_max_threads.restype = ctypes.c_int
+        lib.oracle_sos_det_sign_expand.argtypes = [ctypes.c_int, i64p]
+        lib.oracle_sos_det_sign_expand.restype = ctypes.c_int
         lib.oracle_test_faces.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, i32p,
                                           i64p, ctypes.c_int64, i8p]
         lib.oracle_test_faces.restype = None
@@ -283,8 +296,23 @@ def face_punctured(V) -> bool:
     return bool(clib().oracle_face_punctured(n, _p64(V.reshape(-1))))
 
 
-def scan_faces(G: np.ndarray, grid: Grid, t_lo: int = 0, t_hi: int | None = None) -> np.ndarray:
-    """Ids (ascending) of all punctured faces with base slice in [t_lo, t_hi)."""
+def sos_det_sign_expand(M) -> int:
+    """The same sign from the full expansion (every coefficient)."""
+    M = np.asarray(M, dtype=np.int64)
+    n = M.shape[0]
+    colmajor = np.ascontiguousarray(M.T).reshape(-1)
+    return int(clib().oracle_sos_det_sign_expand(n, _p64(colmajor)))
+
+
+def max_threads() -> int:
+    """Threads the C scan can use (1 if it was built without OpenMP)."""
+    return int(clib().oracle_max_threads())
+
+
+def scan_faces(G: np.ndarray, grid: Grid, t_lo: int = 0, t_hi: int | None = None,
+               threads: int = 1) -> np.ndarray:
+    """Ids (ascending) of all punctured faces with base slice in [t_lo, t_hi).
+    ``threads`` > 1 splits the base vertices over OpenMP threads (same ids)."""
     t_hi = grid.dims[-1] if t_hi is None else t_hi
     Gf = np.ascontiguousarray(G.reshape(-1, grid.n).astype(np.int64))
     dims = np.asarray(grid.dims, dtype=np.int64)
@@ -293,9 +321,14 @@ def scan_faces(G: np.ndarray, grid: Grid, t_lo: int = 0, t_hi: int | None = None
     cap = 1 << 16
     while True:
         out = np.empty(cap, dtype=np.int64)
-        cnt = lib.oracle_scan(grid.n, _p64(dims), _p64(Gf), grid.T,
-                              tab.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                              t_lo, t_hi, _p64(out), cap)
+        chp = tab.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        if threads > 1:
+            cnt = lib.oracle_scan_mt(grid.n, _p64(dims), _p64(Gf), grid.T, chp, t_lo, t_hi,
+                                     _p64(out), cap, int(threads))
+            if cnt < 0:
+                raise MemoryError("oracle scan: host allocation failed")
+        else:
+            cnt = lib.oracle_scan(grid.n, _p64(dims), _p64(Gf), grid.T, chp, t_lo, t_hi, _p64(out), cap)
         if cnt <= cap:
             return out[:cnt].copy()
         cap = int(cnt)
@@ -414,20 +447,20 @@ class PairingError(AssertionError):
     """A spacetime cell had a punctured-face count other than 0 or 2."""
 
 
-def link(grid: Grid, punct_ids, cell_filter=None):
-    """Union the punctured sides of every cell that has one; returns
-    {face_id: label} with label = min face id of the component.
+def cell_pairs(grid: Grid, punct_ids, visit=None, cell_filter=None):
+    """Pairs of punctured faces that share a spacetime cell (Algorithm 1,
+    second loop): the cells containing a face of ``visit`` (default: every
+    punctured face) that pass ``cell_filter(base, cell)``, each checked to
+    have 0 or 2 punctured sides (Sec. 4.2, pairing).
 
     Only cells that contain at least one punctured face can contribute, so
     visiting the cofaces of punctured faces visits every such cell.
-    ``cell_filter(base, cell)`` can restrict the cells (streaming prefixes).
     """
     S = set(int(x) for x in punct_ids)
-    uf = UnionFind()
-    for f in S:
-        uf.add(f)
+    todo = sorted(S) if visit is None else sorted(int(x) for x in visit)
     seen = set()
-    for f in sorted(S):
+    pairs = []
+    for f in todo:
         base, chain = grid.decode_face(f)
         for cb, cc in grid.cofaces(base, chain):
             key = (cb, cc)
@@ -441,33 +474,40 @@ def link(grid: Grid, punct_ids, cell_filter=None):
             if len(hit) not in (0, 2):
                 raise PairingError(f"cell {key} has {len(hit)} punctured sides")
             if len(hit) == 2:
-                uf.unite(hit[0], hit[1])
-    return {f: uf.find(f) for f in S}
+                pairs.append((hit[0], hit[1]))
+    return pairs
+
+
+def labels_from_pairs(punct_ids, pairs):
+    """{face_id: label}: components of the faces under the pairs, label =
+    smallest face id of the component."""
+    uf = UnionFind()
+    for f in punct_ids:
+        uf.add(int(f))
+    for a, b in pairs:
+        uf.unite(a, b)
+    return {int(f): uf.find(int(f)) for f in punct_ids}
+
+
+def link(grid: Grid, punct_ids, cell_filter=None):
+    """Union the punctured sides of every cell that has one; returns
+    {face_id: label} with label = min face id of the component.
+    ``cell_filter(base, cell)`` can restrict the cells (streaming prefixes).
+    """
+    S = sorted(set(int(x) for x in punct_ids))
+    return labels_from_pairs(S, cell_pairs(grid, S, cell_filter=cell_filter))
 
 
 # ----------------------------------------------------------------------------
 # Whole pipeline
 # ----------------------------------------------------------------------------
-def track(f: np.ndarray, shift: int = 20, t_lo: int = 0, t_hi: int | None = None,
-          with_types: bool = True, with_links: bool = True):
-    """Exact critical-point tracking of a 2D (nt, ny, nx) or 3D
-    (nt, nz, ny, nx) float32 field.
-
-    Returns a dict of numpy arrays, ordered by face id:
-      face_id (int64), base (int32, [P, 4] = x, y, z, t), off (float64,
-      [P, 4] in-cell offsets), morse (int8), ordinal (uint8), label (int64).
-    ``t_lo/t_hi`` restrict the base slices of the faces (a bounded sample).
-    """
-    f = np.asarray(f, dtype=np.float32)
-    n = f.ndim - 1
-    nt = f.shape[0]
-    dims = tuple(reversed(f.shape[1:]))
-    grid = Grid(dims, nt)
-    F = quantise(f, shift)
-    G = gradient(F, n)
-    ids = scan_faces(G, grid, t_lo, t_hi)
+def describe_punctures(grid: Grid, G: np.ndarray, H, ids):
+    """Location (Eq. 1), ordinal flag and Morse type (Sec. 4.1) of each
+    punctured face in ``ids``; G and H are the gradient / Hessian arrays of
+    the grid's vertices (H may be None: types are then left at -2)."""
+    n = grid.n
     Gflat = G.reshape(-1, n)
-    H = hessian(G, n).reshape(-1, n, n) if with_types else None
+    Hflat = H.reshape(-1, n, n) if H is not None else None
     P = len(ids)
     base = np.zeros((P, 4), dtype=np.int32)
     off = np.zeros((P, 4), dtype=np.float64)
@@ -488,14 +528,136 @@ def track(f: np.ndarray, shift: int = 20, t_lo: int = 0, t_hi: int | None = None
             o = sum(float(mu[k]) for k in range(n + 1) if (ms[k] >> a) & 1)
             off[i, a if a < n else 3] = o
         ordinal[i] = 0 if (chain[-1] & tbit) else 1
-        if with_types:
-            morse[i] = classify(D, [H[g] for g in gids])
+        if Hflat is not None:
+            morse[i] = classify(D, [Hflat[g] for g in gids])
+    return base, off, morse, ordinal
+
+
+def track(f: np.ndarray, shift: int = 20, t_lo: int = 0, t_hi: int | None = None,
+          with_types: bool = True, with_links: bool = True, threads: int = 1):
+    """Exact critical-point tracking of a 2D (nt, ny, nx) or 3D
+    (nt, nz, ny, nx) float32 field.
+
+    Returns a dict of numpy arrays, ordered by face id:
+      face_id (int64), base (int32, [P, 4] = x, y, z, t), off (float64,
+      [P, 4] in-cell offsets), morse (int8), ordinal (uint8), label (int64).
+    ``t_lo/t_hi`` restrict the base slices of the faces (a bounded sample).
+    ``threads`` is passed to the face scan.
+    """
+    f = np.asarray(f, dtype=np.float32)
+    n = f.ndim - 1
+    nt = f.shape[0]
+    dims = tuple(reversed(f.shape[1:]))
+    grid = Grid(dims, nt)
+    F = quantise(f, shift)
+    G = gradient(F, n)
+    ids = scan_faces(G, grid, t_lo, t_hi, threads=threads)
+    H = hessian(G, n) if with_types else None
+    base, off, morse, ordinal = describe_punctures(grid, G, H, ids)
+    P = len(ids)
     label = np.full(P, -1, dtype=np.int64)
     if with_links and P:
         lab = link(grid, ids)
         label = np.asarray([lab[int(x)] for x in ids], dtype=np.int64)
     return dict(face_id=ids, base=base, off=off, morse=morse, ordinal=ordinal,
                 label=label, T=grid.T, grid=grid)
+
+
+# ----------------------------------------------------------------------------
+# The same pipeline spread over host processes, one base slice per task
+# ----------------------------------------------------------------------------
+def _slab_task(args):
+    """Faces with base slice t of the whole field, computed from slices t and
+    t+1 alone: gradients and Hessians are per slice (Sec. 4.3), and a face
+    with base slice t has its vertices in slices t and t+1.  Ids and base t
+    are returned in the whole field's numbering."""
+    f_slab, shift, dims, t = args
+    n = len(dims)
+    sub = Grid(dims, f_slab.shape[0])
+    F = quantise(f_slab, shift)
+    G = gradient(F, n)
+    ids = scan_faces(G, sub, 0, 1)
+    H = hessian(G, n)
+    base, off, morse, ordinal = describe_punctures(sub, G, H, ids)
+    base[:, 3] += t
+    shift_ids = t * sub.stride[-1] * sub.T
+    return ids + shift_ids, base, off, morse, ordinal
+
+
+def _pair_task(args):
+    """Pairs of the cells whose base vertex lies in slice t: their sides are
+    faces with base slice t and ordinal faces of slice t+1."""
+    dims, nt, t, S = args
+    grid = Grid(dims, nt)
+    return cell_pairs(grid, S, cell_filter=lambda cb, cc: cb[-1] == t)
+
+
+def track_parallel(f: np.ndarray, shift: int = 20, workers: int | None = None):
+    """``track`` computed by a pool of host processes (spawned, so the pool
+    is safe next to a CUDA context): one task per base slice for detection,
+    location and types, one task per slice of cells for the pairs, and the
+    union-find over all pairs in this process.  Returns the same arrays as
+    ``track``."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    f = np.asarray(f, dtype=np.float32)
+    n = f.ndim - 1
+    nt = f.shape[0]
+    dims = tuple(reversed(f.shape[1:]))
+    grid = Grid(dims, nt)
+    workers = workers or os.cpu_count() or 1
+    tasks = [(np.ascontiguousarray(f[t:t + 2]), shift, dims, t) for t in range(nt)]
+    # a worker that dies makes the executor raise (a plain Pool would
+    # restart it forever)
+    with ProcessPoolExecutor(max_workers=min(workers, nt), mp_context=mp.get_context("spawn")) as pool:
+        parts = list(pool.map(_slab_task, tasks))
+        ids = np.concatenate([p[0] for p in parts]) if parts else np.zeros(0, np.int64)
+        base = np.concatenate([p[1] for p in parts])
+        off = np.concatenate([p[2] for p in parts])
+        morse = np.concatenate([p[3] for p in parts])
+        ordinal = np.concatenate([p[4] for p in parts])
+        tbit = 1 << n
+        per_t = []
+        for t in range(nt):
+            own = parts[t][0]
+            nxt = []
+            if t + 1 < nt:
+                nb = parts[t + 1][0]
+                types = nb % grid.T
+                chains_last = np.asarray([c[-1] for c in grid.ftypes])
+                nxt = nb[(chains_last[types] & tbit) == 0]
+            per_t.append((dims, nt, t, np.concatenate([own, nxt]).tolist()))
+        pairs = list(pool.map(_pair_task, per_t))
+    label = np.full(len(ids), -1, dtype=np.int64)
+    if len(ids):
+        lab = labels_from_pairs(ids.tolist(), [pr for ps in pairs for pr in ps])
+        label = np.asarray([lab[int(x)] for x in ids], dtype=np.int64)
+    return dict(face_id=ids, base=base, off=off, morse=morse, ordinal=ordinal,
+                label=label, T=grid.T, grid=grid)
+
+
+def _track_task(args):
+    f, shift = args
+    r = track(f, shift=shift)
+    return {k: r[k] for k in ("face_id", "base", "off", "morse", "ordinal", "label")}
+
+
+def track_many(fields, shift: int = 20, workers: int | None = None):
+    """``track`` of many independent fields, one task per field on a pool of
+    spawned host processes; returns one result dict per field (without the
+    grid object)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    workers = workers or os.cpu_count() or 1
+    # largest fields first so that they do not end up last on one worker
+    order = sorted(range(len(fields)), key=lambda i: -np.asarray(fields[i]).size)
+    out = [None] * len(fields)
+    with ProcessPoolExecutor(max_workers=max(1, min(workers, len(fields))),
+                             mp_context=mp.get_context("spawn")) as pool:
+        for i, r in zip(order, pool.map(_track_task, [(np.asarray(fields[i], dtype=np.float32), shift)
+                                                       for i in order])):
+            out[i] = r
+    return out
 
 
 def stream_push_index(grid: Grid, fid: int) -> int:
