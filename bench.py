@@ -43,12 +43,16 @@ WORKLOADS = {
     "batch2d": dict(name="batch_256_blob_fields_N64-512_nt8-32", ndim=2, count=256),
     "serve2d": dict(name="serve_32_streams_N256-2048_poisson200", ndim=2, count=32, rate=200.0),
 }
-# bounded CPU-oracle sample per workload: (spatial dims, slices)
+# bounded CPU-oracle sample per workload: (spatial dims, slices), timed on
+# all host cores (and the single-core sample, where it is smaller)
 ORACLE_SAMPLE = {
     "spiral2d": ((1024, 1024), 2),
-    "blobs3d": ((48, 48, 48), 2),
+    "blobs3d": ((128, 128, 128), 2),
     "batch2d": ((128, 128), 8),
     "serve2d": ((512, 512), 2),
+}
+SINGLE_SAMPLE = {
+    "blobs3d": ((64, 64, 64), 2),
 }
 
 
@@ -86,11 +90,12 @@ def make_field(wl: str, seed: int, dims=None, nt=None):
     return synth.gaussian_blobs(dims, nt, nblobs=32, seed=seed)
 
 
-def sample_field(wl: str, seed: int):
+def sample_field(wl: str, seed: int, single: bool = False):
     """The bounded oracle sample: the same generator law on a smaller grid /
-    fewer slices (spiral: the first slices of the full field)."""
+    fewer slices (spiral and blobs at full size: the first slices of the full
+    field)."""
     from paper_2011_08697_gb300 import synth
-    dims, s = ORACLE_SAMPLE[wl]
+    dims, s = (SINGLE_SAMPLE.get(wl, ORACLE_SAMPLE[wl]) if single else ORACLE_SAMPLE[wl])
     if wl == "spiral2d":
         return synth.spiral_woven(dims[0], WORKLOADS[wl]["nt"], sigma=1e-3, seed=seed,
                                   ny=dims[1], k_stop=s)
@@ -189,28 +194,33 @@ def profiled_traffic(wl: str):
         return None
 
 
-def run_oracle_sample(wl: str, seed: int = 0):
+def run_oracle_sample(wl: str, seed: int = 0, threads: int = 1, single: bool = False):
+    """The oracle on a bounded sample (``single``: the single-core sample);
+    ``threads`` OpenMP threads for the face scan."""
     from oracle import cp
-    f = sample_field(wl, seed)
-    dims, s = ORACLE_SAMPLE[wl]
+    f = sample_field(wl, seed, single)
+    dims, s = (SINGLE_SAMPLE.get(wl, ORACLE_SAMPLE[wl]) if single else ORACLE_SAMPLE[wl])
     t0 = time.perf_counter()
-    r = cp.track(f)
+    r = cp.track(f, threads=threads)
     dt = time.perf_counter() - t0
     return face_count(dims, s), dt, r
 
 
 def reference_arm(args):
+    """The oracle as it stands, timed on all host cores (OpenMP face scan) on
+    a bounded sample of the workload per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     wl = args.workload
     dims, s = ORACLE_SAMPLE[wl]
+    ncpu = os.cpu_count() or 1
     for _ in range(args.warmup):
-        run_oracle_sample(wl)
+        run_oracle_sample(wl, threads=ncpu)
     times = []
     faces = 0
     for _ in range(args.steps):
-        faces, dt, _ = run_oracle_sample(wl)
+        faces, dt, _ = run_oracle_sample(wl, threads=ncpu)
         times.append(dt)
     tot = sum(times)
     value = faces * args.steps / tot
@@ -225,8 +235,8 @@ def reference_arm(args):
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i64", "data": "synthetic",
         "config": {"workload": WORKLOADS[wl]["name"], "sample": sample},
-        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": ncpu, "kind": "oracle",
+                         "sample": sample + f", face scan on {ncpu} OpenMP threads"},
         "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -293,11 +303,23 @@ def _oracle_check(res, f) -> bool:
                 and (len(ref["face_id"]) == 0 or float(np.max(np.abs(res["off"] - ref["off"]))) <= 1e-5))
 
 
-def _cpu_baseline(wl):
-    fs, dt, _ = run_oracle_sample(wl, seed=0)
-    dims, sl = ORACLE_SAMPLE[wl]
+def _cpu_baseline_single(wl):
+    """The oracle on one core over the bounded single-core sample."""
+    fs, dt, _ = run_oracle_sample(wl, seed=0, threads=1, single=True)
+    dims, sl = SINGLE_SAMPLE.get(wl, ORACLE_SAMPLE[wl])
     return {"value": fs / dt, "unit": "simplices/s", "cores": 1, "kind": "oracle",
             "sample": f"{'x'.join(map(str, dims))} grid x {sl} slices ({fs} faces), same generator law"}
+
+
+def _cpu_baseline(wl):
+    """The oracle on all host cores (OpenMP face scan) over the bounded
+    sample, with the single-core figure beside it."""
+    ncpu = os.cpu_count() or 1
+    fs, dt, _ = run_oracle_sample(wl, seed=0, threads=ncpu)
+    dims, sl = ORACLE_SAMPLE[wl]
+    return {"value": fs / dt, "unit": "simplices/s", "cores": ncpu, "kind": "oracle",
+            "sample": f"{'x'.join(map(str, dims))} grid x {sl} slices ({fs} faces), same generator law",
+            "single_core": _cpu_baseline_single(wl)}
 
 
 def batch_arm(args):
@@ -652,16 +674,40 @@ def serve_arm(args):
         dist.destroy_process_group()
 
 
-def gpu_arm(args):
+def _pinned_records(n: int):
+    """A CP_DTYPE numpy array of n records in pinned host memory (and the
+    tensor that owns the memory)."""
     import torch
-    from paper_2011_08697_gb300 import build as _b, ftk
+    from paper_2011_08697_gb300 import ftk
+    t = torch.empty(max(1, n) * ftk.CP_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    return t.numpy().view(ftk.CP_DTYPE), t
 
-    dist, rank, world, local = _dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    _b.build()
-    ftk.lib()
-    wl = args.workload
+
+def _full_oracle_check(res, f):
+    """Whole-workload parity against the oracle on all host cores: punctured
+    set, Morse index, ordinal flag, base vertex and label equal, offsets
+    within 1e-5 of a cell.  Returns (report, oracle seconds, faces)."""
+    from oracle import cp
+    t0 = time.perf_counter()
+    ref = cp.track_parallel(f)
+    dt = time.perf_counter() - t0
+    ok = bool(np.array_equal(res["face_id"], ref["face_id"]))
+    err = None
+    if ok:
+        ok = all(np.array_equal(res[a], ref[b]) for a, b in
+                 (("morse_index", "morse"), ("ordinal", "ordinal"), ("base", "base"), ("label", "label")))
+        err = float(np.max(np.abs(res["off"] - ref["off"]))) if len(res) else 0.0
+        ok = ok and err <= 1e-5
+    return {"full_workload": ok, "punctures": int(len(ref["face_id"])), "max_offset_err": err,
+            "compared": "face ids, Morse index, ordinal flag, base vertex, label: equal; offsets <= 1e-5 cell"}, dt
+
+
+def _measure_plain(wl, args, dev, dist, world, rank, local):
+    """One plain-path workload: K timed steps (L2 flushed between steps), the
+    dominant kernel's live duration, end to end through the C ABI with pinned
+    host buffers."""
+    import torch
+    from paper_2011_08697_gb300 import ftk
     W = WORKLOADS[wl]
     f_np = make_field(wl, seed=shard_seed(wl, rank))
     nverts = f_np.size
@@ -669,7 +715,6 @@ def gpu_arm(args):
     x = torch.from_numpy(f_np).to(dev)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
-
     plan = ftk.Plan(f_np.shape)
     timed_plan = ftk.Plan(f_np.shape, ftk.make_params(flags=ftk.FTK_FLAG_STAGE_TIMES))
 
@@ -692,7 +737,6 @@ def gpu_arm(args):
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        t_wall = time.perf_counter()
         with torch.cuda.stream(stream):
             for k in range(args.steps):
                 flush.zero_()
@@ -700,17 +744,13 @@ def gpu_arm(args):
                 plan.execute(x, stream)
                 ends[k].record(stream)
         torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall
     barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    P_check = plan.count()
-    assert P_check == P, "puncture count changed between steps"
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    assert plan.count() == P, "puncture count changed between steps"
     tot_ms = _max_over_ranks(dist, sum(step_ms))
-    value = weak_value(faces, world, args.steps, tot_ms)
 
-    # ---- roofline of the dominant kernel (detect), live CUDA events ---------
-    det = []
-    stages = []
+    # ---- the dominant kernel (detect), live CUDA events on its stream ------
+    det, stages = [], []
     with torch.cuda.stream(stream):
         for k in range(max(3, min(args.steps, 20))):
             flush.zero_()
@@ -729,70 +769,106 @@ def gpu_arm(args):
     alg_bytes = 4.0 * nverts
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (det_ms / 1e3) / 1e9
+    step_mean = tot_ms / args.steps
 
-    # ---- end to end through the C ABI with pinned host buffers -------------
+    # ---- end to end through the C ABI: pinned host field in, records out ---
     host = torch.from_numpy(f_np).pin_memory()
+    outbuf, _keep = _pinned_records(int(P) + 1024)
     e2e_plan = ftk.Plan(f_np.shape)
     with torch.cuda.stream(stream):
         e2e_plan.execute(host, stream)
-        e2e_plan.download()
+        e2e_plan.download_into(outbuf)
         torch.cuda.synchronize()
+        barrier()
         t0 = time.perf_counter()
         for k in range(args.steps):
             e2e_plan.execute(host, stream)
-            r = e2e_plan.download()
+            r = e2e_plan.download_into(outbuf)
         e2e_s = time.perf_counter() - t0
+    assert len(r) == P
     e2e_val = weak_value(faces, world, args.steps, 1e3 * _max_over_ranks(dist, e2e_s))
-
-    # ---- bit-exact self-check on the oracle's bounded sample + CPU baseline --
-    cpu = None
-    exact = None
-    if rank == 0 and world == 1 and wl == "spiral2d":
-        fs, dt, ref = run_oracle_sample(wl, seed=0)
-        sel = (res["base"][:, 3] == 0) | ((res["base"][:, 3] == 1) & (res["ordinal"] == 1))
-        exact = bool(np.array_equal(res["face_id"][sel], ref["face_id"])
-                     and np.array_equal(res["morse_index"][sel], ref["morse"]))
-        dims, s = ORACLE_SAMPLE[wl]
-        cpu = {"value": fs / dt, "unit": "simplices/s", "cores": 1, "kind": "oracle",
-               "sample": f"{'x'.join(map(str, dims))} grid x {s} slices ({fs} faces), first slices of the workload"}
-    elif rank == 0 and world == 1:
-        fs, dt, _ = run_oracle_sample(wl, seed=0)
-        dims, s = ORACLE_SAMPLE[wl]
-        cpu = {"value": fs / dt, "unit": "simplices/s", "cores": 1, "kind": "oracle",
-               "sample": f"{'x'.join(map(str, dims))} grid x {s} slices ({fs} faces), same generator law"}
-
-    if rank == 0:
-        sm = sorted(step_ms)
-        p99 = sm[min(len(sm) - 1, int(round(0.99 * (len(sm) - 1))))]
-        line = {
-            "metric": METRIC, "value": value, "unit": "simplices/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
-            "data": "synthetic",
-            "config": {"workload": W["name"], "grid": list(W["dims"]), "nt": W["nt"],
-                       "faces_per_step": faces, "vertices_per_step": nverts,
-                       "l2": "256 MB buffer written between steps (L2 flushed); steps timed individually",
-                       "parallelism": f"replicas{world}" if world > 1 else "single"},
-            "timesteps_per_s": W["nt"] * world * args.steps / (tot_ms / 1e3),
-            "p50_step_ms": statistics.median(step_ms), "p99_step_ms": p99,
-            "punctures": int(P), "trajectories": int(len(np.unique(res["label"]))),
-            "bit_exact_sample": exact,
-            "stages_ms": {k: statistics.mean(s[i] for s in stages) for i, k in enumerate(stage_names)},
-            "plan": desc,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(wl),
-                         "kernel": detect_kernel, "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": det_ms},
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": "simplices/s",
-                    "h2d_bytes_per_step": int(nverts * 4), "d2h_bytes_per_step": int(P * 56 + 24)},
-            "gpu_launches": int(desc["kernels_per_execute"]) * args.steps,
-            "clocks": clk.summary(),
-        }
-        print(json.dumps(line), flush=True)
     plan.close()
     timed_plan.close()
     e2e_plan.close()
+    sm = sorted(step_ms)
+    return dict(
+        W=W, f_np=f_np, res=res, P=int(P), faces=faces, nverts=nverts, desc=desc, clocks=clk.summary(),
+        value=weak_value(faces, world, args.steps, tot_ms), tot_ms=tot_ms, step_ms=step_ms,
+        p99=sm[min(len(sm) - 1, int(round(0.99 * (len(sm) - 1))))],
+        stages={k: statistics.mean(s[i] for s in stages) for i, k in enumerate(stage_names)},
+        roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                  "frac": achieved / peak, "traffic": profiled_traffic(wl),
+                  "kernel": detect_kernel, "peak_kind": peak_kind,
+                  "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": det_ms,
+                  "whole_step_frac": (alg_bytes / (step_mean / 1e3) / 1e9) / peak},
+        e2e={"value": e2e_val, "unit": "simplices/s", "ms_per_step": 1e3 * e2e_s / args.steps,
+             "h2d_bytes_per_step": int(nverts * 4), "d2h_bytes_per_step": int(P * 56 + 24),
+             "form": "plan execute from a pinned host field + download_into a pinned record buffer"},
+        gpu_launches=int(desc["kernels_per_execute"]) * args.steps,
+    )
+
+
+def gpu_arm(args):
+    import torch
+    from paper_2011_08697_gb300 import build as _b, ftk
+
+    dist, rank, world, local = _dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _b.build()
+    ftk.lib()
+    wl = args.workload
+    m = _measure_plain(wl, args, dev, dist, world, rank, local)
+    extra = None
+    if args.with_2d and wl == "blobs3d":
+        extra = _measure_plain("spiral2d", args, dev, dist, world, rank, local)
+
+    if rank == 0:
+        W = m["W"]
+        line = {
+            "metric": METRIC, "value": m["value"], "unit": "simplices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["tot_ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": W["name"], "grid": list(W["dims"]), "nt": W["nt"],
+                       "faces_per_step": m["faces"], "vertices_per_step": m["nverts"],
+                       "l2": "256 MB buffer written between steps (L2 flushed); steps timed individually",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "timesteps_per_s": W["nt"] * world * args.steps / (m["tot_ms"] / 1e3),
+            "p50_step_ms": statistics.median(m["step_ms"]), "p99_step_ms": m["p99"],
+            "punctures": m["P"], "trajectories": int(len(np.unique(m["res"]["label"]))),
+            "stages_ms": m["stages"], "plan": m["desc"], "roofline": m["roofline"],
+            "e2e": m["e2e"], "gpu_launches": m["gpu_launches"] + (extra["gpu_launches"] if extra else 0),
+            "clocks": m["clocks"],
+        }
+        if extra is not None:
+            E = extra["W"]
+            line["spiral2d"] = {
+                "workload": E["name"], "value": extra["value"], "unit": "simplices/s",
+                "ms_per_step": extra["tot_ms"] / args.steps, "p99_step_ms": extra["p99"],
+                "timesteps_per_s": E["nt"] * world * args.steps / (extra["tot_ms"] / 1e3),
+                "punctures": extra["P"], "stages_ms": extra["stages"], "plan": extra["desc"],
+                "roofline": extra["roofline"], "e2e": extra["e2e"], "clocks": extra["clocks"],
+                "gpu_launches": extra["gpu_launches"],
+            }
+        if world == 1:
+            # the oracle on the full workload, all host cores: the bit-exact
+            # check and the all-core CPU baseline in one run
+            rep, dt = _full_oracle_check(m["res"], m["f_np"])
+            line["bit_exact"] = rep
+            ncpu = os.cpu_count() or 1
+            single = _cpu_baseline_single(wl)
+            line["cpu_baseline"] = {
+                "value": m["faces"] / dt, "unit": "simplices/s", "cores": ncpu, "kind": "oracle",
+                "sample": f"the full workload ({m['faces']} faces), one process per base slice on {ncpu} cores",
+                "seconds": dt, "single_core": single}
+            if extra is not None:
+                rep2, dt2 = _full_oracle_check(extra["res"], extra["f_np"])
+                line["spiral2d"]["bit_exact"] = rep2
+                line["spiral2d"]["cpu_baseline"] = {
+                    "value": extra["faces"] / dt2, "unit": "simplices/s", "cores": ncpu, "kind": "oracle",
+                    "sample": "the full workload", "seconds": dt2}
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -803,7 +879,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=list(WORKLOADS), default="spiral2d")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="blobs3d")
+    ap.add_argument("--no-2d", dest="with_2d", action="store_false",
+                    help="blobs3d: skip the 2D spiral workload reported beside it")
     ap.add_argument("--duration", type=float, default=60.0, help="serve2d: Poisson phase seconds")
     ap.add_argument("--sat-pushes", type=int, default=24, help="serve2d: saturated pushes per stream")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="serve2d: admission budget")

@@ -132,13 +132,20 @@ void          ftk_result_free(ftk_result *r);
  * pointer or a host pointer (copied to a plan-owned device buffer on the
  * same stream).  ftk_plan_count / ftk_plan_download synchronise the plan's
  * last stream, re-run the pipeline with a larger capacity if the punctures
- * outgrew it, and report device-side errors.
+ * outgrew it, and report device-side errors.  With a host pointer f,
+ * ftk_plan_execute returns once the copy of f has completed (the caller may
+ * then overwrite f); the pipeline itself may still be running.
  * ------------------------------------------------------------------- */
 ftk_status ftk_plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt,
                            const ftk_params *p, ftk_plan **plan);
 ftk_status ftk_plan_execute(ftk_plan *plan, const float *f, void *cuda_stream);
 ftk_status ftk_plan_count(ftk_plan *plan, int64_t *count);
 ftk_status ftk_plan_download(ftk_plan *plan, ftk_result **out);
+/* Copies the last execute's records (sorted by face_id) into a caller-owned
+ * host buffer of cap records (pinned memory gives the full link speed);
+ * *count receives the number of punctures.  More punctures than cap:
+ * FTK_ERR_NOMEM with *count set and nothing copied.  Synchronises. */
+ftk_status ftk_plan_download_into(ftk_plan *plan, ftk_cp *dst, int64_t cap, int64_t *count);
 ftk_status ftk_plan_device_view(ftk_plan *plan, ftk_device_view *view);
 /* Per-stage device times (ms) of the last synchronised execute (plan created
  * with FTK_FLAG_STAGE_TIMES), five entries: dense detect; survivor

@@ -546,7 +546,24 @@ ftk_status ftk_plan_execute(ftk_plan *pl, const float *f, void *cuda_stream) {
     pl->last_f = f;
     pl->last_dev = src;
     pl->last_host = host;
-    return launch(pl, src, s, pl->variant);
+    cudaEvent_t copied = nullptr;
+    if (host) {
+        // the host buffer may be reused as soon as this call returns: wait for
+        // the copy (not for the pipeline queued behind it)
+        if (!pl->copy_ev) {
+            cudaError_t e = cudaEventCreateWithFlags(&pl->copy_ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(e, "event creation");
+        }
+        copied = pl->copy_ev;
+        cudaError_t e = cudaEventRecord(copied, s);
+        if (e != cudaSuccess) return cuda_fail(e, "event record");
+    }
+    st = launch(pl, src, s, pl->variant);
+    if (copied) {
+        cudaError_t e = cudaEventSynchronize(copied);
+        if (e != cudaSuccess && st == FTK_OK) st = cuda_fail(e, "input copy");
+    }
+    return st;
 }
 
 ftk_status ftk_plan_count(ftk_plan *pl, int64_t *count) {
@@ -563,6 +580,22 @@ ftk_status ftk_plan_download(ftk_plan *pl, ftk_result **out) {
     ftk_status s = settle(pl);
     if (s != FTK_OK) return s;
     return make_result(pl, out);
+}
+
+ftk_status ftk_plan_download_into(ftk_plan *pl, ftk_cp *dst, int64_t cap, int64_t *count) {
+    if (!pl || !count || (cap > 0 && !dst) || cap < 0) return fail(FTK_ERR_ARG, "invalid argument");
+    *count = 0;
+    ftk_status s = settle(pl);
+    if (s != FTK_OK) return s;
+    const long long P = pl->h_ctr->punctures;
+    *count = P;
+    if (P > cap) return fail(FTK_ERR_NOMEM, "the output buffer holds fewer records than there are punctures");
+    if (P > 0) {
+        cudaError_t e = cudaMemcpyAsync(dst, pl->W.packed, (size_t)P * sizeof(ftk_cp), cudaMemcpyDeviceToHost, pl->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "result download");
+    }
+    return FTK_OK;
 }
 
 ftk_status ftk_plan_device_view(ftk_plan *pl, ftk_device_view *v) {
@@ -606,6 +639,7 @@ ftk_status ftk_plan_destroy(ftk_plan *pl) {
     if (pl->h_ctr) cudaFreeHost(pl->h_ctr);
     if (pl->timing)
         for (int i = 0; i < 6; ++i) cudaEventDestroy(pl->ev[i]);
+    if (pl->copy_ev) cudaEventDestroy(pl->copy_ev);
     delete pl;
     return FTK_OK;
 }

@@ -32,6 +32,7 @@ struct ftk_plan {
     bool executed;
     bool timing;
     cudaEvent_t ev[6];
+    cudaEvent_t copy_ev;       // end of the host-input copy of the last execute
     float stage_ms[5];
     int nstage;
 };

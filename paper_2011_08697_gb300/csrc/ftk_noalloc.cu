@@ -37,13 +37,21 @@ ftk_status cuda_err(cudaError_t e, const char *what) {
     return err(FTK_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// device memory of the current device (whose scratch array and kernels the
+// call uses), or managed memory
 bool on_device(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // one-time set-up per device: the scratch array's device address
@@ -81,7 +89,7 @@ extern "C" ftk_status ftk_track_cp2d_noalloc(const float *f_dev, int64_t nx, int
     if (prm.quant_shift < 0 || prm.quant_shift > 40) return err(FTK_ERR_ARG, "quant_shift must lie in [0, 40]");
     if (prm.flags != 0) return err(FTK_ERR_ARG, "no flags are supported by the no-alloc entry point");
     if (!on_device(f_dev) || !on_device(out_dev))
-        return err(FTK_ERR_ARG, "f_dev and out_dev must be device pointers");
+        return err(FTK_ERR_ARG, "f_dev and out_dev must be device pointers on the current device");
 
     unsigned char *base = nullptr;
     ftk_status s = scratch_base(&base);
@@ -150,10 +158,11 @@ extern "C" ftk_status ftk_track_cp2d_noalloc(const float *f_dev, int64_t nx, int
     cudaStream_t st = (cudaStream_t)cuda_stream;
     cudaError_t e = launch_pipeline(2, VAR_TILE, F, B, W, st, nullptr);
     if (e != cudaSuccess) return cuda_err(e, "pipeline launch");
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_err(e, "cudaStreamSynchronize");
+    // counters read back on the caller's stream (no legacy-stream copy, which
+    // would wait for every blocking stream of the context)
     RunCounters h;
-    e = cudaMemcpy(&h, W.ctr, sizeof(h), cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(&h, W.ctr, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_err(e, "counter read-back");
     *count = h.punctures;
     if (h.status & ST_RANGE)

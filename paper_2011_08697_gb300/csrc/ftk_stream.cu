@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -86,11 +87,14 @@ struct ftk_stream {
 
 namespace {
 
+// capacity an array grows to when it must hold `need` entries
+long long grow_cap(long long need) { return std::max<long long>(need + need / 2, 1 << 12); }
+
 template <typename T>
 ftk_status grow(T **ptr, long long cap, long long need, long long keep, cudaStream_t s, long long *newcap) {
     *newcap = cap;
     if (need <= cap) return FTK_OK;
-    long long nc = std::max<long long>(need + need / 2, 1 << 12);
+    long long nc = grow_cap(need);
     T *np = nullptr;
     if (cudaMalloc(&np, sizeof(T) * nc) != cudaSuccess) {
         cudaGetLastError();
@@ -112,45 +116,75 @@ void drop_graph(ftk_stream *st) {
     st->exec = nullptr;
 }
 
-void account(ftk_stream *st, size_t add) {
-    st->footprint += add;
+// reserves `add` more bytes of device memory for the stream: within the
+// server's budget (checked and charged under its mutex), else FTK_ERR_BUSY
+ftk_status reserve(ftk_stream *st, size_t add) {
     if (st->server) {
         std::lock_guard<std::mutex> lock(st->server->mu);
+        if (st->server->used + add > st->server->budget)
+            return fail(FTK_ERR_BUSY, "the stream's device state would grow past the server's memory budget (" +
+                                          std::to_string(add) + " more bytes)");
         st->server->used += add;
     }
+    st->footprint += add;
+    return FTK_OK;
+}
+
+void unreserve(ftk_stream *st, size_t sub) {
+    if (st->server) {
+        std::lock_guard<std::mutex> lock(st->server->mu);
+        st->server->used -= std::min(st->server->used, sub);
+    }
+    st->footprint -= std::min(st->footprint, sub);
 }
 
 // every per-push array sized for a run of up to cap punctures on top of the
-// n slots in use; a reallocation invalidates the captured push
+// n slots in use; a reallocation invalidates the captured push.  Growth is
+// charged to the server's budget before any allocation (FTK_ERR_BUSY when it
+// does not fit); slot indices are 32-bit, so n + cap must stay below 2^31.
 ftk_status ensure_all(ftk_stream *st, long long cap) {
     ftk_status s;
     const long long need = st->n + cap;
+    if (need > INT_MAX)
+        return fail(FTK_ERR_RANGE, "the stream holds too many punctures for its 32-bit union-find slots");
     if (need > st->acap) {
+        const size_t add = (size_t)(grow_cap(need) - st->acap) * (8 + 4 + 8 + 4 + sizeof(ftk_cp));
+        if ((s = reserve(st, add)) != FTK_OK) return s;
         long long c0, c1, c2, c3, c4;
         if ((s = grow(&st->gfid, st->acap, need, st->n, st->cs, &c0)) != FTK_OK ||
             (s = grow(&st->gparent, st->acap, need, st->n, st->cs, &c1)) != FTK_OK ||
             (s = grow(&st->gmin, st->acap, need, st->n, st->cs, &c2)) != FTK_OK ||
             (s = grow(&st->gshadow, st->acap, need, st->n, st->cs, &c3)) != FTK_OK ||
-            (s = grow(&st->grec, st->acap, need, st->n, st->cs, &c4)) != FTK_OK)
+            (s = grow(&st->grec, st->acap, need, st->n, st->cs, &c4)) != FTK_OK) {
+            // arrays that did grow keep their new size; what was charged for
+            // the rest is returned, and the next call grows them again
+            unreserve(st, add);
             return s;
-        account(st, (size_t)(c0 - st->acap) * (8 + 4 + 8 + 4 + sizeof(ftk_cp)));
+        }
         st->acap = c0;
         drop_graph(st);
     }
     if (cap > st->lcap) {
+        const size_t add = (size_t)(grow_cap(cap) - st->lcap) * 8;
+        if ((s = reserve(st, add)) != FTK_OK) return s;
         long long a, b;
         if ((s = grow(&st->link_prev, st->lcap, cap, 0, st->cs, &a)) != FTK_OK ||
-            (s = grow(&st->old_root, st->lcap, cap, 0, st->cs, &b)) != FTK_OK)
+            (s = grow(&st->old_root, st->lcap, cap, 0, st->cs, &b)) != FTK_OK) {
+            unreserve(st, add);
             return s;
-        account(st, (size_t)(a - st->lcap) * 8);
+        }
         st->lcap = a;
         drop_graph(st);
     }
     const long long nblk = 4 * (cap / DELTA_BLOCK + 1);
     if (nblk > st->bcap) {
+        const size_t add = (size_t)(grow_cap(nblk) - st->bcap) * 8;
+        if ((s = reserve(st, add)) != FTK_OK) return s;
         long long a;
-        if ((s = grow(&st->blk, st->bcap, nblk, 0, st->cs, &a)) != FTK_OK) return s;
-        account(st, (size_t)(a - st->bcap) * 8);
+        if ((s = grow(&st->blk, st->bcap, nblk, 0, st->cs, &a)) != FTK_OK) {
+            unreserve(st, add);
+            return s;
+        }
         st->bcap = a;
         drop_graph(st);
     }
@@ -159,13 +193,16 @@ ftk_status ensure_all(ftk_stream *st, long long cap) {
         const int keep = (int)((st->k - 1) & 1);
         long long nk = 0;
         if (st->k > 0) cudaMemcpy(&nk, &st->dS->n_ord[keep], sizeof(long long), cudaMemcpyDeviceToHost);
+        const size_t add = (size_t)(grow_cap(cap) - st->ocap) * 24;
+        if ((s = reserve(st, add)) != FTK_OK) return s;
         long long a = 0, b = 0;
         for (int q = 0; q < 2; ++q) {
             if ((s = grow(&st->ord_fid[q], st->ocap, cap, q == keep ? nk : 0, st->cs, &a)) != FTK_OK ||
-                (s = grow(&st->ord_gi[q], st->ocap, cap, q == keep ? nk : 0, st->cs, &b)) != FTK_OK)
+                (s = grow(&st->ord_gi[q], st->ocap, cap, q == keep ? nk : 0, st->cs, &b)) != FTK_OK) {
+                unreserve(st, add);
                 return s;
+            }
         }
-        account(st, (size_t)(a - st->ocap) * 24);
         st->ocap = a;
         drop_graph(st);
     }
@@ -347,6 +384,12 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
     }
     st->footprint = sizeof(float) * 2 * st->slice_elems + plan_bytes(st->plan1) + plan_bytes(st->plan2) +
                     sizeof(uint32_t) * 2 * (size_t)st->st_words;
+    // the union-find and delta arrays for the first pushes are part of the
+    // footprint admission checks (later growth is charged push by push)
+    if ((s = ensure_all(st, std::max(st->plan1->W.cap, st->plan2->W.cap))) != FTK_OK) {
+        release(st);
+        return s;
+    }
     if (srv) {
         std::lock_guard<std::mutex> lock(srv->mu);
         if (srv->used + st->footprint > srv->budget) {

@@ -61,7 +61,7 @@ EXPORTS = [
     "ftk_params_default", "ftk_status_string", "ftk_last_error", "ftk_version",
     "ftk_track_cp2d", "ftk_track_cp3d", "ftk_result_count", "ftk_result_data",
     "ftk_result_free", "ftk_plan_create", "ftk_plan_execute", "ftk_plan_count",
-    "ftk_plan_download", "ftk_plan_device_view", "ftk_plan_stage_times", "ftk_plan_destroy",
+    "ftk_plan_download", "ftk_plan_download_into", "ftk_plan_device_view", "ftk_plan_stage_times", "ftk_plan_destroy",
     "ftk_track_cp2d_noalloc",
     "ftk_batch_create", "ftk_batch_execute", "ftk_batch_counts", "ftk_batch_download",
     "ftk_batch_destroy", "ftk_track_cp2d_batch", "ftk_plan_describe", "ftk_batch_kernels",
@@ -95,6 +95,7 @@ def lib():
         "ftk_plan_execute": (i32, [vp, vp, vp]),
         "ftk_plan_count": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ftk_plan_download": (i32, [vp, pp]),
+        "ftk_plan_download_into": (i32, [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)]),
         "ftk_plan_device_view": (i32, [vp, ctypes.POINTER(ftk_device_view)]),
         "ftk_plan_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
         "ftk_plan_destroy": (i32, [vp]),
@@ -162,17 +163,31 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+class _ResultOwner:
+    """Frees an ftk_result when the array viewing its records is released."""
+
+    def __init__(self, rp):
+        self.rp = rp
+
+    def __del__(self):
+        try:
+            lib().ftk_result_free(self.rp)
+        except Exception:
+            pass
+
+
 def _take_result(rp) -> np.ndarray:
+    """A structured array viewing the result's records in place (no copy);
+    the result is freed with the last reference to the array."""
     L = lib()
-    try:
-        n = L.ftk_result_count(rp)
-        data = L.ftk_result_data(rp)
-        out = np.empty(n, dtype=CP_DTYPE)
-        if n:
-            ctypes.memmove(out.ctypes.data, data, n * CP_DTYPE.itemsize)
-        return out
-    finally:
-        L.ftk_result_free(rp)
+    owner = _ResultOwner(rp)
+    n = L.ftk_result_count(rp)
+    if n == 0:
+        return np.empty(0, dtype=CP_DTYPE)
+    data = L.ftk_result_data(rp)
+    raw = (ctypes.c_char * (n * CP_DTYPE.itemsize)).from_address(data)
+    raw.owner = owner
+    return np.frombuffer(raw, dtype=CP_DTYPE)
 
 
 def ftk_track_cp2d(f, params: ftk_params | None = None, stream=None) -> np.ndarray:
@@ -237,6 +252,15 @@ class Plan:
         out = ctypes.c_void_p()
         _check(lib().ftk_plan_download(self._h, ctypes.byref(out)))
         return _take_result(out)
+
+    def download_into(self, buf: np.ndarray) -> np.ndarray:
+        """Records of the last execute copied into ``buf`` (a CP_DTYPE array,
+        ideally in pinned memory); returns the filled prefix of buf."""
+        if buf.dtype != CP_DTYPE or not buf.flags.c_contiguous:
+            raise ValueError("buffer must be a contiguous CP_DTYPE array")
+        c = ctypes.c_int64()
+        _check(lib().ftk_plan_download_into(self._h, ctypes.c_void_p(buf.ctypes.data), len(buf), ctypes.byref(c)))
+        return buf[: c.value]
 
     def device_view(self) -> ftk_device_view:
         v = ftk_device_view()

@@ -19,9 +19,9 @@ pytestmark = pytest.mark.gpu
 OFF_TOL = 1e-5   # the tolerance the parity tests use for locations
 
 
-def _noalloc(F, x, cap):
+def _noalloc(F, x, cap, dims=None):
     L = F.lib()
-    nt, ny, nx = x.shape
+    nt, ny, nx = dims if dims is not None else x.shape
     out = torch.empty(max(cap, 1) * F.CP_DTYPE.itemsize, dtype=torch.uint8, device=x.device)
     cnt = ctypes.c_int64(-1)
     p = F.make_params()
@@ -69,3 +69,38 @@ def test_noalloc_reports_short_output_buffer():
     st, n, got = _noalloc(F, x, cap=len(ref))
     assert st == 0
     _same(got, ref)
+
+
+def test_noalloc_odd_shapes_and_no_device_allocation():
+    """Odd widths and heights (the tiled kernel reads them in place), and
+    device free memory unchanged across calls once the kernels are loaded."""
+    from paper_2011_08697_gb300 import build, ftk as F
+    build.build()
+    for f in (synth.random_levels((5, 17, 33), seed=5),
+              synth.spiral_woven(37, 6, sigma=0.02, seed=1, ny=29)):
+        x = torch.from_numpy(f).cuda()
+        ref = F.ftk_track_cp2d(x)
+        st, n, got = _noalloc(F, x, cap=len(ref) + 3)
+        assert st == 0, F.lib().ftk_last_error()
+        _same(got, ref)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(2):
+            st, n, got = _noalloc(F, x, cap=len(ref) + 3)
+            assert st == 0
+            _same(got, ref)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_noalloc_rejects_grids_beyond_its_limits():
+    from paper_2011_08697_gb300 import build, ftk as F
+    build.build()
+    # more segments (nt * ceil(ny / rows per tile)) than FTK_NOALLOC_MAX_SEGMENTS
+    x = torch.zeros((300_000, 2, 4), dtype=torch.float32, device="cuda")
+    st, n, _ = _noalloc(F, x, cap=16)
+    assert st == 1 and n == 0
+    # rows too wide for the detect tile
+    x = torch.zeros((1, 2, 4000), dtype=torch.float32, device="cuda")
+    st, n, _ = _noalloc(F, x, cap=16)
+    assert st == 1 and n == 0
