@@ -466,9 +466,6 @@ def serve_arm(args):
     """In-situ serving: 32 streams, slices arriving as a Poisson process;
     per-slice latency at that load, then saturated throughput against the
     plain path run on the same slabs one at a time."""
-    import queue
-    import threading
-
     # one hardware work queue per concurrent stream (the default 8 would make
     # unrelated streams wait on each other); read when CUDA initialises
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
@@ -498,70 +495,52 @@ def serve_arm(args):
 
     budget = int(args.serve_budget_gb * (1 << 30))
     server = ftk.Server(budget)
-    streams = [ftk.Stream((n, n), server=server) for n, _ in specs]
+    streams = [ftk.Stream((n, n), server=server, wait_ms=60_000) for n, _ in specs]
     footprint_open = server.used()
-    lat_poisson = [[] for _ in range(ns)]
-    lat_sat = [[] for _ in range(ns)]
-    done_sat = [0.0] * ns
-    qs = [queue.Queue() for _ in range(ns)]
-    start_sat = threading.Barrier(ns + 1)
-    errors = []
+    kpos = [0] * ns               # next slice of each stream
+    lat_poisson, lat_sat = [], []
+    batch_sizes = []
 
-    def worker(i):
-        try:
-            torch.cuda.set_device(local)
-            st = streams[i]
-            k = 0
-            while True:
-                item = qs[i].get()
-                if item is None:
-                    break
-                st.push(views[i][k])
-                lat_poisson[i].append(time.perf_counter() - item)
-                k += 1
-            start_sat.wait()
-            for j in range(n_sat):
-                t0 = time.perf_counter()
-                st.push(views[i][k])
-                lat_sat[i].append(time.perf_counter() - t0)
-                k += 1
-            done_sat[i] = time.perf_counter()
-        except Exception as e:      # reported after the join
-            errors.append(repr(e))
-            try:
-                start_sat.abort()
-            except Exception:
-                pass
-
-    threads = [threading.Thread(target=worker, args=(i,), daemon=True) for i in range(ns)]
-    for t in threads:
-        t.start()
+    # continuous batching from one host thread: every call pushes the slices
+    # that have arrived (at most one per stream, in arrival order); slices
+    # arriving while a call is on the GPU join the next call
+    from collections import deque
+    pending = [deque() for _ in range(ns)]
     if dist is not None:
         dist.barrier()
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
-        for (ta, s_) in events:
-            target = t0 + ta
-            now = time.perf_counter()
-            if target > now:
-                time.sleep(target - now)
-            qs[s_].put(target)
-        for q in qs:
-            q.put(None)
+        ei, done_n = 0, 0
+        while done_n < len(events):
+            now = time.perf_counter() - t0
+            while ei < len(events) and events[ei][0] <= now:
+                pending[events[ei][1]].append(events[ei][0])
+                ei += 1
+            batch = [i for i in range(ns) if pending[i]]
+            if not batch:
+                time.sleep(max(0.0, min(1e-3, events[ei][0] - now)))
+                continue
+            ftk.ftk_streams_push([streams[i] for i in batch], [views[i][kpos[i]] for i in batch])
+            t_done = time.perf_counter() - t0
+            batch_sizes.append(len(batch))
+            for i in batch:
+                lat_poisson.append(t_done - pending[i].popleft())
+                kpos[i] += 1
+                done_n += 1
         poisson_wall = time.perf_counter() - t0
-        try:
-            start_sat.wait()
-        except threading.BrokenBarrierError:
-            pass
+        # saturated: every stream always has a slice waiting
+        torch.cuda.synchronize()
         t_sat = time.perf_counter()
-        for t in threads:
-            t.join()
-        sat_wall = max(done_sat) - t_sat if not errors else float("nan")
-    if errors:
-        raise RuntimeError("stream worker failed: " + errors[0])
+        for j in range(n_sat):
+            ta = time.perf_counter()
+            ftk.ftk_streams_push(streams, [views[i][kpos[i]] for i in range(ns)])
+            lat_sat.append(time.perf_counter() - ta)
+            for i in range(ns):
+                kpos[i] += 1
+        sat_wall = time.perf_counter() - t_sat
     total_arrivals = len(events)
-    lp = [x * 1e3 for L in lat_poisson for x in L]
-    ls = [x * 1e3 for L in lat_sat for x in L]
+    lp = [x * 1e3 for x in lat_poisson]
+    ls = [x * 1e3 for x in lat_sat]
     sat_faces = sum(new_faces[i] * n_sat for i in range(ns))
     sat_wall = _max_over_ranks(dist, sat_wall)
     served_steps_s = ns * n_sat * world / sat_wall
@@ -587,31 +566,17 @@ def serve_arm(args):
         plain_wall = _max_over_ranks(dist, time.perf_counter() - t0)
     plain_steps_s = ns * n_sat * world / plain_wall
 
-    # e2e: new streams fed from pinned host slices (the copy is inside push);
-    # two untimed pushes open each stream, then n_e2e timed pushes
+    # e2e: new streams fed from pinned host slices (the copy is inside push),
+    # one batched call per round; two untimed rounds open each stream
     n_e2e = min(8, n_sat)
     hosts = [slices[i][arrivals[i]:arrivals[i] + n_e2e + 2].cpu().pin_memory() for i in range(ns)]
     e2e_streams = [ftk.Stream((n, n)) for n, _ in specs]
-    e2e_bar = threading.Barrier(ns + 1)
-    e2e_done = [0.0] * ns
-
-    def e2e_worker(i):
-        torch.cuda.set_device(local)
-        for j in range(2):
-            e2e_streams[i].push(hosts[i][j])
-        e2e_bar.wait()
-        for j in range(2, n_e2e + 2):
-            e2e_streams[i].push(hosts[i][j])
-        e2e_done[i] = time.perf_counter()
-
-    th = [threading.Thread(target=e2e_worker, args=(i,), daemon=True) for i in range(ns)]
-    for t in th:
-        t.start()
-    e2e_bar.wait()
+    for j in range(2):
+        ftk.ftk_streams_push(e2e_streams, [hosts[i][j] for i in range(ns)])
     t0 = time.perf_counter()
-    for t in th:
-        t.join()
-    e2e_wall = _max_over_ranks(dist, max(e2e_done) - t0)
+    for j in range(2, n_e2e + 2):
+        ftk.ftk_streams_push(e2e_streams, [hosts[i][j] for i in range(ns)])
+    e2e_wall = _max_over_ranks(dist, time.perf_counter() - t0)
     for s_ in e2e_streams:
         s_.close(False)
 
@@ -645,10 +610,13 @@ def serve_arm(args):
             "config": {"workload": W["name"], "streams": ns, "grid_N": [n for n, _ in specs],
                        "poisson_rate_steps_s": W["rate"], "poisson_duration_s": args.duration,
                        "saturated_pushes_per_stream": n_sat,
-                       "timing": "host wall clock per push (arrival to delta on the host)",
+                       "timing": "host wall clock per slice (arrival to delta on the host)",
+                       "serving": "continuous batching from one host thread: each ftk_streams_push call "
+                                  "takes every slice that has arrived (one per stream)",
                        "l2": "slices of 32 streams (~130 MB per round) rotate through L2; no flush",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "poisson": {"arrivals": total_arrivals, "wall_s": poisson_wall,
+                        "mean_batch": statistics.mean(batch_sizes) if batch_sizes else None,
                         "throughput_steps_s": total_arrivals / poisson_wall,
                         "p50_step_ms": _pct(lp, 0.5), "p99_step_ms": _pct(lp, 0.99),
                         "max_step_ms": max(lp) if lp else None},

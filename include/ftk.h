@@ -96,7 +96,16 @@ typedef struct {
     const int8_t  *morse;     /* [count] */
 } ftk_device_view;
 
+/* A point where a trajectory crosses the time slice t = t0 (grid units). */
+typedef struct {
+    int64_t label;           /* the trajectory's label */
+    int64_t face_a, face_b;  /* punctured faces at the ends of the crossing segment, face_a < face_b */
+    double  pos[3];          /* grid coordinates x, y, z of the crossing (z = 0 in 2D) */
+} ftk_slice_point;           /* 48 bytes */
+
 typedef struct ftk_result ftk_result;
+typedef struct ftk_traj ftk_traj;
+typedef struct ftk_slice ftk_slice;
 typedef struct ftk_plan ftk_plan;
 typedef struct ftk_stream ftk_stream;
 typedef struct ftk_batch ftk_batch;
@@ -147,6 +156,35 @@ ftk_status ftk_plan_download(ftk_plan *plan, ftk_result **out);
  * FTK_ERR_NOMEM with *count set and nothing copied.  Synchronises. */
 ftk_status ftk_plan_download_into(ftk_plan *plan, ftk_cp *dst, int64_t cap, int64_t *count);
 ftk_status ftk_plan_device_view(ftk_plan *plan, ftk_device_view *view);
+/* Trajectories of the last execute as ordered polylines (paper Sec. 4.1: a
+ * trajectory is a PL curve through spacetime).  Two punctured sides of one
+ * spacetime cell are consecutive points (the interpolated field is linear
+ * in the cell, so its zero set there is the segment between them); every
+ * face lies in at most two cells, so a trajectory is a path or a loop.
+ * Trajectories come in increasing label order; trajectory i holds the
+ * records points[offsets[i] .. offsets[i+1]) in path order, starting at
+ * the end with the smaller record index (= smaller face id) -- a loop
+ * starts at its smallest face id and continues to its smaller neighbour,
+ * and closed[i] = 1.  Synchronises; results are library-owned host arrays
+ * released with ftk_traj_free. */
+ftk_status     ftk_plan_trajectories(ftk_plan *plan, ftk_traj **out);
+int64_t        ftk_traj_count(const ftk_traj *tr);
+const int64_t *ftk_traj_offsets(const ftk_traj *tr);    /* [count + 1] */
+const ftk_cp  *ftk_traj_points(const ftk_traj *tr);     /* [offsets[count]] */
+const uint8_t *ftk_traj_closed(const ftk_traj *tr);     /* [count] */
+void           ftk_traj_free(ftk_traj *tr);
+/* The crossings of every trajectory of the last execute with the time
+ * slice t (grid units: slice k is at t = k; paper Sec. 4.1, slicing the PL
+ * curve at t = t0): one point per segment (consecutive points a, b of a
+ * trajectory, and the closing segment of a loop) with t_a <= t < t_b or
+ * t_b <= t < t_a, where t of a point is base[3] + off[3], interpolated
+ * linearly in time along the segment (in double precision).  At an integer
+ * t = k every crossing is an ordinal puncture of slice k.  Points come
+ * grouped by trajectory (label order), in path order.  Synchronises. */
+ftk_status             ftk_plan_slice(ftk_plan *plan, double t, ftk_slice **out);
+int64_t                ftk_slice_count(const ftk_slice *s);
+const ftk_slice_point *ftk_slice_data(const ftk_slice *s);
+void                   ftk_slice_free(ftk_slice *s);
 /* Per-stage device times (ms) of the last synchronised execute (plan created
  * with FTK_FLAG_STAGE_TIMES), five entries: dense detect; survivor
  * evaluation and the scans (tiled variant: the segment scan); placement,
@@ -209,14 +247,35 @@ ftk_status ftk_stream_open(int ndim, int64_t nx, int64_t ny, int64_t nz, const f
 ftk_status ftk_stream_push(ftk_stream *s, const float *slice, ftk_result **delta);
 ftk_status ftk_stream_close(ftk_stream *s, ftk_result **final);
 
+/* Pushes one slice into each of n distinct streams in one call (continuous
+ * batching: a serving loop passes every slice that has arrived since its
+ * last call).  All n pushes are queued before any is waited for, so their
+ * device work overlaps; deltas[i] receives stream i's delta as from
+ * ftk_stream_push.  On an error the first failing status is returned, the
+ * failing streams' deltas are NULL (and those streams accept no more
+ * pushes) and the other streams' deltas are valid and must be freed. */
+ftk_status ftk_streams_push(int n, ftk_stream *const *streams, const float *const *slices, ftk_result **deltas);
+
 /* Serving: streams opened in a server are admitted only while the sum of
- * their device-memory footprints stays within budget_bytes; otherwise
- * ftk_stream_open_in returns FTK_ERR_BUSY (retry after a stream closes). */
+ * their device-memory footprints stays within budget_bytes.  The footprint
+ * (ftk_stream_footprint: the stream's plans, two-slice window and the
+ * union-find and delta arrays of its first pushes) is known from the shape
+ * and checked before anything is allocated.  ftk_stream_open_in refuses
+ * with FTK_ERR_BUSY when it does not fit now (or earlier opens are
+ * waiting); ftk_stream_open_wait queues first-come first-served and admits
+ * the stream as soon as closing streams have freed enough of the budget,
+ * or refuses with FTK_ERR_BUSY after timeout_ms.  A stream whose state
+ * later grows charges the growth to the budget before allocating it; growth
+ * past the budget fails that push with FTK_ERR_BUSY. */
 ftk_status ftk_server_create(uint64_t budget_bytes, ftk_server **server);
 ftk_status ftk_server_used(ftk_server *server, uint64_t *used_bytes);
 ftk_status ftk_server_destroy(ftk_server *server);   /* FTK_ERR_STATE while streams are open */
 ftk_status ftk_stream_open_in(ftk_server *server, int ndim, int64_t nx, int64_t ny, int64_t nz,
                               const ftk_params *p, ftk_stream **s);
+ftk_status ftk_stream_open_wait(ftk_server *server, int ndim, int64_t nx, int64_t ny, int64_t nz,
+                                const ftk_params *p, int64_t timeout_ms, ftk_stream **s);
+ftk_status ftk_stream_footprint(int ndim, int64_t nx, int64_t ny, int64_t nz, const ftk_params *p,
+                                uint64_t *bytes);
 
 /* ---------------------------------------------------------------------
  * Tracking without device allocation.  The paper has no counterpart: this

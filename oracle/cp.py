@@ -660,6 +660,77 @@ def track_many(fields, shift: int = 20, workers: int | None = None):
     return out
 
 
+# ----------------------------------------------------------------------------
+# Trajectories as ordered polylines and their slices at a time t (Sec. 4.1:
+# a trajectory is a PL curve in spacetime that can be sliced at t = t0)
+# ----------------------------------------------------------------------------
+def trajectories(grid: Grid, ids, labels):
+    """Each trajectory as its punctured faces in path order.
+
+    Two punctured sides of one cell are consecutive points (the PL field is
+    linear in the cell, so its zero set there is the segment between them).
+    Returns a list, in increasing label order, of (face ids in path order,
+    closed): a path starts at its end with the smaller face id; a loop (no
+    ends) starts at its smallest face id and continues to its smaller
+    neighbour."""
+    ids = [int(x) for x in ids]
+    nbr = {f: [] for f in ids}
+    for a, b in cell_pairs(grid, ids):
+        nbr[a].append(b)
+        nbr[b].append(a)
+    groups = {}
+    for f, lab in zip(ids, [int(x) for x in labels]):
+        groups.setdefault(lab, []).append(f)
+    out = []
+    for lab in sorted(groups):
+        members = groups[lab]
+        ends = [f for f in members if len(nbr[f]) < 2]
+        closed = not ends
+        start = min(ends) if ends else min(members)
+        order = [start]
+        prev, cur = None, start
+        while True:
+            nxt = [g for g in sorted(nbr[cur]) if g != prev]
+            if not nxt or nxt[0] == start:
+                break
+            prev, cur = cur, nxt[0]
+            order.append(cur)
+        out.append((order, closed))
+    return out
+
+
+def slice_trajectories(trajs, pos, t0):
+    """Crossings of the polylines with the time slice t = t0: one point per
+    segment (consecutive points a, b, and the closing segment of a loop)
+    with t_a <= t0 < t_b or t_b <= t0 < t_a, interpolated linearly in time.
+    ``pos[f]`` = (x, y, z, t) of face f.  Returns a list of
+    (label, face_a, face_b, (x, y, z)) with face_a < face_b, grouped by
+    trajectory in path order."""
+    out = []
+    for order, closed in trajs:
+        lab = min(order)
+        n = len(order)
+        segs = [(order[j], order[j + 1]) for j in range(n - 1)]
+        if closed and n > 1:
+            segs.append((order[-1], order[0]))
+        for a, b in segs:
+            pa, pb = pos[a], pos[b]
+            ta, tb = pa[3], pb[3]
+            if not ((ta <= t0 < tb) or (tb <= t0 < ta)):
+                continue
+            s = (t0 - ta) / (tb - ta)
+            xyz = tuple(pa[k] + s * (pb[k] - pa[k]) for k in range(3))
+            out.append((lab, min(a, b), max(a, b), xyz))
+    return out
+
+
+def positions(result):
+    """{face id: (x, y, z, t)} = base + in-cell offset of each puncture."""
+    b = result["base"].astype(np.float64)
+    o = result["off"]
+    return {int(f): tuple(b[i, k] + o[i, k] for k in range(4)) for i, f in enumerate(result["face_id"])}
+
+
 def stream_push_index(grid: Grid, fid: int) -> int:
     """Push (time slice) after which a face becomes known in a stream:
     ordinal faces at slice t with slice t, interval faces of slab [t, t+1]

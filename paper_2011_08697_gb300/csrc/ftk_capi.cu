@@ -175,8 +175,8 @@ ftk_status choose_blocking(int ndim, const Field &F, Blocking &B, int &variant) 
     }
     if (ndim == 3 && F.pitch % 4 == 0 && F.pitch <= STREAM3_MAX_NX) {
         variant = VAR_STREAM3;
-        // plane chunks of (ry + 3) rows of about 10 KB or less; 8 cube planes
-        B.ry = std::max(1, std::min(15, std::min(F.ny, 10240 / (F.pitch * 4) - 3)));
+        // the kernel's consumer warps fix the rows per unit; 8 cube planes
+        B.ry = stream3_ry(F.pitch);
         B.rz = std::min(8, F.nz);
         B.nyb = (F.ny + B.ry - 1) / B.ry;
         B.nzb = (F.nz + B.rz - 1) / B.rz;
@@ -233,6 +233,7 @@ ftk_status status_of(unsigned st) {
 
 ftk_status launch(ftk_plan *pl, const float *dev_f, cudaStream_t s, int variant) {
     pl->F.f = dev_f;
+    pl->traj_valid = false;
     cudaError_t e = launch_pipeline(pl->ndim, variant, pl->F, pl->B, pl->W, s, pl->timing ? pl->ev : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, (std::string("pipeline launch (") + last_launch_stage() + ")").c_str());
     pl->stream = s;
@@ -452,6 +453,40 @@ const char *ftk_version(void) { return "ftk-gb300 0.1 sm_103a"; }
 
 }  // extern "C"
 
+// initial puncture and survivor capacities of a plan (grow on demand)
+static long long initial_cap(const ftk_params &p, long long nverts) {
+    return p.max_punctures > 0 ? p.max_punctures
+                               : std::max<long long>(1 << 16, std::min<long long>(nverts / 32, 1LL << 26));
+}
+static long long initial_scap(long long nverts) {
+    return std::max<long long>(1 << 16, std::min<long long>(nverts / 32, 1LL << 26));
+}
+
+ftk_status ftk::plan_sizes(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, const ftk_params *p,
+                           PlanSizes *out) {
+    if (ndim != 2 && ndim != 3) return fail(FTK_ERR_ARG, "ndim must be 2 or 3");
+    if (ndim == 2) nz = 1;
+    if (nx < 2 || ny < 2 || (ndim == 3 && nz < 2) || nt < 1)
+        return fail(FTK_ERR_ARG, "every spatial extent must be >= 2 and nt >= 1");
+    if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30) || nt > (1 << 30))
+        return fail(FTK_ERR_ARG, "extent too large");
+    ftk_status s = check_params(p);
+    if (s != FTK_OK) return s;
+    ftk_params prm;
+    if (p) prm = *p;
+    else ftk_params_default(&prm);
+    std::memset(out, 0, sizeof(*out));
+    out->F.nx = (int)nx; out->F.ny = (int)ny; out->F.nz = (int)nz; out->F.nt = (int)nt;
+    out->F.pitch = stream_pitch(ndim, (int)nx);
+    s = choose_blocking(ndim, out->F, out->B, out->variant);
+    if (s != FTK_OK) return s;
+    const long long nverts = (long long)nx * ny * nz * nt;
+    out->nseg = (long long)nt * nz * out->B.nyb;
+    out->cap = initial_cap(prm, nverts);
+    out->scap = out->variant != VAR_TILE ? initial_scap(nverts) : 0;
+    return FTK_OK;
+}
+
 ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, const ftk_params *p,
                             RunCounters *ctr, ftk_plan **plan) {
     if (plan) *plan = nullptr;
@@ -500,10 +535,7 @@ ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_
         delete pl;
         return fail(FTK_ERR_NOMEM, "device allocation failed");
     }
-    long long cap = pl->p.max_punctures > 0
-                        ? pl->p.max_punctures
-                        : std::max<long long>(1 << 16, std::min<long long>(pl->nverts / 32, 1LL << 26));
-    s = alloc_capacity(W, cap);
+    s = alloc_capacity(W, initial_cap(pl->p, pl->nverts));
     if (s == FTK_OK && pl->variant != VAR_TILE) {
         const long long nst = (W.nseg + SEG_TILE - 1) / SEG_TILE;
         if (cudaMalloc(&W.seg_scnt, W.nseg * sizeof(int)) != cudaSuccess ||
@@ -512,7 +544,7 @@ ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_
             cudaGetLastError();
             s = fail(FTK_ERR_NOMEM, "device allocation failed");
         } else {
-            s = alloc_survivors(W, std::max<long long>(1 << 16, std::min<long long>(pl->nverts / 32, 1LL << 26)));
+            s = alloc_survivors(W, initial_scap(pl->nverts));
         }
     }
     if (s != FTK_OK) {
@@ -640,6 +672,7 @@ ftk_status ftk_plan_destroy(ftk_plan *pl) {
     if (pl->timing)
         for (int i = 0; i < 6; ++i) cudaEventDestroy(pl->ev[i]);
     if (pl->copy_ev) cudaEventDestroy(pl->copy_ev);
+    free_traj(pl);
     delete pl;
     return FTK_OK;
 }

@@ -33,12 +33,26 @@ struct ftk_plan {
     bool timing;
     cudaEvent_t ev[6];
     cudaEvent_t copy_ev;       // end of the host-input copy of the last execute
+    ftk::TrajBuffers traj;     // trajectory buffers (allocated on first use)
+    long long traj_cap;        // punctures they hold
+    long long traj_n;          // trajectories of the last execute (valid if traj_valid)
+    bool traj_valid;
     float stage_ms[5];
     int nstage;
 };
 
 
 namespace ftk {
+
+// what a plan of a shape would allocate, computed without allocating
+struct PlanSizes {
+    int variant;
+    Field F;
+    Blocking B;
+    long long nseg, cap, scap;
+};
+ftk_status plan_sizes(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, const ftk_params *p,
+                      PlanSizes *out);
 
 ftk_status fail(ftk_status s, const std::string &msg);
 ftk_status cuda_fail(cudaError_t e, const char *what);
@@ -56,5 +70,7 @@ ftk_status plan_check(ftk_plan *pl);
 ftk_status plan_result(ftk_plan *pl, ftk_result **out);
 // measured choice of the time chunking for the plan's shape (cached per shape)
 ftk_status plan_autotune(ftk_plan *pl, const float *f, cudaStream_t s);
+// releases the plan's trajectory buffers
+void free_traj(ftk_plan *pl);
 
 }  // namespace ftk

@@ -2033,3 +2033,257 @@ cudaError_t launch_pipeline(int ndim, int variant, const Field &F, const Blockin
 }
 
 }  // namespace ftk
+
+// ----------------------------------------------------------------------------
+// Trajectories as ordered polylines, and their slices at a time t (paper
+// Sec. 4.1: a trajectory is a PL curve through spacetime that can be sliced
+// at t = t0; Sec. 3.2).  Two punctured sides of one cell are consecutive
+// points of a trajectory: inside the cell the interpolated field is linear,
+// so its zero set is the segment between them.  Every face lies in at most
+// two cells, so each puncture has at most two neighbours and a trajectory is
+// a path or a closed loop.
+// ----------------------------------------------------------------------------
+namespace ftk {
+
+// start of a trajectory without ends (a loop): the bytes 0x7f of a memset,
+// above every puncture index
+constexpr int TRAJ_NO_END = 0x7f7f7f7f;
+
+// index of face id key in the sorted puncture array, or -1
+__device__ __forceinline__ long long find_face(const long long *face, long long P, long long key) {
+    long long lo = 0, hi = P;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (face[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < P && face[lo] == key) ? lo : -1;
+}
+
+// per puncture i: the punctured partner in each cell containing it (the
+// cell's other punctured side), nbr[2i] <= nbr[2i+1], -1 for none
+template <int N>
+__global__ void __launch_bounds__(NT) k_traj_edges(Field F, Workspace W, int *nbr) {
+    constexpr int D = N + 1;
+    constexpr int FULL = (1 << D) - 1;
+    const long long P = W.ctr->punctures;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        const long long fid = W.face[i];
+        int tt;
+        const Pt base = decode_face<N>(F, fid, tt);
+        int m[N];
+        for (int k = 0; k < N; ++k) m[k] = mesh<N>().face[tt][k];
+        Pt cb[2];
+        int cm[2][D];
+        int ncell = 0;
+        if (m[N - 1] == FULL) {
+            int prev = 0;
+            for (int j = 0; j < N; ++j) {
+                const int step = m[j] ^ prev;
+                if (__popc(step) == 2) {
+                    for (int a = 0; a < D; ++a) {
+                        if (!((step >> a) & 1)) continue;
+                        for (int q = 0; q < j; ++q) cm[ncell][q] = m[q];
+                        cm[ncell][j] = prev | (1 << a);
+                        for (int q = j; q < N; ++q) cm[ncell][q + 1] = m[q];
+                        cb[ncell] = base;
+                        ++ncell;
+                    }
+                    break;
+                }
+                prev = m[j];
+            }
+        } else {
+            const int a = __ffs(FULL ^ m[N - 1]) - 1;
+            const int ca = a == N ? 3 : a;
+            const int ext = a == N ? F.nt : (a == 0 ? F.nx : a == 1 ? F.ny : F.nz);
+            if (base.c[ca] >= 1) {
+                cb[ncell] = base;
+                cb[ncell].c[ca] -= 1;
+                cm[ncell][0] = 1 << a;
+                for (int q = 0; q < N; ++q) cm[ncell][q + 1] = m[q] | (1 << a);
+                ++ncell;
+            }
+            if (base.c[ca] + 1 < ext) {
+                cb[ncell] = base;
+                for (int q = 0; q < N; ++q) cm[ncell][q] = m[q];
+                cm[ncell][N] = FULL;
+                ++ncell;
+            }
+        }
+        int out[2] = {-1, -1};
+        for (int c = 0; c < ncell; ++c) {
+            for (int k = 0; k <= D; ++k) {
+                Pt sb = cb[c];
+                int sm[N];
+                if (k == 0) {
+                    sb = add_mask<N>(cb[c], cm[c][0]);
+                    for (int q = 0; q < N; ++q) sm[q] = cm[c][q + 1] ^ cm[c][0];
+                } else if (k == D) {
+                    for (int q = 0; q < N; ++q) sm[q] = cm[c][q];
+                } else {
+                    int w = 0;
+                    for (int q = 0; q < D; ++q)
+                        if (q != k - 1) sm[w++] = cm[c][q];
+                }
+                const long long sid = face_id_of<N>(F, sb, sm);
+                if (sid == fid) continue;
+                const long long j = find_face(W.face, P, sid);
+                if (j >= 0) out[c] = (int)j;
+            }
+        }
+        if (out[0] > out[1]) { const int t = out[0]; out[0] = out[1]; out[1] = t; }
+        nbr[2 * i] = out[0];
+        nbr[2 * i + 1] = out[1];
+    }
+}
+
+// per puncture: the index of its trajectory's root (the face with the
+// smallest id, its label), the trajectory's size, and its smallest end
+// (a puncture with fewer than two neighbours; TRAJ_NO_END for a loop)
+__global__ void __launch_bounds__(NT) k_traj_roots(Workspace W, const int *nbr, int *root, int *size, int *start) {
+    const long long P = W.ctr->punctures;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        const long long r = find_face(W.face, P, W.label[i]);
+        root[i] = (int)r;
+        if (r < 0) {
+            atomicOr(&W.ctr->status, ST_PAIRING);
+            continue;
+        }
+        atomicAdd(&size[r], 1);
+        if (nbr[2 * i] < 0) atomicMin(&start[r], (int)i);
+    }
+}
+
+// exclusive scan of v[0..n) into out[0..n], out[n] = total, by one block of
+// NT threads: each thread sums a contiguous chunk, the block scans the sums
+__global__ void __launch_bounds__(NT) k_scan_one_block(const int *v, long long n, long long *out) {
+    __shared__ long long red[NT / 32 + 1];
+    const long long per = (n + NT - 1) / NT;
+    const long long a = threadIdx.x * per, b = min(n, a + per);
+    long long loc = 0;
+    for (long long i = a; i < b; ++i) loc += v[i];
+    long long tot;
+    long long ex = block_excl_scan<long long>(loc, red, tot);
+    for (long long i = a; i < b; ++i) {
+        out[i] = ex;
+        ex += v[i];
+    }
+    if (threadIdx.x == 0) out[n] = tot;
+}
+
+// sizes of the trajectories at their roots (0 elsewhere), for the scan of
+// the trajectories' offsets; ones at the roots for their numbering
+__global__ void __launch_bounds__(NT) k_traj_root_sizes(Workspace W, const int *root, const int *size, int *rsize,
+                                                         int *isroot) {
+    const long long P = W.ctr->punctures;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        const bool r = root[i] == (int)i;
+        rsize[i] = r ? size[i] : 0;
+        isroot[i] = r ? 1 : 0;
+    }
+}
+
+// one thread per trajectory (at its root): walk the path from its smallest
+// end (a loop: from the root, towards its smaller neighbour) and write the
+// punctures' records in path order
+__global__ void __launch_bounds__(NT) k_traj_walk(Workspace W, const int *nbr, const int *root, const int *size,
+                                                   const int *start, const long long *off, const long long *tidx,
+                                                   int *order, long long *toff, uint8_t *closed, ftk_cp *rec) {
+    const long long P = W.ctr->punctures;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        if (root[i] != (int)i) continue;
+        const long long t = tidx[i];
+        const long long o = off[i];
+        const int n = size[i];
+        const bool loop = start[i] == TRAJ_NO_END;
+        toff[t] = o;
+        closed[t] = loop ? 1 : 0;
+        int prev = -1, cur = loop ? (int)i : start[i];
+        int j = 0;
+        for (; j < n && cur >= 0; ++j) {
+            order[o + j] = cur;
+            rec[o + j] = W.packed[cur];
+            const int a = nbr[2 * cur], b = nbr[2 * cur + 1];
+            const int next = a >= 0 && a != prev ? a : (b != prev ? b : -1);
+            prev = cur;
+            cur = next;
+            if (loop && cur == (int)i) cur = -1;
+        }
+        if (j != n) atomicOr(&W.ctr->status, ST_PAIRING);   // a path that is not one component
+    }
+}
+
+// time (grid units) of a puncture record
+__device__ __forceinline__ double rec_t(const ftk_cp &r) { return (double)r.base[3] + (double)r.off[3]; }
+__device__ __forceinline__ double rec_c(const ftk_cp &r, int a) { return (double)r.base[a] + (double)r.off[a]; }
+
+// segments of trajectory t (consecutive points in path order, and the
+// closing segment of a loop) that cross time t0: t_a <= t0 < t_b or
+// t_b <= t0 < t_a.  Pass 1 counts per trajectory; pass 2 writes the crossing
+// points, interpolated linearly in time along the segment.
+__global__ void __launch_bounds__(NT) k_traj_slice(const ftk_cp *rec, const long long *toff, const uint8_t *closed,
+                                                    long long ntraj, double t0, int *cnt, const long long *soff,
+                                                    ftk_slice_point *pts) {
+    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < ntraj; t += (long long)gridDim.x * NT) {
+        const long long a0 = toff[t], n = toff[t + 1] - a0;
+        const long long nseg = closed[t] ? n : n - 1;
+        int c = 0;
+        long long w = pts ? soff[t] : 0;
+        for (long long j = 0; j < nseg; ++j) {
+            const ftk_cp &A = rec[a0 + j];
+            const ftk_cp &B = rec[a0 + (j + 1 == n ? 0 : j + 1)];
+            const double ta = rec_t(A), tb = rec_t(B);
+            if (!((ta <= t0 && t0 < tb) || (tb <= t0 && t0 < ta))) continue;
+            ++c;
+            if (!pts) continue;
+            const double s = (t0 - ta) / (tb - ta);
+            ftk_slice_point p;
+            p.label = A.label;
+            p.face_a = A.face_id < B.face_id ? A.face_id : B.face_id;
+            p.face_b = A.face_id < B.face_id ? B.face_id : A.face_id;
+            for (int a = 0; a < 3; ++a) p.pos[a] = rec_c(A, a) + s * (rec_c(B, a) - rec_c(A, a));
+            pts[w++] = p;
+        }
+        if (!pts) cnt[t] = c;
+    }
+}
+
+}  // namespace ftk
+
+namespace ftk {
+
+cudaError_t launch_trajectories(int ndim, const Field &F, const Workspace &W, long long P, const TrajBuffers &T,
+                                cudaStream_t s, long long *ntraj) {
+    const int grid = sparse_grid();
+    cudaError_t e;
+    if (ndim == 2) k_traj_edges<2><<<grid, NT, 0, s>>>(F, W, T.nbr);
+    else k_traj_edges<3><<<grid, NT, 0, s>>>(F, W, T.nbr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(T.size, 0, sizeof(int) * P, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(T.start, 0x7f, sizeof(int) * P, s)) != cudaSuccess) return e;   // TRAJ_NO_END
+    k_traj_roots<<<grid, NT, 0, s>>>(W, T.nbr, T.root, T.size, T.start);
+    k_traj_root_sizes<<<grid, NT, 0, s>>>(W, T.root, T.size, T.rsize, T.isroot);
+    k_scan_one_block<<<1, NT, 0, s>>>(T.rsize, P, T.off);
+    k_scan_one_block<<<1, NT, 0, s>>>(T.isroot, P, T.tidx);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(ntraj, T.tidx + P, sizeof(long long), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t launch_traj_walk(const Workspace &W, long long P, long long ntraj, const TrajBuffers &T, cudaStream_t s) {
+    k_traj_walk<<<sparse_grid(), NT, 0, s>>>(W, T.nbr, T.root, T.size, T.start, T.off, T.tidx, T.order, T.toff,
+                                             T.closed, T.rec);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(T.toff + ntraj, T.off + P, sizeof(long long), cudaMemcpyDeviceToDevice, s);
+}
+
+cudaError_t launch_traj_slice(const TrajBuffers &T, long long ntraj, double t0, int *cnt, long long *soff,
+                              ftk_slice_point *pts, cudaStream_t s) {
+    k_traj_slice<<<sparse_grid(), NT, 0, s>>>(T.rec, T.toff, T.closed, ntraj, t0, cnt, soff, pts);
+    if (!pts) k_scan_one_block<<<1, NT, 0, s>>>(cnt, ntraj, soff);
+    return cudaGetLastError();
+}
+
+}  // namespace ftk

@@ -154,6 +154,8 @@ long long stream2_state_words(const Field &F, const Blocking &B);
 size_t stream3_smem_bytes(int nx, const Blocking &B);
 int stream3_threads();
 int stream3_ctas_per_sm(int nx, const Blocking &B);
+// cube rows per unit of the 3D streaming kernel for a row pitch
+int stream3_ry(int nx);
 cudaError_t launch_detect3(int variant, const Field &F, const Blocking &B, const Workspace &W, cudaStream_t s,
                            bool capturing);
 // Raises a kernel's dynamic shared-memory cap to at least `smem` bytes and
@@ -229,6 +231,27 @@ cudaError_t launch_stream_copy(const StreamSrc *src, float *dst, int nx, int pit
 cudaError_t launch_stream_final(long long n, const int *gshadow, int *gparent, const long long *gmin,
                                 const ftk_cp *grec, ftk_cp *out, long long *count, unsigned *status,
                                 cudaStream_t s);
+
+// Trajectories of a run (ordered polylines) and their slices at a time.
+struct TrajBuffers {
+    int *nbr;            // [2P] punctured partners in the face's cells
+    int *root, *size, *start, *rsize, *isroot;   // [P]
+    long long *off;      // [P + 1] first point of each root's trajectory
+    long long *tidx;     // [P + 1] trajectory number of each root
+    int *order;          // [P] punctures in trajectory, then path order
+    ftk_cp *rec;         // [P] their records
+    long long *toff;     // [ntraj + 1] first point of each trajectory
+    uint8_t *closed;     // [ntraj] 1 for a loop
+};
+// edges, roots, sizes and the scans; *ntraj (host) after a synchronisation
+cudaError_t launch_trajectories(int ndim, const Field &F, const Workspace &W, long long P, const TrajBuffers &T,
+                                cudaStream_t s, long long *ntraj);
+// the walk: order, records, toff, closed
+cudaError_t launch_traj_walk(const Workspace &W, long long P, long long ntraj, const TrajBuffers &T, cudaStream_t s);
+// pts == nullptr: counts per trajectory into cnt and their scan into soff
+// (soff[ntraj] = total); else the crossing points at soff
+cudaError_t launch_traj_slice(const TrajBuffers &T, long long ntraj, double t0, int *cnt, long long *soff,
+                              ftk_slice_point *pts, cudaStream_t s);
 
 // name of the step whose CUDA call failed in the last launch_pipeline
 const char *last_launch_stage();

@@ -21,7 +21,12 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <climits>
+#include <condition_variable>
+#include <deque>
+#include <unordered_set>
+#include <vector>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -38,6 +43,9 @@ struct ftk_server {
     size_t budget = 0;
     size_t used = 0;
     std::mutex mu;
+    std::condition_variable cv;     // signalled whenever memory is returned or the queue moves
+    std::deque<uint64_t> queue;     // tickets of the opens waiting for admission, oldest first
+    uint64_t next_ticket = 0;
 };
 
 struct ftk_stream {
@@ -132,8 +140,11 @@ ftk_status reserve(ftk_stream *st, size_t add) {
 
 void unreserve(ftk_stream *st, size_t sub) {
     if (st->server) {
-        std::lock_guard<std::mutex> lock(st->server->mu);
-        st->server->used -= std::min(st->server->used, sub);
+        {
+            std::lock_guard<std::mutex> lock(st->server->mu);
+            st->server->used -= std::min(st->server->used, sub);
+        }
+        st->server->cv.notify_all();
     }
     st->footprint -= std::min(st->footprint, sub);
 }
@@ -312,27 +323,108 @@ void release(ftk_stream *st) {
     if (st->done) cudaEventDestroy(st->done);
     if (st->cs) cudaStreamDestroy(st->cs);
     if (st->server) {
-        std::lock_guard<std::mutex> lock(st->server->mu);
-        st->server->used -= std::min(st->server->used, st->footprint);
+        {
+            std::lock_guard<std::mutex> lock(st->server->mu);
+            st->server->used -= std::min(st->server->used, st->footprint);
+        }
+        st->server->cv.notify_all();
     }
     delete st;
 }
 
-size_t plan_bytes(const ftk_plan *pl) {
-    const Workspace &W = pl->W;
-    return (size_t)W.cap * (8 + 8 + 4 + 16 + 1 + 8 + sizeof(ftk_cp)) + (size_t)W.scap * (8 + 8 + 4) +
-           (size_t)W.nseg * (4 + 8 + 8 + 4 + 8);
+// device bytes charged for a plan's workspace
+size_t plan_bytes(long long cap, long long scap, long long nseg) {
+    return (size_t)cap * (8 + 8 + 4 + 16 + 1 + 8 + sizeof(ftk_cp)) + (size_t)scap * (8 + 8 + 4) +
+           (size_t)nseg * (4 + 8 + 8 + 4 + 8);
+}
+size_t plan_bytes(const ftk_plan *pl) { return plan_bytes(pl->W.cap, pl->W.scap, pl->W.nseg); }
+
+// bytes ensure_all charges when it first sizes the per-push arrays for cap
+size_t first_push_bytes(long long cap) {
+    return (size_t)grow_cap(cap) * (8 + 4 + 8 + 4 + sizeof(ftk_cp)) + (size_t)grow_cap(cap) * 8 +
+           (size_t)grow_cap(4 * (cap / DELTA_BLOCK + 1)) * 8 + (size_t)grow_cap(cap) * 24;
+}
+
+// the footprint open_stream charges for a stream of this shape, computed
+// without allocating anything (the same sizes its plans and arrays get)
+ftk_status stream_footprint(int ndim, int64_t nx, int64_t ny, int64_t nz, const ftk_params *p, size_t *fp) {
+    ftk_params prm;
+    if (p) prm = *p;
+    else ftk_params_default(&prm);
+    prm.flags &= ~FTK_FLAG_STAGE_TIMES;
+    if (ndim == 2) nz = 1;
+    PlanSizes a, b;
+    ftk_status s;
+    if ((s = plan_sizes(ndim, nx, ny, nz, 1, &prm, &a)) != FTK_OK || (s = plan_sizes(ndim, nx, ny, nz, 2, &prm, &b)) != FTK_OK)
+        return s;
+    long long st_words = 0;
+    if (ndim == 2 && a.variant != VAR_TILE && b.variant != VAR_TILE && a.B.nyb == b.B.nyb)
+        st_words = stream2_state_words(b.F, b.B);
+    const long long slice_elems = (long long)ny * nz * b.F.pitch;
+    *fp = sizeof(float) * 2 * (size_t)slice_elems + plan_bytes(a.cap, a.scap, a.nseg) +
+          plan_bytes(b.cap, b.scap, b.nseg) + sizeof(uint32_t) * 2 * (size_t)st_words +
+          first_push_bytes(std::max(a.cap, b.cap));
+    return FTK_OK;
+}
+
+// admission of a footprint by a server: immediately (timeout_ms = 0: only if
+// no earlier open is waiting and it fits now) or after waiting in FIFO order
+// for streams to close, for at most timeout_ms
+ftk_status admit(ftk_server *srv, size_t fp, long long timeout_ms) {
+    std::unique_lock<std::mutex> lock(srv->mu);
+    if (fp > srv->budget)
+        return fail(FTK_ERR_BUSY, "admission refused: the stream needs " + std::to_string(fp) +
+                                      " bytes of device memory, more than the whole budget");
+    if (srv->queue.empty() && srv->used + fp <= srv->budget) {
+        srv->used += fp;
+        return FTK_OK;
+    }
+    if (timeout_ms <= 0)
+        return fail(FTK_ERR_BUSY, "admission refused: the stream needs " + std::to_string(fp) +
+                                      " bytes of device memory beyond the budget");
+    const uint64_t ticket = srv->next_ticket++;
+    srv->queue.push_back(ticket);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    const bool ok = srv->cv.wait_until(lock, deadline, [&] {
+        return srv->queue.front() == ticket && srv->used + fp <= srv->budget;
+    });
+    srv->queue.erase(std::find(srv->queue.begin(), srv->queue.end(), ticket));
+    if (ok) srv->used += fp;
+    lock.unlock();
+    srv->cv.notify_all();   // the next waiter may be at the head now
+    if (!ok)
+        return fail(FTK_ERR_BUSY, "admission refused: no room within " + std::to_string(timeout_ms) + " ms");
+    return FTK_OK;
 }
 
 ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_t nz, const ftk_params *p,
-                       ftk_stream **out) {
+                       long long timeout_ms, ftk_stream **out) {
     if (out) *out = nullptr;
     if (!out) return fail(FTK_ERR_ARG, "out is NULL");
     if (ndim != 2 && ndim != 3) return fail(FTK_ERR_ARG, "ndim must be 2 or 3");
     if (ndim == 2) nz = 1;
     if (nx < 2 || ny < 2 || (ndim == 3 && nz < 2)) return fail(FTK_ERR_ARG, "every spatial extent must be >= 2");
+    // admission before any allocation: the footprint is known from the shape
+    size_t fp = 0;
+    ftk_status s = FTK_OK;
+    if (srv) {
+        if ((s = stream_footprint(ndim, nx, ny, nz, p, &fp)) != FTK_OK) return s;
+        if ((s = admit(srv, fp, timeout_ms)) != FTK_OK) return s;
+    }
+    // returns the admitted bytes when the open fails below
+    auto give_back = [&]() {
+        if (!srv) return;
+        {
+            std::lock_guard<std::mutex> lock(srv->mu);
+            srv->used -= std::min(srv->used, fp);
+        }
+        srv->cv.notify_all();
+    };
     ftk_stream *st = new (std::nothrow) ftk_stream;
-    if (!st) return fail(FTK_ERR_NOMEM, "host allocation failed");
+    if (!st) {
+        give_back();
+        return fail(FTK_ERR_NOMEM, "host allocation failed");
+    }
     st->ndim = ndim;
     st->nx = (int)nx; st->ny = (int)ny; st->nz = (int)nz;
     if (p) st->p = *p;
@@ -341,10 +433,10 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
     st->slice_verts = (long long)nx * ny * nz;
     st->T = ndim == 2 ? 12 : 60;
     st->tbit = ndim == 2 ? 4 : 8;
-    ftk_status s = FTK_OK;
     if ((s = plan_create(ndim, nx, ny, nz, 1, &st->p, nullptr, &st->plan1)) != FTK_OK ||
         (s = plan_create(ndim, nx, ny, nz, 2, &st->p, nullptr, &st->plan2)) != FTK_OK) {
         release(st);
+        give_back();
         return s;
     }
     // incremental detect (2D streaming plans): push 0 stores slice 0's
@@ -356,6 +448,7 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
             cudaMalloc(&st->st_out, sizeof(uint32_t) * st->st_words) != cudaSuccess) {
             cudaGetLastError();
             release(st);
+            give_back();
             return fail(FTK_ERR_NOMEM, "stream allocation failed");
         }
         st->plan1->B.st_mode = 1;
@@ -380,6 +473,7 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
         cudaHostGetDevicePointer((void **)&st->dSrc, st->hSrc, 0) != cudaSuccess) {
         cudaGetLastError();
         release(st);
+        give_back();
         return fail(FTK_ERR_NOMEM, "stream allocation failed");
     }
     st->footprint = sizeof(float) * 2 * st->slice_elems + plan_bytes(st->plan1) + plan_bytes(st->plan2) +
@@ -388,19 +482,13 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
     // footprint admission checks (later growth is charged push by push)
     if ((s = ensure_all(st, std::max(st->plan1->W.cap, st->plan2->W.cap))) != FTK_OK) {
         release(st);
+        give_back();
         return s;
     }
     if (srv) {
+        // the admitted bytes become the stream's; they equal what it holds
         std::lock_guard<std::mutex> lock(srv->mu);
-        if (srv->used + st->footprint > srv->budget) {
-            const std::string msg = "admission refused: the stream needs " + std::to_string(st->footprint) +
-                                    " bytes of device memory beyond the budget";
-            st->footprint = 0;
-            st->server = nullptr;
-            release(st);
-            return fail(FTK_ERR_BUSY, msg);
-        }
-        srv->used += st->footprint;
+        srv->used = srv->used - std::min(srv->used, fp) + st->footprint;
         st->server = srv;
     }
     *out = st;
@@ -457,18 +545,40 @@ ftk_status ftk_server_destroy(ftk_server *s) {
 }
 
 ftk_status ftk_stream_open(int ndim, int64_t nx, int64_t ny, int64_t nz, const ftk_params *p, ftk_stream **s) {
-    return open_stream(nullptr, ndim, nx, ny, nz, p, s);
+    return open_stream(nullptr, ndim, nx, ny, nz, p, 0, s);
 }
 
 ftk_status ftk_stream_open_in(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_t nz, const ftk_params *p,
                               ftk_stream **s) {
+    if (s) *s = nullptr;
     if (!srv) return fail(FTK_ERR_ARG, "server is NULL");
-    return open_stream(srv, ndim, nx, ny, nz, p, s);
+    return open_stream(srv, ndim, nx, ny, nz, p, 0, s);
 }
 
-ftk_status ftk_stream_push(ftk_stream *st, const float *slice, ftk_result **delta) {
-    if (delta) *delta = nullptr;
-    if (!st || !slice || !delta) return fail(FTK_ERR_ARG, "stream, slice and delta must be non-NULL");
+ftk_status ftk_stream_open_wait(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_t nz, const ftk_params *p,
+                                int64_t timeout_ms, ftk_stream **s) {
+    if (s) *s = nullptr;
+    if (!srv) return fail(FTK_ERR_ARG, "server is NULL");
+    if (timeout_ms < 0) return fail(FTK_ERR_ARG, "timeout_ms must be >= 0");
+    return open_stream(srv, ndim, nx, ny, nz, p, (long long)timeout_ms, s);
+}
+
+ftk_status ftk_stream_footprint(int ndim, int64_t nx, int64_t ny, int64_t nz, const ftk_params *p, uint64_t *bytes) {
+    if (!bytes) return fail(FTK_ERR_ARG, "bytes is NULL");
+    if (ndim != 2 && ndim != 3) return fail(FTK_ERR_ARG, "ndim must be 2 or 3");
+    size_t fp = 0;
+    ftk_status st = stream_footprint(ndim, nx, ny, nz, p, &fp);
+    if (st == FTK_OK) *bytes = fp;
+    return st;
+}
+
+}  // extern "C"
+
+namespace {
+
+// first half of a push: queue the device work on the stream's CUDA stream
+// (one graph replay for a steady-state device slice) without waiting
+ftk_status push_begin(ftk_stream *st, const float *slice) {
     if (st->failed) return fail(FTK_ERR_STATE, "an earlier push of this stream failed");
     const long long k = st->k;
     ftk_plan *pl = k == 0 ? st->plan1 : st->plan2;
@@ -488,9 +598,17 @@ ftk_status ftk_stream_push(ftk_stream *st, const float *slice, ftk_result **delt
     } else if ((s = enqueue_push(st, pl, k, on_dev ? nullptr : slice)) != FTK_OK) {
         return stream_error(st, s, nullptr);
     }
+    if ((e = cudaEventRecord(st->done, st->cs)) != cudaSuccess) return stream_error(st, FTK_ERR_CUDA, cudaGetErrorString(e));
+    return FTK_OK;
+}
+
+// second half: wait for the push, repair an overflowed run, hand out the delta
+ftk_status push_end(ftk_stream *st, ftk_result **delta) {
+    ftk_plan *pl = st->k == 0 ? st->plan1 : st->plan2;
+    ftk_status s;
+    cudaError_t e;
     // a blocking-sync event: the waiting thread sleeps instead of spinning
-    if ((e = cudaEventRecord(st->done, st->cs)) != cudaSuccess || (e = cudaEventSynchronize(st->done)) != cudaSuccess)
-        return stream_error(st, FTK_ERR_CUDA, cudaGetErrorString(e));
+    if ((e = cudaEventSynchronize(st->done)) != cudaSuccess) return stream_error(st, FTK_ERR_CUDA, cudaGetErrorString(e));
     StreamView v = read_view(st);
     if (v.run_status & (ST_OVERFLOW | ST_SOVERFLOW | ST_WIDE)) {
         // not merged: repair the run (larger capacity or exact rounding),
@@ -521,6 +639,47 @@ ftk_status ftk_stream_push(ftk_stream *st, const float *slice, ftk_result **delt
     st->n += v.punctures;
     st->k += 1;
     *delta = r;
+    return FTK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ftk_status ftk_stream_push(ftk_stream *st, const float *slice, ftk_result **delta) {
+    if (delta) *delta = nullptr;
+    if (!st || !slice || !delta) return fail(FTK_ERR_ARG, "stream, slice and delta must be non-NULL");
+    ftk_status s = push_begin(st, slice);
+    if (s != FTK_OK) return s;
+    return push_end(st, delta);
+}
+
+ftk_status ftk_streams_push(int n, ftk_stream *const *streams, const float *const *slices, ftk_result **deltas) {
+    if (n < 0 || (n > 0 && (!streams || !slices || !deltas))) return fail(FTK_ERR_ARG, "invalid argument");
+    for (int i = 0; i < n; ++i) deltas[i] = nullptr;
+    {
+        std::unordered_set<const ftk_stream *> seen;
+        for (int i = 0; i < n; ++i) {
+            if (!streams[i] || !slices[i]) return fail(FTK_ERR_ARG, "NULL stream or slice");
+            if (!seen.insert(streams[i]).second) return fail(FTK_ERR_ARG, "a stream appears twice in one call");
+        }
+    }
+    // queue every push first (their device work overlaps on the streams' own
+    // CUDA streams), then collect them in order
+    ftk_status first = FTK_OK;
+    std::string first_msg;
+    std::vector<char> begun((size_t)n, 0);
+    for (int i = 0; i < n; ++i) {
+        const ftk_status s = push_begin(streams[i], slices[i]);
+        if (s == FTK_OK) begun[(size_t)i] = 1;
+        else if (first == FTK_OK) { first = s; first_msg = ftk_last_error(); }
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!begun[(size_t)i]) continue;
+        const ftk_status s = push_end(streams[i], &deltas[i]);
+        if (s != FTK_OK && first == FTK_OK) { first = s; first_msg = ftk_last_error(); }
+    }
+    if (first != FTK_OK) return fail(first, first_msg);
     return FTK_OK;
 }
 

@@ -67,7 +67,13 @@ EXPORTS = [
     "ftk_batch_destroy", "ftk_track_cp2d_batch", "ftk_plan_describe", "ftk_batch_kernels",
     "ftk_stream_open", "ftk_stream_push", "ftk_stream_close", "ftk_server_create",
     "ftk_server_used", "ftk_server_destroy", "ftk_stream_open_in",
+    "ftk_streams_push", "ftk_stream_open_wait", "ftk_stream_footprint",
+    "ftk_plan_trajectories", "ftk_traj_count", "ftk_traj_offsets", "ftk_traj_points", "ftk_traj_closed",
+    "ftk_traj_free", "ftk_plan_slice", "ftk_slice_count", "ftk_slice_data", "ftk_slice_free",
 ]
+
+SLICE_DTYPE = np.dtype([("label", "<i8"), ("face_a", "<i8"), ("face_b", "<i8"), ("pos", "<f8", (3,))])
+assert SLICE_DTYPE.itemsize == 48
 
 
 def lib():
@@ -116,6 +122,20 @@ def lib():
         "ftk_server_used": (i32, [vp, ctypes.POINTER(ctypes.c_uint64)]),
         "ftk_server_destroy": (i32, [vp]),
         "ftk_stream_open_in": (i32, [vp, i32, i64, i64, i64, ctypes.POINTER(ftk_params), pp]),
+        "ftk_streams_push": (i32, [i32, vp, vp, vp]),
+        "ftk_stream_open_wait": (i32, [vp, i32, i64, i64, i64, ctypes.POINTER(ftk_params), i64, pp]),
+        "ftk_stream_footprint": (i32, [i32, i64, i64, i64, ctypes.POINTER(ftk_params),
+                                       ctypes.POINTER(ctypes.c_uint64)]),
+        "ftk_plan_trajectories": (i32, [vp, pp]),
+        "ftk_traj_count": (i64, [vp]),
+        "ftk_traj_offsets": (vp, [vp]),
+        "ftk_traj_points": (vp, [vp]),
+        "ftk_traj_closed": (vp, [vp]),
+        "ftk_traj_free": (None, [vp]),
+        "ftk_plan_slice": (i32, [vp, ctypes.c_double, pp]),
+        "ftk_slice_count": (i64, [vp]),
+        "ftk_slice_data": (vp, [vp]),
+        "ftk_slice_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -261,6 +281,42 @@ class Plan:
         c = ctypes.c_int64()
         _check(lib().ftk_plan_download_into(self._h, ctypes.c_void_p(buf.ctypes.data), len(buf), ctypes.byref(c)))
         return buf[: c.value]
+
+    def trajectories(self):
+        """(offsets [n+1], points [P] CP_DTYPE in trajectory then path order,
+        closed [n] bool) of the last execute."""
+        L = lib()
+        h = ctypes.c_void_p()
+        _check(L.ftk_plan_trajectories(self._h, ctypes.byref(h)))
+        try:
+            n = L.ftk_traj_count(h)
+            off = np.ctypeslib.as_array(ctypes.cast(L.ftk_traj_offsets(h), ctypes.POINTER(ctypes.c_int64)),
+                                        (n + 1,)).copy()
+            P = int(off[-1])
+            pts = np.empty(P, dtype=CP_DTYPE)
+            if P:
+                ctypes.memmove(pts.ctypes.data, L.ftk_traj_points(h), P * CP_DTYPE.itemsize)
+            closed = np.zeros(n, dtype=bool)
+            if n:
+                closed = np.ctypeslib.as_array(ctypes.cast(L.ftk_traj_closed(h), ctypes.POINTER(ctypes.c_uint8)),
+                                               (n,)).astype(bool)
+            return off, pts, closed
+        finally:
+            L.ftk_traj_free(h)
+
+    def slice(self, t: float) -> np.ndarray:
+        """Crossings of the last execute's trajectories with time t (SLICE_DTYPE)."""
+        L = lib()
+        h = ctypes.c_void_p()
+        _check(L.ftk_plan_slice(self._h, float(t), ctypes.byref(h)))
+        try:
+            n = L.ftk_slice_count(h)
+            out = np.empty(n, dtype=SLICE_DTYPE)
+            if n:
+                ctypes.memmove(out.ctypes.data, L.ftk_slice_data(h), n * SLICE_DTYPE.itemsize)
+            return out
+        finally:
+            L.ftk_slice_free(h)
 
     def device_view(self) -> ftk_device_view:
         v = ftk_device_view()
@@ -427,10 +483,53 @@ class Server:
             self._h = None
 
 
-class Stream:
-    """In-situ stream (``ftk_stream_*``): push one slice at a time."""
+def _spatial(shape):
+    shp = tuple(int(v) for v in shape)
+    if len(shp) == 2:
+        return shp, 2, shp[1], shp[0], 1
+    if len(shp) == 3:
+        return shp, 3, shp[2], shp[1], shp[0]
+    raise ValueError("spatial shape must be (ny, nx) or (nz, ny, nx)")
 
-    def __init__(self, spatial_shape, params: ftk_params | None = None, server: Server | None = None):
+
+def ftk_stream_footprint(spatial_shape, params: ftk_params | None = None) -> int:
+    """Device bytes a server charges for a stream of this shape at open."""
+    _, ndim, nx, ny, nz = _spatial(spatial_shape)
+    p = params if params is not None else make_params()
+    b = ctypes.c_uint64()
+    _check(lib().ftk_stream_footprint(ndim, nx, ny, nz, ctypes.byref(p), ctypes.byref(b)))
+    return b.value
+
+
+def ftk_streams_push(streams, slices):
+    """One slice into each of several distinct streams in one call; returns
+    the deltas in order."""
+    n = len(streams)
+    if len(slices) != n:
+        raise ValueError("one slice per stream")
+    hs = (ctypes.c_void_p * n)()
+    ps = (ctypes.c_void_p * n)()
+    keep = []
+    for i, (st, sl) in enumerate(zip(streams, slices)):
+        ptr, k, shape = _field_ptr(sl)
+        if tuple(shape) != st.shape:
+            raise ValueError(f"slice {i}: shape {shape} != {st.shape}")
+        hs[i] = st._h.value
+        ps[i] = ptr.value
+        keep.append(k)
+    outs = (ctypes.c_void_p * n)()
+    status = lib().ftk_streams_push(n, hs, ps, outs)
+    res = [_take_result(ctypes.c_void_p(outs[i])) if outs[i] else None for i in range(n)]
+    _check(status)
+    return res
+
+
+class Stream:
+    """In-situ stream (``ftk_stream_*``): push one slice at a time.  With a
+    server, ``wait_ms`` > 0 waits (first come, first served) for admission."""
+
+    def __init__(self, spatial_shape, params: ftk_params | None = None, server: Server | None = None,
+                 wait_ms: int = 0):
         shp = tuple(int(v) for v in spatial_shape)
         if len(shp) == 2:
             ny, nx = shp
@@ -445,6 +544,9 @@ class Stream:
         h = ctypes.c_void_p()
         if server is None:
             _check(lib().ftk_stream_open(ndim, nx, ny, nz, ctypes.byref(self._p), ctypes.byref(h)))
+        elif wait_ms > 0:
+            _check(lib().ftk_stream_open_wait(server._h, ndim, nx, ny, nz, ctypes.byref(self._p), int(wait_ms),
+                                              ctypes.byref(h)))
         else:
             _check(lib().ftk_stream_open_in(server._h, ndim, nx, ny, nz, ctypes.byref(self._p), ctypes.byref(h)))
         self._h = h

@@ -87,3 +87,76 @@ def test_streams_alone_equal_mixed_and_admission():
     assert e.value.status == 6
     tiny.close()
     srv.close()
+
+
+def test_batched_push_equals_alone():
+    """ftk_streams_push (one slice for each of several streams per call, their
+    device work overlapping) gives every stream the deltas and final result
+    it gets pushed alone, and the oracle's."""
+    from paper_2011_08697_gb300 import build, ftk as F
+    build.build()
+    fields = [synth.gaussian_blobs((48 + 8 * i, 40 + 4 * i), 7, nblobs=10, seed=40 + i, sigma_range=(2.0, 6.0))
+              for i in range(3)]
+    fields.append(synth.random_levels((7, 21, 30), seed=44))
+    alone = [_run_stream(F, f) for f in fields]
+    srv = F.Server(1 << 34)
+    streams = [F.Stream(f.shape[1:], server=srv) for f in fields]
+    deltas = [[] for _ in fields]
+    for k in range(fields[0].shape[0]):
+        xs = [torch.from_numpy(np.ascontiguousarray(f[k])).cuda() for f in fields]
+        for i, d in enumerate(F.ftk_streams_push(streams, xs)):
+            deltas[i].append(d)
+    finals = [s.close() for s in streams]
+    for i, f in enumerate(fields):
+        ref_d, ref_final = alone[i]
+        for a, b in zip(deltas[i], ref_d):
+            assert np.array_equal(a["face_id"], b["face_id"]) and np.array_equal(a["label"], b["label"])
+        compare_full(finals[i], cp.track(f))
+        assert np.array_equal(finals[i]["face_id"], ref_final["face_id"])
+    assert srv.used() == 0
+    srv.close()
+
+
+def test_admission_waits_for_a_closing_stream():
+    """A stream that does not fit the budget waits (first come, first served)
+    and is admitted once a closing stream frees its footprint; its results
+    are the same as alone.  A wait that runs out refuses with FTK_ERR_BUSY."""
+    import time
+    from paper_2011_08697_gb300 import build, ftk as F
+    build.build()
+    fa = synth.gaussian_blobs((48, 40), 6, nblobs=10, seed=50, sigma_range=(2.0, 6.0))
+    fb = synth.gaussian_blobs((48, 40), 6, nblobs=10, seed=51, sigma_range=(2.0, 6.0))
+    fp = F.ftk_stream_footprint((40, 48))
+    srv = F.Server(fp + fp // 2)            # room for one stream, not two
+    a = F.Stream((40, 48), server=srv)
+    assert srv.used() == fp
+    with pytest.raises(F.FtkError) as e:    # no waiting: refused at once
+        F.Stream((40, 48), server=srv)
+    assert e.value.status == 6
+    t0 = time.perf_counter()
+    with pytest.raises(F.FtkError) as e:    # a bounded wait that runs out
+        F.Stream((40, 48), server=srv, wait_ms=200)
+    assert e.value.status == 6 and time.perf_counter() - t0 >= 0.15
+    got = {}
+
+    def opener():
+        s = F.Stream((40, 48), server=srv, wait_ms=60_000)
+        got["admitted_at"] = time.perf_counter()
+        got["res"] = [s.push(torch.from_numpy(np.ascontiguousarray(fb[k])).cuda()) for k in range(fb.shape[0])]
+        got["final"] = s.close()
+
+    th = threading.Thread(target=opener)
+    th.start()
+    for k in range(fa.shape[0]):            # a keeps running while b waits
+        a.push(torch.from_numpy(np.ascontiguousarray(fa[k])).cuda())
+    time.sleep(0.3)
+    assert "admitted_at" not in got
+    t_close = time.perf_counter()
+    fa_final = a.close()
+    th.join(timeout=120)
+    assert not th.is_alive()
+    assert got["admitted_at"] >= t_close
+    compare_full(got["final"], cp.track(fb))
+    compare_full(fa_final, cp.track(fa))
+    assert srv.used() == 0
+    srv.close()
