@@ -116,6 +116,14 @@ const char *ftk_status_string(ftk_status s);
 const char *ftk_last_error(void);
 /* Library version string, e.g. "ftk-gb300 0.1 sm_103a". */
 const char *ftk_version(void);
+/* Test hook (the paper has no counterpart): bounds, on the current device,
+ * of the union-find loops (path steps and retries per operation) and of the
+ * decoupled look-back waits of the scans (clock cycles).  A loop that runs
+ * out gives up, and the run reports FTK_ERR_TIMEOUT; the device stays
+ * usable.  Values <= 0 restore the defaults (2^22 steps, 4e9 cycles).  The
+ * detect kernels' waits on their bulk copies keep their own bound.  Affects
+ * every plan on the device; not for concurrent use with other calls. */
+ftk_status ftk_debug_set_wait_limits(int64_t uf_steps, int64_t lookback_cycles);
 
 /* ---------------------------------------------------------------------
  * One-shot tracking (paper Sec. 8, post hoc analysis of a whole field).
@@ -173,6 +181,24 @@ const int64_t *ftk_traj_offsets(const ftk_traj *tr);    /* [count + 1] */
 const ftk_cp  *ftk_traj_points(const ftk_traj *tr);     /* [offsets[count]] */
 const uint8_t *ftk_traj_closed(const ftk_traj *tr);     /* [count] */
 void           ftk_traj_free(ftk_traj *tr);
+/* Post-processing of the trajectories (paper Sec. 4.2: filtering by
+ * attributes, and smoothing of the critical-point types along a trajectory
+ * with a shifting window).  A trajectory is kept iff its time extent
+ * (largest minus smallest point time base[3] + off[3]) is >= min_duration,
+ * it has >= min_points points, and it is not a loop when drop_loops is set.
+ * With smooth_half_window = h > 0, a point's morse_index becomes the common
+ * index of the h points before and the h points after it along the path
+ * when those 2h points agree and it differs (a loop wraps around; a point
+ * of a path with fewer than h points on a side keeps its index); every
+ * decision reads the unsmoothed indices.  Same layout as
+ * ftk_plan_trajectories. */
+typedef struct {
+    double  min_duration;
+    int64_t min_points;
+    int32_t drop_loops;
+    int32_t smooth_half_window;
+} ftk_traj_filter;
+ftk_status ftk_plan_trajectories_filtered(ftk_plan *plan, const ftk_traj_filter *filter, ftk_traj **out);
 /* The crossings of every trajectory of the last execute with the time
  * slice t (grid units: slice k is at t = k; paper Sec. 4.1, slicing the PL
  * curve at t = t0): one point per segment (consecutive points a, b of a

@@ -724,6 +724,40 @@ def slice_trajectories(trajs, pos, t0):
     return out
 
 
+def filter_trajectories(trajs, pos, morse, min_duration=0.0, min_points=0, drop_loops=False, half_window=0):
+    """Post-processing (Sec. 4.2): keep a trajectory iff its time extent
+    (max - min of its points' t) >= min_duration, it has >= min_points
+    points and (drop_loops) it is not closed; then smooth the types: a
+    point's type becomes the common type of the h points before and the h
+    after it along the path when those 2h agree and it differs (loops wrap;
+    on a path a point needs h points on each side).  ``morse[f]`` = type of
+    face f.  Returns [(order, closed, types)]."""
+    out = []
+    h = half_window
+    for order, closed in trajs:
+        ts = [pos[f][3] for f in order]
+        n = len(order)
+        if n < min_points or max(ts) - min(ts) < min_duration or (drop_loops and closed):
+            continue
+        types = [int(morse[f]) for f in order]
+        new = list(types)
+        for j in range(n):
+            if h <= 0:
+                break
+            if closed:
+                if n <= 2 * h:
+                    continue
+                win = [types[(j - q) % n] for q in range(1, h + 1)] + [types[(j + q) % n] for q in range(1, h + 1)]
+            else:
+                if j < h or j + h >= n:
+                    continue
+                win = types[j - h:j] + types[j + 1:j + h + 1]
+            if all(w == win[0] for w in win) and win[0] != types[j]:
+                new[j] = win[0]
+        out.append((order, closed, new))
+    return out
+
+
 def positions(result):
     """{face id: (x, y, z, t)} = base + in-cell offset of each puncture."""
     b = result["base"].astype(np.float64)

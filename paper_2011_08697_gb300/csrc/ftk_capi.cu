@@ -451,6 +451,12 @@ const char *ftk_last_error(void) { return g_err.c_str(); }
 
 const char *ftk_version(void) { return "ftk-gb300 0.1 sm_103a"; }
 
+ftk_status ftk_debug_set_wait_limits(int64_t uf_steps, int64_t lookback_cycles) {
+    const cudaError_t e = set_wait_limits(uf_steps, lookback_cycles);
+    if (e != cudaSuccess) return cuda_fail(e, "setting the wait limits");
+    return FTK_OK;
+}
+
 }  // extern "C"
 
 // initial puncture and survivor capacities of a plan (grow on demand)

@@ -328,15 +328,18 @@ __global__ void __launch_bounds__(S3_THREADS, 2) k_detect3_stream(Field F, Block
                 qa_or |= o[0] | o[1];
                 qa_or |= o[2] | o[3];
             }
-            uint32_t g = 0;
+            // three independent 4-bit chains (short dependency chains), then
+            // one combine: G_x in bits 0-3, G_y in 4-7, G_z in 8-11
+            uint32_t gz = 0, gy = 0, gx = 0;
 #pragma unroll
-            for (int i = 3; i >= 0; --i) g = __funnelshift_l(qd<EXACT>(P.v[r + 1][i], M.v[r + 1][i]), g, 1);
+            for (int i = 3; i >= 0; --i) gz = __funnelshift_l(qd<EXACT>(P.v[r + 1][i], M.v[r + 1][i]), gz, 1);
 #pragma unroll
-            for (int i = 3; i >= 0; --i) g = __funnelshift_l(qd<EXACT>(Y.v[r + 2][i], Y.v[r][i]), g, 1);
-            g = __funnelshift_l(qd<EXACT>(rq, o[2]), g, 1);
-            g = __funnelshift_l(qd<EXACT>(o[3], o[1]), g, 1);
-            g = __funnelshift_l(qd<EXACT>(o[2], o[0]), g, 1);
-            g = __funnelshift_l(qd<EXACT>(o[1], lq), g, 1);
+            for (int i = 3; i >= 0; --i) gy = __funnelshift_l(qd<EXACT>(Y.v[r + 2][i], Y.v[r][i]), gy, 1);
+            gx = __funnelshift_l(qd<EXACT>(rq, o[2]), gx, 1);
+            gx = __funnelshift_l(qd<EXACT>(o[3], o[1]), gx, 1);
+            gx = __funnelshift_l(qd<EXACT>(o[2], o[0]), gx, 1);
+            gx = __funnelshift_l(qd<EXACT>(o[1], lq), gx, 1);
+            const uint32_t g = gx | (gy << 4) | (gz << 8);
             w[r] = g | (g << 16);
         }
     };

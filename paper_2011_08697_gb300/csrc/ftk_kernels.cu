@@ -57,6 +57,11 @@ template <> __device__ __forceinline__ const CellTables<3> &cells<3>() { return 
 
 constexpr int NT = 256;              // threads per CTA of every kernel here
 constexpr int UF_LIMIT = 1 << 22;    // bound on union-find retries / path steps
+// The bounds in force (device globals, so that a test can make a bounded loop
+// run out; the mbarrier waits of the detect kernels, which also drain copies
+// in flight, keep their own fixed bound)
+__device__ int g_uf_limit = UF_LIMIT;
+__device__ long long g_lookback_cycles = WAIT_CYCLES;
 
 // Exact SoS puncture test of one face; V[k] = gradient at the k-th vertex in
 // increasing global-id order.
@@ -153,7 +158,7 @@ __device__ long long warp_lookback(unsigned long long *tile_state, long long t, 
         unsigned long long v = LB_INC;   // before tile 0: prefix 0
         if (j >= 0) v = st[j];
         if (__any_sync(0xffffffffu, (v >> 62) == 0)) {
-            if (clock64() - t0 > WAIT_CYCLES) {
+            if (clock64() - t0 > g_lookback_cycles) {
                 if (lane == 0) atomicOr(status, ST_TIMEOUT);
                 break;
             }
@@ -976,7 +981,8 @@ __global__ void __launch_bounds__(NT) k_finalize(Field F, Blocking B, Workspace 
 // Linking
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ int uf_find(int *parent, int x, unsigned *status) {
-    for (int it = 0; it < UF_LIMIT; ++it) {
+    const int lim = g_uf_limit;
+    for (int it = 0; it < lim; ++it) {
         const int p = *(volatile int *)&parent[x];
         if (p == x) return x;
         const int gp = *(volatile int *)&parent[p];
@@ -988,7 +994,8 @@ __device__ __forceinline__ int uf_find(int *parent, int x, unsigned *status) {
 }
 
 __device__ __forceinline__ void uf_unite(int *parent, int a, int b, unsigned *status) {
-    for (int it = 0; it < UF_LIMIT; ++it) {
+    const int lim = g_uf_limit;
+    for (int it = 0; it < lim; ++it) {
         a = uf_find(parent, a, status);
         b = uf_find(parent, b, status);
         if (a == b) return;
@@ -1406,6 +1413,22 @@ __global__ void __launch_bounds__(NT) k_survive_eval(Field F, Workspace W) {
     const long long ns = (long long)W.ctr->survivors;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * WPB;
+    // lane l evaluates face types l and l + 32 of every cube: their chains
+    // and corner masks are read once (per-lane indices into constant memory
+    // would serialise inside the loop)
+    constexpr int NF = (T + 31) / 32;
+    int chs[NF][N];
+    uint32_t Ms[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const int tt = f * 32 + lane;
+        Ms[f] = 1u;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            chs[f][k] = tt < T ? mesh<N>().face[tt][k] : 0;
+            Ms[f] |= 1u << chs[f][k];
+        }
+    }
     for (long long s = (long long)blockIdx.x * WPB + warp; s < ns; s += stride) {
         const long long g = W.surv[s];
         const Pt b = decode_vertex(F, g);
@@ -1416,37 +1439,45 @@ __global__ void __launch_bounds__(NT) k_survive_eval(Field F, Workspace W) {
             const int ext = a == N ? F.nt : ext_of(F, a);
             if (b.c[slot] + 1 < ext) inside |= 1 << a;
         }
-        if (lane < NCRN) {
-            if (lane & ~inside) {
+        int32_t gc[N] = {};
+        if (lane < NCRN && !(lane & ~inside)) {
+            const Pt p = add_mask<N>(b, lane);
+            const long long ip = vindex(F, b) + mask_offset<N>(F, lane);
 #pragma unroll
-                for (int r = 0; r < N; ++r) Gs[warp][lane][r] = 0;
-            } else {
-                const Pt p = add_mask<N>(b, lane);
-                const long long ip = vindex(F, b) + mask_offset<N>(F, lane);
-#pragma unroll
-                for (int r = 0; r < N; ++r) Gs[warp][lane][r] = grad_at(F, p, ip, r);
-            }
+            for (int r = 0; r < N; ++r) gc[r] = grad_at(F, p, ip, r);
         }
+        if (lane < NCRN)
+#pragma unroll
+            for (int r = 0; r < N; ++r) Gs[warp][lane][r] = gc[r];
+        // bit c of neg[r]: component r is negative at corner c (the corner
+        // index is its axis mask); a face whose corners all agree in the sign
+        // of one component cannot be punctured (zero counts as positive)
+        uint32_t neg[N];
+#pragma unroll
+        for (int r = 0; r < N; ++r) neg[r] = __ballot_sync(0xffffffffu, lane < NCRN && gc[r] < 0);
         __syncwarp();
         unsigned long long m = 0;
 #pragma unroll
-        for (int t0 = 0; t0 < T; t0 += 32) {
-            const int tt = t0 + lane;
+        for (int f = 0; f < NF; ++f) {
+            const int tt = f * 32 + lane;
             bool pun = false;
             if (tt < T) {
-                const uint8_t *ch = mesh<N>().face[tt];
-                if (!(ch[N - 1] & ~inside)) {
+                const uint32_t M = Ms[f];
+                bool mixed = true;
+#pragma unroll
+                for (int r = 0; r < N; ++r) mixed &= (neg[r] & M) != 0 && (neg[r] & M) != M;
+                if (mixed && !(chs[f][N - 1] & ~inside)) {
                     int32_t V[N + 1][N];
 #pragma unroll
                     for (int k = 0; k <= N; ++k) {
-                        const int c = k == 0 ? 0 : ch[k - 1];
+                        const int c = k == 0 ? 0 : chs[f][k - 1];
 #pragma unroll
                         for (int r = 0; r < N; ++r) V[k][r] = Gs[warp][c][r];
                     }
                     pun = face_punctured<N>(V);
                 }
             }
-            m |= (unsigned long long)__ballot_sync(0xffffffffu, pun) << t0;
+            m |= (unsigned long long)__ballot_sync(0xffffffffu, pun) << (32 * f);
         }
         if (lane == 0) W.surv_mask[s] = m;
         __syncwarp();
@@ -2214,6 +2245,61 @@ __global__ void __launch_bounds__(NT) k_traj_walk(Workspace W, const int *nbr, c
     }
 }
 
+// Post-processing of the trajectories (paper Sec. 4.2, filtering and type
+// smoothing).  Per trajectory: kept iff its time extent (largest minus
+// smallest point time) is at least min_duration, it has at least min_points
+// points and it is not a loop when loops are dropped.
+__global__ void __launch_bounds__(NT) k_traj_keep(const ftk_cp *rec, const long long *toff, const uint8_t *closed,
+                                                   long long ntraj, double min_duration, long long min_points,
+                                                   int drop_loops, int *kept_size, int *kept_one) {
+    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < ntraj; t += (long long)gridDim.x * NT) {
+        const long long a0 = toff[t], n = toff[t + 1] - a0;
+        double lo = 1e300, hi = -1e300;
+        for (long long j = 0; j < n; ++j) {
+            const double tt = (double)rec[a0 + j].base[3] + (double)rec[a0 + j].off[3];
+            lo = tt < lo ? tt : lo;
+            hi = tt > hi ? tt : hi;
+        }
+        const bool keep = n >= min_points && hi - lo >= min_duration && !(drop_loops && closed[t]);
+        kept_size[t] = keep ? (int)n : 0;
+        kept_one[t] = keep ? 1 : 0;
+    }
+}
+
+// Copies the kept trajectories to their new offsets; with h > 0 a point's
+// Morse index is replaced by the common index of the h points before and
+// the h points after it along the path when those 2h points all agree and
+// it differs (loops wrap around; on a path, points with fewer than h
+// neighbours on a side keep theirs).  Every decision reads the original
+// indices.
+__global__ void __launch_bounds__(NT) k_traj_compact(const ftk_cp *rec, const long long *toff, const uint8_t *closed,
+                                                      long long ntraj, int h, const long long *noff,
+                                                      const long long *nidx, const int *kept_one, ftk_cp *out,
+                                                      long long *out_off, uint8_t *out_closed) {
+    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < ntraj; t += (long long)gridDim.x * NT) {
+        if (!kept_one[t]) continue;
+        const long long a0 = toff[t], n = toff[t + 1] - a0;
+        const long long o = noff[t], k = nidx[t];
+        out_off[k] = o;
+        out_closed[k] = closed[t];
+        const bool loop = closed[t] != 0;
+        for (long long j = 0; j < n; ++j) {
+            ftk_cp r = rec[a0 + j];
+            if (h > 0 && (loop ? n > 2 * (long long)h : (j >= h && j + h < n))) {
+                const long long jm = (j - 1 + n) % n;
+                const int8_t ref = rec[a0 + jm].morse_index;
+                bool same = true;
+                for (int q = 1; q <= h && same; ++q) {
+                    same &= rec[a0 + (j - q + n) % n].morse_index == ref;
+                    same &= rec[a0 + (j + q) % n].morse_index == ref;
+                }
+                if (same && ref != r.morse_index) r.morse_index = ref;
+            }
+            out[o + j] = r;
+        }
+    }
+}
+
 // time (grid units) of a puncture record
 __device__ __forceinline__ double rec_t(const ftk_cp &r) { return (double)r.base[3] + (double)r.off[3]; }
 __device__ __forceinline__ double rec_c(const ftk_cp &r, int a) { return (double)r.base[a] + (double)r.off[a]; }
@@ -2283,6 +2369,40 @@ cudaError_t launch_traj_slice(const TrajBuffers &T, long long ntraj, double t0, 
                               ftk_slice_point *pts, cudaStream_t s) {
     k_traj_slice<<<sparse_grid(), NT, 0, s>>>(T.rec, T.toff, T.closed, ntraj, t0, cnt, soff, pts);
     if (!pts) k_scan_one_block<<<1, NT, 0, s>>>(cnt, ntraj, soff);
+    return cudaGetLastError();
+}
+
+}  // namespace ftk
+
+namespace ftk {
+
+cudaError_t set_wait_limits(long long uf_steps, long long lookback_cycles) {
+    const int u = uf_steps > 0 ? (int)std::min<long long>(uf_steps, UF_LIMIT) : UF_LIMIT;
+    const long long c = lookback_cycles > 0 ? std::min<long long>(lookback_cycles, WAIT_CYCLES) : WAIT_CYCLES;
+    cudaError_t e = cudaMemcpyToSymbol(g_uf_limit, &u, sizeof(u));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_lookback_cycles, &c, sizeof(c));
+    return e;
+}
+
+}  // namespace ftk
+
+namespace ftk {
+
+cudaError_t launch_traj_filter(const TrajBuffers &T, long long ntraj, double min_duration, long long min_points,
+                               int drop_loops, int h, int *kept_size, int *kept_one, long long *noff,
+                               long long *nidx, cudaStream_t s) {
+    k_traj_keep<<<sparse_grid(), NT, 0, s>>>(T.rec, T.toff, T.closed, ntraj, min_duration, min_points, drop_loops,
+                                             kept_size, kept_one);
+    k_scan_one_block<<<1, NT, 0, s>>>(kept_size, ntraj, noff);
+    k_scan_one_block<<<1, NT, 0, s>>>(kept_one, ntraj, nidx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_traj_compact(const TrajBuffers &T, long long ntraj, int h, const long long *noff,
+                                const long long *nidx, const int *kept_one, ftk_cp *out, long long *out_off,
+                                uint8_t *out_closed, cudaStream_t s) {
+    k_traj_compact<<<sparse_grid(), NT, 0, s>>>(T.rec, T.toff, T.closed, ntraj, h, noff, nidx, kept_one, out, out_off,
+                                                out_closed);
     return cudaGetLastError();
 }
 

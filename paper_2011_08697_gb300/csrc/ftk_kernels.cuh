@@ -253,6 +253,20 @@ cudaError_t launch_traj_walk(const Workspace &W, long long P, long long ntraj, c
 cudaError_t launch_traj_slice(const TrajBuffers &T, long long ntraj, double t0, int *cnt, long long *soff,
                               ftk_slice_point *pts, cudaStream_t s);
 
+// bounds of the union-find loops and the look-back waits on the current
+// device (<= 0: the defaults)
+cudaError_t set_wait_limits(long long uf_steps, long long lookback_cycles);
+
+// filtering: kept sizes / flags per trajectory and their scans (noff[ntraj],
+// nidx[ntraj] = totals); compaction of the kept trajectories with type
+// smoothing of half-window h
+cudaError_t launch_traj_filter(const TrajBuffers &T, long long ntraj, double min_duration, long long min_points,
+                               int drop_loops, int h, int *kept_size, int *kept_one, long long *noff,
+                               long long *nidx, cudaStream_t s);
+cudaError_t launch_traj_compact(const TrajBuffers &T, long long ntraj, int h, const long long *noff,
+                                const long long *nidx, const int *kept_one, ftk_cp *out, long long *out_off,
+                                uint8_t *out_closed, cudaStream_t s);
+
 // name of the step whose CUDA call failed in the last launch_pipeline
 const char *last_launch_stage();
 

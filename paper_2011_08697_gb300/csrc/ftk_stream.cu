@@ -90,8 +90,15 @@ struct ftk_stream {
     uint32_t *st_in = nullptr, *st_out = nullptr;
     long long st_words = 0;
     // one captured push (k >= 2) replayed for every later push
+    cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    uint64_t serial = 0;          // unique per stream opened in this process
+    uint64_t graph_version = 0;   // bumped whenever the captured push is dropped
 };
+
+namespace {
+std::atomic<uint64_t> g_stream_serial{1};
+}
 
 namespace {
 
@@ -121,7 +128,10 @@ ftk_status grow(T **ptr, long long cap, long long need, long long keep, cudaStre
 
 void drop_graph(ftk_stream *st) {
     if (st->exec) cudaGraphExecDestroy(st->exec);
+    if (st->graph) cudaGraphDestroy(st->graph);
+    if (st->exec || st->graph) ++st->graph_version;
     st->exec = nullptr;
+    st->graph = nullptr;
 }
 
 // reserves `add` more bytes of device memory for the stream: within the
@@ -301,13 +311,90 @@ void capture_push(ftk_stream *st) {
     if (cudaGraphInstantiate(&st->exec, g, 0) != cudaSuccess) {
         cudaGetLastError();
         st->exec = nullptr;
+        cudaGraphDestroy(g);
+        return;
     }
-    cudaGraphDestroy(g);
+    st->graph = g;   // kept: batched pushes nest it in a graph of many streams
+}
+
+// Graphs of several streams' steady-state pushes (their captured graphs as
+// children of one graph, so one launch queues them all), cached by the
+// streams' serials and graph versions; a stream's entries go when it closes.
+struct BatchGraph {
+    std::vector<uint64_t> key;   // serial, version of each stream in call order
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batches;
+uint64_t g_batch_clock = 0;
+constexpr size_t kMaxBatchGraphs = 8;
+
+void evict_batches(uint64_t serial) {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (size_t i = 0; i < g_batches.size();) {
+        bool hit = false;
+        for (size_t k = 0; k < g_batches[i].key.size(); k += 2) hit |= g_batches[i].key[k] == serial;
+        if (hit) {
+            cudaGraphExecDestroy(g_batches[i].exec);
+            g_batches.erase(g_batches.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+// the executable graph of these streams' captured pushes (nullptr if it
+// cannot be built)
+cudaGraphExec_t batch_exec(ftk_stream *const *v, int n) {
+    std::vector<uint64_t> key;
+    key.reserve(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        key.push_back(v[i]->serial);
+        key.push_back(v[i]->graph_version);
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (auto &b : g_batches)
+        if (b.key == key) {
+            b.last_use = ++g_batch_clock;
+            return b.exec;
+        }
+    cudaGraph_t parent = nullptr;
+    if (cudaGraphCreate(&parent, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    bool ok = true;
+    for (int i = 0; i < n && ok; ++i) {
+        cudaGraphNode_t node;
+        ok = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, v[i]->graph) == cudaSuccess;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&exec, parent, 0) == cudaSuccess;
+    cudaGraphDestroy(parent);
+    if (!ok) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (g_batches.size() >= kMaxBatchGraphs) {
+        size_t lru = 0;
+        for (size_t i = 1; i < g_batches.size(); ++i)
+            if (g_batches[i].last_use < g_batches[lru].last_use) lru = i;
+        cudaGraphExecDestroy(g_batches[lru].exec);
+        g_batches.erase(g_batches.begin() + (long)lru);
+    }
+    BatchGraph b;
+    b.key = std::move(key);
+    b.exec = exec;
+    b.last_use = ++g_batch_clock;
+    g_batches.push_back(std::move(b));
+    return exec;
 }
 
 void release(ftk_stream *st) {
     if (!st) return;
     if (st->cs) cudaStreamSynchronize(st->cs);
+    if (st->serial) evict_batches(st->serial);
     drop_graph(st);
     if (st->plan1) ftk_plan_destroy(st->plan1);
     if (st->plan2) ftk_plan_destroy(st->plan2);
@@ -433,6 +520,7 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
     st->slice_verts = (long long)nx * ny * nz;
     st->T = ndim == 2 ? 12 : 60;
     st->tbit = ndim == 2 ? 4 : 8;
+    st->serial = g_stream_serial.fetch_add(1);
     if ((s = plan_create(ndim, nx, ny, nz, 1, &st->p, nullptr, &st->plan1)) != FTK_OK ||
         (s = plan_create(ndim, nx, ny, nz, 2, &st->p, nullptr, &st->plan2)) != FTK_OK) {
         release(st);
@@ -603,12 +691,13 @@ ftk_status push_begin(ftk_stream *st, const float *slice) {
 }
 
 // second half: wait for the push, repair an overflowed run, hand out the delta
-ftk_status push_end(ftk_stream *st, ftk_result **delta) {
+ftk_status push_end(ftk_stream *st, ftk_result **delta, bool synced = false) {
     ftk_plan *pl = st->k == 0 ? st->plan1 : st->plan2;
     ftk_status s;
     cudaError_t e;
     // a blocking-sync event: the waiting thread sleeps instead of spinning
-    if ((e = cudaEventSynchronize(st->done)) != cudaSuccess) return stream_error(st, FTK_ERR_CUDA, cudaGetErrorString(e));
+    if (!synced && (e = cudaEventSynchronize(st->done)) != cudaSuccess)
+        return stream_error(st, FTK_ERR_CUDA, cudaGetErrorString(e));
     StreamView v = read_view(st);
     if (v.run_status & (ST_OVERFLOW | ST_SOVERFLOW | ST_WIDE)) {
         // not merged: repair the run (larger capacity or exact rounding),
@@ -662,6 +751,42 @@ ftk_status ftk_streams_push(int n, ftk_stream *const *streams, const float *cons
         for (int i = 0; i < n; ++i) {
             if (!streams[i] || !slices[i]) return fail(FTK_ERR_ARG, "NULL stream or slice");
             if (!seen.insert(streams[i]).second) return fail(FTK_ERR_ARG, "a stream appears twice in one call");
+        }
+    }
+    // steady state (every stream past its second push, device slices): the
+    // streams' captured pushes as one graph, one launch for the whole call
+    bool batched = n >= 2;
+    for (int i = 0; i < n && batched; ++i)
+        batched = !streams[i]->failed && streams[i]->k >= 2 && is_device_pointer(slices[i]);
+    if (batched) {
+        for (int i = 0; i < n && batched; ++i) {
+            ftk_stream *st = streams[i];
+            st->hSrc->ptr = slices[i];
+            if (ensure_all(st, st->plan2->W.cap) != FTK_OK) {
+                batched = false;   // the per-stream path below reports it
+                break;
+            }
+            if (!st->exec) capture_push(st);
+            batched = st->exec != nullptr;
+        }
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        cudaGraphExec_t ex = batched ? batch_exec(streams, n) : nullptr;
+        if (ex) {
+            cudaStream_t cs = streams[0]->cs;
+            cudaError_t e;
+            if ((e = cudaGraphLaunch(ex, cs)) != cudaSuccess || (e = cudaEventRecord(streams[0]->done, cs)) != cudaSuccess ||
+                (e = cudaEventSynchronize(streams[0]->done)) != cudaSuccess) {
+                for (int i = 0; i < n; ++i) stream_error(streams[i], FTK_ERR_CUDA, nullptr);
+                return cuda_fail(e, "batched push");
+            }
+            ftk_status first = FTK_OK;
+            std::string first_msg;
+            for (int i = 0; i < n; ++i) {
+                const ftk_status s = push_end(streams[i], &deltas[i], true);
+                if (s != FTK_OK && first == FTK_OK) { first = s; first_msg = ftk_last_error(); }
+            }
+            if (first != FTK_OK) return fail(first, first_msg);
+            return FTK_OK;
         }
     }
     // queue every push first (their device work overlaps on the streams' own

@@ -131,6 +131,79 @@ ftk_status ftk_plan_trajectories(ftk_plan *pl, ftk_traj **out) {
     return FTK_OK;
 }
 
+ftk_status ftk_plan_trajectories_filtered(ftk_plan *pl, const ftk_traj_filter *flt, ftk_traj **out) {
+    if (out) *out = nullptr;
+    if (!pl || !flt || !out) return fail(FTK_ERR_ARG, "plan, filter and out must be non-NULL");
+    if (flt->smooth_half_window < 0 || flt->min_points < 0 || !(flt->min_duration == flt->min_duration))
+        return fail(FTK_ERR_ARG, "invalid filter");
+    long long P = 0;
+    ftk_status s = build_traj(pl, &P);
+    if (s != FTK_OK) return s;
+    const long long n = pl->traj_n;
+    ftk_traj *tr = new (std::nothrow) ftk_traj;
+    if (!tr) return fail(FTK_ERR_NOMEM, "host allocation failed");
+    tr->n = 0;
+    tr->off = nullptr;
+    tr->pts = nullptr;
+    tr->closed = nullptr;
+    int *ksize = nullptr, *kone = nullptr;
+    long long *noff = nullptr, *nidx = nullptr, *d_off = nullptr;
+    ftk_cp *d_pts = nullptr;
+    uint8_t *d_closed = nullptr;
+    long long tot[2] = {0, 0};
+    cudaError_t e = cudaSuccess;
+    cudaStream_t st = pl->stream;
+    const size_t nn = (size_t)std::max<long long>(1, n);
+    if (cudaMalloc(&ksize, sizeof(int) * nn) != cudaSuccess || cudaMalloc(&kone, sizeof(int) * nn) != cudaSuccess ||
+        cudaMalloc(&noff, sizeof(long long) * (nn + 1)) != cudaSuccess ||
+        cudaMalloc(&nidx, sizeof(long long) * (nn + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        s = fail(FTK_ERR_NOMEM, "device allocation failed");
+    } else if (n > 0) {
+        if ((e = launch_traj_filter(pl->traj, n, flt->min_duration, flt->min_points, flt->drop_loops,
+                                    flt->smooth_half_window, ksize, kone, noff, nidx, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&tot[0], noff + n, sizeof(long long), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&tot[1], nidx + n, sizeof(long long), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            s = cuda_fail(e, "trajectory filter");
+        } else if (cudaMalloc(&d_pts, sizeof(ftk_cp) * (size_t)std::max<long long>(1, tot[0])) != cudaSuccess ||
+                   cudaMalloc(&d_off, sizeof(long long) * (size_t)(tot[1] + 1)) != cudaSuccess ||
+                   cudaMalloc(&d_closed, (size_t)std::max<long long>(1, tot[1])) != cudaSuccess) {
+            cudaGetLastError();
+            s = fail(FTK_ERR_NOMEM, "device allocation failed");
+        } else if ((e = launch_traj_compact(pl->traj, n, flt->smooth_half_window, noff, nidx, kone, d_pts, d_off,
+                                            d_closed, st)) != cudaSuccess ||
+                   (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            s = cuda_fail(e, "trajectory compaction");
+        }
+    }
+    if (s == FTK_OK) {
+        const long long nk = tot[1], pk = tot[0];
+        tr->n = nk;
+        tr->off = (int64_t *)std::malloc(sizeof(int64_t) * (size_t)(nk + 1));
+        tr->pts = (ftk_cp *)std::malloc(sizeof(ftk_cp) * (size_t)std::max<long long>(1, pk));
+        tr->closed = (uint8_t *)std::malloc((size_t)std::max<long long>(1, nk));
+        if (!tr->off || !tr->pts || !tr->closed) {
+            s = fail(FTK_ERR_NOMEM, "host allocation failed");
+        } else {
+            tr->off[nk] = pk;
+            if (nk > 0 &&
+                ((e = cudaMemcpy(tr->off, d_off, sizeof(int64_t) * (size_t)nk, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+                 (e = cudaMemcpy(tr->pts, d_pts, sizeof(ftk_cp) * (size_t)pk, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+                 (e = cudaMemcpy(tr->closed, d_closed, (size_t)nk, cudaMemcpyDeviceToHost)) != cudaSuccess))
+                s = cuda_fail(e, "filtered trajectory download");
+        }
+    }
+    cudaFree(ksize); cudaFree(kone); cudaFree(noff); cudaFree(nidx);
+    cudaFree(d_pts); cudaFree(d_off); cudaFree(d_closed);
+    if (s != FTK_OK) {
+        ftk_traj_free(tr);
+        return s;
+    }
+    *out = tr;
+    return FTK_OK;
+}
+
 int64_t ftk_traj_count(const ftk_traj *tr) { return tr ? tr->n : 0; }
 const int64_t *ftk_traj_offsets(const ftk_traj *tr) { return tr ? tr->off : nullptr; }
 const ftk_cp *ftk_traj_points(const ftk_traj *tr) { return tr ? tr->pts : nullptr; }

@@ -70,7 +70,13 @@ EXPORTS = [
     "ftk_streams_push", "ftk_stream_open_wait", "ftk_stream_footprint",
     "ftk_plan_trajectories", "ftk_traj_count", "ftk_traj_offsets", "ftk_traj_points", "ftk_traj_closed",
     "ftk_traj_free", "ftk_plan_slice", "ftk_slice_count", "ftk_slice_data", "ftk_slice_free",
+    "ftk_debug_set_wait_limits", "ftk_plan_trajectories_filtered",
 ]
+
+
+class ftk_traj_filter(ctypes.Structure):
+    _fields_ = [("min_duration", ctypes.c_double), ("min_points", ctypes.c_int64),
+                ("drop_loops", ctypes.c_int32), ("smooth_half_window", ctypes.c_int32)]
 
 SLICE_DTYPE = np.dtype([("label", "<i8"), ("face_a", "<i8"), ("face_b", "<i8"), ("pos", "<f8", (3,))])
 assert SLICE_DTYPE.itemsize == 48
@@ -126,7 +132,9 @@ def lib():
         "ftk_stream_open_wait": (i32, [vp, i32, i64, i64, i64, ctypes.POINTER(ftk_params), i64, pp]),
         "ftk_stream_footprint": (i32, [i32, i64, i64, i64, ctypes.POINTER(ftk_params),
                                        ctypes.POINTER(ctypes.c_uint64)]),
+        "ftk_debug_set_wait_limits": (i32, [i64, i64]),
         "ftk_plan_trajectories": (i32, [vp, pp]),
+        "ftk_plan_trajectories_filtered": (i32, [vp, ctypes.POINTER(ftk_traj_filter), pp]),
         "ftk_traj_count": (i64, [vp]),
         "ftk_traj_offsets": (vp, [vp]),
         "ftk_traj_points": (vp, [vp]),
@@ -282,12 +290,19 @@ class Plan:
         _check(lib().ftk_plan_download_into(self._h, ctypes.c_void_p(buf.ctypes.data), len(buf), ctypes.byref(c)))
         return buf[: c.value]
 
-    def trajectories(self):
+    def trajectories(self, min_duration: float | None = None, min_points: int = 0, drop_loops: bool = False,
+                     smooth_half_window: int = 0):
         """(offsets [n+1], points [P] CP_DTYPE in trajectory then path order,
-        closed [n] bool) of the last execute."""
+        closed [n] bool) of the last execute; with any filter argument set,
+        the filtered and type-smoothed trajectories."""
         L = lib()
         h = ctypes.c_void_p()
-        _check(L.ftk_plan_trajectories(self._h, ctypes.byref(h)))
+        if min_duration is None and not min_points and not drop_loops and not smooth_half_window:
+            _check(L.ftk_plan_trajectories(self._h, ctypes.byref(h)))
+        else:
+            flt = ftk_traj_filter(float(min_duration or 0.0), int(min_points), int(bool(drop_loops)),
+                                  int(smooth_half_window))
+            _check(L.ftk_plan_trajectories_filtered(self._h, ctypes.byref(flt), ctypes.byref(h)))
         try:
             n = L.ftk_traj_count(h)
             off = np.ctypeslib.as_array(ctypes.cast(L.ftk_traj_offsets(h), ctypes.POINTER(ctypes.c_int64)),

@@ -87,3 +87,26 @@ def test_stream_growth_is_charged_to_the_budget(F):
     s.close(False)
     assert tight.used() == 0
     tight.close()
+
+
+def test_bounded_device_loops_report_timeout(F):
+    """With the union-find bound set to one step, a run whose trajectories
+    need deeper finds gives up and reports FTK_ERR_TIMEOUT (no fault, no
+    hang); with the defaults restored the same plan matches the oracle."""
+    L = F.lib()
+    cases = [synth.spiral_woven(32, 10), synth.random_levels((4, 7, 9, 8), seed=21)]
+    for f in cases:
+        ref = cp.track(f)
+        assert len(np.unique(ref["label"])) < len(ref["face_id"])   # some trajectory has >= 2 faces
+        with F.Plan(f.shape) as plan:
+            x = torch.from_numpy(f).cuda()
+            try:
+                assert L.ftk_debug_set_wait_limits(1, 1) == 0
+                plan.execute(x)
+                with pytest.raises(F.FtkError) as e:
+                    plan.count()
+                assert e.value.status == 5
+            finally:
+                assert L.ftk_debug_set_wait_limits(0, 0) == 0
+            plan.execute(x)
+            compare_full(plan.download(), ref)

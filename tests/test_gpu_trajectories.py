@@ -75,3 +75,27 @@ def test_trajectories_and_slices_match_oracle(F, name, make, shift):
                 assert np.max(np.abs(g["pos"] - np.asarray(w[3]))) <= OFF_TOL
         if name.startswith("minimum"):
             assert len(trajs) == 1 and not closed[0]
+
+
+@pytest.mark.parametrize("name,make,shift", [CASES[1], CASES[3], CASES[5], CASES[8]], ids=[CASES[i][0] for i in (1, 3, 5, 8)])
+@pytest.mark.parametrize("flt", [
+    dict(min_duration=1.45), dict(min_points=4), dict(drop_loops=True), dict(smooth_half_window=2),
+    dict(min_duration=0.55, drop_loops=True, smooth_half_window=1),
+])
+def test_filtered_trajectories_match_oracle(F, name, make, shift, flt):
+    f = make()
+    ref = cp.track(f, shift=shift)
+    trajs = cp.trajectories(ref["grid"], ref["face_id"], ref["label"])
+    pos = cp.positions(ref)
+    morse = dict(zip(ref["face_id"].tolist(), ref["morse"].tolist()))
+    want = cp.filter_trajectories(trajs, pos, morse, min_duration=flt.get("min_duration", 0.0),
+                                  min_points=flt.get("min_points", 0), drop_loops=flt.get("drop_loops", False),
+                                  half_window=flt.get("smooth_half_window", 0))
+    with F.Plan(f.shape, F.make_params(quant_shift=shift)) as plan:
+        plan.execute(torch.from_numpy(f).cuda())
+        off, pts, closed = plan.trajectories(**flt)
+    assert len(off) == len(want) + 1
+    for i, (order, cl, types) in enumerate(want):
+        assert pts["face_id"][off[i]:off[i + 1]].tolist() == order
+        assert pts["morse_index"][off[i]:off[i + 1]].tolist() == types
+        assert bool(closed[i]) == cl

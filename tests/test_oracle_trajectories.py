@@ -87,3 +87,52 @@ def test_polyline_structure(make):
             assert lo <= t0 <= hi
             s = (t0 - pa[3]) / (pb[3] - pa[3])
             assert np.allclose(xyz, (pa + s * (pb - pa))[:3])
+
+
+def _fake(types, closed=False, times=None):
+    order = list(range(100, 100 + len(types)))
+    ts = times if times is not None else list(range(len(types)))
+    pos = {f: (0.0, 0.0, 0.0, float(t)) for f, t in zip(order, ts)}
+    morse = dict(zip(order, types))
+    return [(order, closed)], pos, morse
+
+
+@pytest.mark.parametrize("types,closed,h,want", [
+    ([0, 0, 0, 1, 0, 0, 0], False, 2, [0, 0, 0, 0, 0, 0, 0]),     # a lone flip inside a run
+    ([0, 0, 1, 1, 0, 0], False, 2, [0, 0, 1, 1, 0, 0]),           # two flips: windows disagree
+    ([1, 0, 0, 0, 0], False, 2, [1, 0, 0, 0, 0]),                 # path ends keep their type
+    ([1, 1, 1, 1, 1, 0], True, 2, [1, 1, 1, 1, 1, 1]),            # loops wrap around
+    ([2, 0, 2], False, 1, [2, 2, 2]),
+    ([2, 0, 2], True, 1, [2, 2, 2]),                              # loop of 3, h = 1: both neighbours agree
+    ([2, 0, 2, 0], True, 2, [2, 0, 2, 0]),                        # a loop of 2h points is left alone
+    ([-1, 1, -1, 1, 1, 1, 1], False, 2, [-1, 1, -1, 1, 1, 1, 1]),
+    ([1, 1, -1, 1, 1], False, 2, [1, 1, 1, 1, 1]),               # a degenerate type is smoothed too
+])
+def test_type_smoothing_rule(types, closed, h, want):
+    trajs, pos, morse = _fake(types, closed)
+    (order, cl, got), = cp.filter_trajectories(trajs, pos, morse, half_window=h)
+    if closed and len(types) <= 2 * h:
+        assert got == types
+    else:
+        assert got == want
+
+
+def test_filters_by_duration_points_and_loops():
+    f = synth.moving_minimum(21, 8, (10, 10), (0.5, 0.5), 2)
+    r, trajs = _trajs(f, 17)
+    pos = cp.positions(r)
+    morse = dict(zip(r["face_id"].tolist(), r["morse"].tolist()))
+    assert len(cp.filter_trajectories(trajs, pos, morse, min_duration=7.0)) == 1     # spans t = 0 .. 7
+    assert len(cp.filter_trajectories(trajs, pos, morse, min_duration=7.001)) == 0
+    n = len(trajs[0][0])
+    assert len(cp.filter_trajectories(trajs, pos, morse, min_points=n)) == 1
+    assert len(cp.filter_trajectories(trajs, pos, morse, min_points=n + 1)) == 0
+    # loops: a degenerate field has closed trajectories; dropping them keeps the rest
+    g = synth.random_levels((5, 13, 22), seed=6)
+    r, trajs = _trajs(g)
+    pos = cp.positions(r)
+    morse = dict(zip(r["face_id"].tolist(), r["morse"].tolist()))
+    nloops = sum(1 for _, c in trajs if c)
+    assert nloops > 0
+    kept = cp.filter_trajectories(trajs, pos, morse, drop_loops=True)
+    assert len(kept) == len(trajs) - nloops and not any(c for _, c, _ in kept)
