@@ -61,7 +61,9 @@ typedef enum {
 } ftk_status;
 
 #define FTK_FLAG_STAGE_TIMES 1u   /* record per-stage device times (plans) */
-#define FTK_FLAG_AUTOTUNE 2u      /* choose each shape's time chunking by measurement */
+#define FTK_FLAG_AUTOTUNE 2u      /* choose each shape's launch shape (time chunking; cube planes
+                                     per unit of the 3D streaming kernel) by measurement on the
+                                     first execute of a plan or batch, cached per shape */
 
 /* Tracking parameters.  ftk_params_default() fills the defaults. */
 typedef struct {
@@ -116,13 +118,14 @@ const char *ftk_status_string(ftk_status s);
 const char *ftk_last_error(void);
 /* Library version string, e.g. "ftk-gb300 0.1 sm_103a". */
 const char *ftk_version(void);
-/* Test hook (the paper has no counterpart): bounds, on the current device,
- * of the union-find loops (path steps and retries per operation) and of the
- * decoupled look-back waits of the scans (clock cycles).  A loop that runs
- * out gives up, and the run reports FTK_ERR_TIMEOUT; the device stays
- * usable.  Values <= 0 restore the defaults (2^22 steps, 4e9 cycles).  The
- * detect kernels' waits on their bulk copies keep their own bound.  Affects
- * every plan on the device; not for concurrent use with other calls. */
+/* Test hook (the paper has no counterpart): bounds of the union-find path
+ * walks of the label pass (steps per find; later launches in this process)
+ * and of the decoupled look-back waits of the scans (clock cycles; on the
+ * current device).  A loop that runs out gives up and the run reports
+ * FTK_ERR_TIMEOUT; the device stays usable.  Values <= 0 restore the
+ * defaults (2^22 steps, 4e9 cycles).  The linking, stream merges and the
+ * detect kernels' waits on their bulk copies keep their own fixed bounds.
+ * Not for concurrent use with other calls. */
 ftk_status ftk_debug_set_wait_limits(int64_t uf_steps, int64_t lookback_cycles);
 
 /* ---------------------------------------------------------------------

@@ -175,9 +175,11 @@ ftk_status choose_blocking(int ndim, const Field &F, Blocking &B, int &variant) 
     }
     if (ndim == 3 && F.pitch % 4 == 0 && F.pitch <= STREAM3_MAX_NX) {
         variant = VAR_STREAM3;
-        // the kernel's consumer warps fix the rows per unit; 8 cube planes
+        // the kernel's consumer warps fix the rows per unit; two cube planes
+        // per unit measured fastest on 128^3 x 16 (against 4 and 8: more,
+        // shorter units balance better than they lose to the z halo)
         B.ry = stream3_ry(F.pitch);
-        B.rz = std::min(8, F.nz);
+        B.rz = std::min(2, F.nz);
         B.nyb = (F.ny + B.ry - 1) / B.ry;
         B.nzb = (F.nz + B.rz - 1) / B.rz;
         choose_time_chunks(F, B, (long long)B.nyb * B.nzb, (long long)sms * stream3_ctas_per_sm(F.pitch, B));
@@ -317,7 +319,12 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tuned_ntc;
+// a tuned launch shape: time chunks, and (3D streaming) cube planes per unit
+struct Tuned {
+    int ntc;
+    int rz;
+};
+std::map<TuneKey, Tuned> g_tuned;
 
 TuneKey tune_key(const ftk_plan *pl) {
     return TuneKey{pl->ndim, pl->F.nx, pl->F.ny, pl->F.nz, pl->F.nt, pl->variant, sm_count()};
@@ -328,10 +335,21 @@ void set_chunks(ftk_plan *pl, int ntc) {
     pl->B.ntc = (pl->F.nt + pl->B.tc - 1) / pl->B.tc;
 }
 
+// cube planes per unit (segments are per z plane, so nothing else changes)
+void set_rz(ftk_plan *pl, int rz) {
+    pl->B.rz = std::max(1, std::min(rz, pl->F.nz));
+    pl->B.nzb = (pl->F.nz + pl->B.rz - 1) / pl->B.rz;
+}
+
+void set_tuned(ftk_plan *pl, const Tuned &t) {
+    if (pl->ndim == 3 && pl->variant != VAR_TILE) set_rz(pl, t.rz);
+    set_chunks(pl, t.ntc);
+}
+
 void apply_tuned(ftk_plan *pl) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tuned_ntc.find(tune_key(pl));
-    if (it != g_tuned_ntc.end()) set_chunks(pl, it->second);
+    auto it = g_tuned.find(tune_key(pl));
+    if (it != g_tuned.end()) set_tuned(pl, it->second);
 }
 
 }  // namespace
@@ -380,24 +398,33 @@ ftk_status ftk::plan_result(ftk_plan *pl, ftk_result **out) { return make_result
 ftk_status ftk::plan_autotune(ftk_plan *pl, const float *f, cudaStream_t s) {
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        auto it = g_tuned_ntc.find(tune_key(pl));
-        if (it != g_tuned_ntc.end()) {
-            set_chunks(pl, it->second);
+        auto it = g_tuned.find(tune_key(pl));
+        if (it != g_tuned.end()) {
+            set_tuned(pl, it->second);
             return FTK_OK;
         }
     }
-    // candidates: the heuristic choice and powers of two around it
+    // candidates: the heuristic time chunking and powers of two around it;
+    // for the 3D streaming kernel also 2, 4 and 8 cube planes per unit (each
+    // with the chunkings that give about one and two waves)
     const int heur = pl->B.ntc;
-    std::vector<int> cand = {heur};
+    const int rz0 = pl->B.rz;
+    std::vector<Tuned> cand = {{heur, rz0}};
     for (int c = 1; c <= pl->F.nt; c *= 2)
-        if (c != heur && c <= 4 * heur + 4 && 4 * c + 4 >= heur) cand.push_back(c);
+        if (c != heur && c <= 4 * heur + 4 && 4 * c + 4 >= heur) cand.push_back({c, rz0});
+    if (pl->ndim == 3 && pl->variant != VAR_TILE) {
+        for (int rz : {2, 4, 8}) {
+            if (rz == rz0 || rz > pl->F.nz) continue;
+            for (int c = 1; c <= pl->F.nt && c <= 8; c *= 2) cand.push_back({c, rz});
+        }
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int best_ntc = heur;
-    for (int c : cand) {
-        set_chunks(pl, c);
+    Tuned bt = cand[0];
+    for (const Tuned &c : cand) {
+        set_tuned(pl, c);
         float tot = 0.0f;
         for (int rep = 0; rep < 3; ++rep) {
             ftk_status st = launch(pl, f, s, pl->variant);      // first run warms up
@@ -412,13 +439,13 @@ ftk_status ftk::plan_autotune(ftk_plan *pl, const float *f, cudaStream_t s) {
             cudaEventElapsedTime(&ms, e0, e1);
             tot += ms;
         }
-        if (tot < best) { best = tot; best_ntc = c; }
+        if (tot < best) { best = tot; bt = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    set_chunks(pl, best_ntc);
+    set_tuned(pl, bt);
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned_ntc[tune_key(pl)] = best_ntc;
+    g_tuned[tune_key(pl)] = bt;
     return FTK_OK;
 }
 
@@ -459,17 +486,22 @@ ftk_status ftk_debug_set_wait_limits(int64_t uf_steps, int64_t lookback_cycles) 
 
 }  // extern "C"
 
-// initial puncture and survivor capacities of a plan (grow on demand)
-static long long initial_cap(const ftk_params &p, long long nverts) {
-    return p.max_punctures > 0 ? p.max_punctures
-                               : std::max<long long>(1 << 16, std::min<long long>(nverts / 32, 1LL << 26));
+// initial puncture and survivor capacities of a plan (grow on demand); the
+// compact form (in-situ stream slabs, which are small and many) starts
+// smaller, so that the grid-stride kernels sized by the capacities launch
+// few blocks
+static long long initial_cap(const ftk_params &p, long long nverts, bool compact = false) {
+    if (p.max_punctures > 0) return p.max_punctures;
+    return compact ? std::max<long long>(1 << 12, std::min<long long>(nverts / 128, 1LL << 26))
+                   : std::max<long long>(1 << 16, std::min<long long>(nverts / 32, 1LL << 26));
 }
-static long long initial_scap(long long nverts) {
-    return std::max<long long>(1 << 16, std::min<long long>(nverts / 32, 1LL << 26));
+static long long initial_scap(long long nverts, bool compact = false) {
+    return compact ? std::max<long long>(1 << 12, std::min<long long>(nverts / 64, 1LL << 26))
+                   : std::max<long long>(1 << 16, std::min<long long>(nverts / 32, 1LL << 26));
 }
 
 ftk_status ftk::plan_sizes(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, const ftk_params *p,
-                           PlanSizes *out) {
+                           PlanSizes *out, bool compact) {
     if (ndim != 2 && ndim != 3) return fail(FTK_ERR_ARG, "ndim must be 2 or 3");
     if (ndim == 2) nz = 1;
     if (nx < 2 || ny < 2 || (ndim == 3 && nz < 2) || nt < 1)
@@ -488,13 +520,13 @@ ftk_status ftk::plan_sizes(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t
     if (s != FTK_OK) return s;
     const long long nverts = (long long)nx * ny * nz * nt;
     out->nseg = (long long)nt * nz * out->B.nyb;
-    out->cap = initial_cap(prm, nverts);
-    out->scap = out->variant != VAR_TILE ? initial_scap(nverts) : 0;
+    out->cap = initial_cap(prm, nverts, compact);
+    out->scap = out->variant != VAR_TILE ? initial_scap(nverts, compact) : 0;
     return FTK_OK;
 }
 
 ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, const ftk_params *p,
-                            RunCounters *ctr, ftk_plan **plan) {
+                            RunCounters *ctr, ftk_plan **plan, bool compact) {
     if (plan) *plan = nullptr;
     if (!plan) return fail(FTK_ERR_ARG, "plan is NULL");
     if (ndim != 2 && ndim != 3) return fail(FTK_ERR_ARG, "ndim must be 2 or 3");
@@ -541,7 +573,7 @@ ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_
         delete pl;
         return fail(FTK_ERR_NOMEM, "device allocation failed");
     }
-    s = alloc_capacity(W, initial_cap(pl->p, pl->nverts));
+    s = alloc_capacity(W, initial_cap(pl->p, pl->nverts, compact));
     if (s == FTK_OK && pl->variant != VAR_TILE) {
         const long long nst = (W.nseg + SEG_TILE - 1) / SEG_TILE;
         if (cudaMalloc(&W.seg_scnt, W.nseg * sizeof(int)) != cudaSuccess ||
@@ -550,7 +582,7 @@ ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_
             cudaGetLastError();
             s = fail(FTK_ERR_NOMEM, "device allocation failed");
         } else {
-            s = alloc_survivors(W, initial_scap(pl->nverts));
+            s = alloc_survivors(W, initial_scap(pl->nverts, compact));
         }
     }
     if (s != FTK_OK) {
@@ -584,6 +616,13 @@ ftk_status ftk_plan_execute(ftk_plan *pl, const float *f, void *cuda_stream) {
     pl->last_f = f;
     pl->last_dev = src;
     pl->last_host = host;
+    if ((pl->p.flags & FTK_FLAG_AUTOTUNE) && !pl->tuned) {
+        // first execute of an autotuned plan: measure the candidate launch
+        // shapes on this field (the result is cached per shape)
+        st = ftk::plan_autotune(pl, src, s);
+        if (st != FTK_OK) return st;
+        pl->tuned = true;
+    }
     cudaEvent_t copied = nullptr;
     if (host) {
         // the host buffer may be reused as soon as this call returns: wait for

@@ -37,6 +37,7 @@ struct ftk_plan {
     long long traj_cap;        // punctures they hold
     long long traj_n;          // trajectories of the last execute (valid if traj_valid)
     bool traj_valid;
+    bool tuned;                // FTK_FLAG_AUTOTUNE: launch shape measured
     float stage_ms[5];
     int nstage;
 };
@@ -52,14 +53,14 @@ struct PlanSizes {
     long long nseg, cap, scap;
 };
 ftk_status plan_sizes(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, const ftk_params *p,
-                      PlanSizes *out);
+                      PlanSizes *out, bool compact = false);
 
 ftk_status fail(ftk_status s, const std::string &msg);
 ftk_status cuda_fail(cudaError_t e, const char *what);
 bool is_device_pointer(const void *p);
 // plan with its counters at ctr (nullptr: the plan allocates them)
 ftk_status plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, const ftk_params *p,
-                       RunCounters *ctr, ftk_plan **plan);
+                       RunCounters *ctr, ftk_plan **plan, bool compact = false);
 // the device field the kernels read (f, or the plan's copy of it queued on s)
 ftk_status plan_source(ftk_plan *pl, const float *f, bool host, cudaStream_t s, const float **src);
 // queue the pipeline on s, reading device field f (no host copies)

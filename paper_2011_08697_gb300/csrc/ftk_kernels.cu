@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <mutex>
 
@@ -57,11 +58,15 @@ template <> __device__ __forceinline__ const CellTables<3> &cells<3>() { return 
 
 constexpr int NT = 256;              // threads per CTA of every kernel here
 constexpr int UF_LIMIT = 1 << 22;    // bound on union-find retries / path steps
-// The bounds in force (device globals, so that a test can make a bounded loop
-// run out; the mbarrier waits of the detect kernels, which also drain copies
-// in flight, keep their own fixed bound)
-__device__ int g_uf_limit = UF_LIMIT;
-__device__ long long g_lookback_cycles = WAIT_CYCLES;
+// The bounds in force, set from the host so that a test can make a bounded
+// loop run out (the mbarrier waits of the detect kernels, which also drain
+// copies in flight, keep their own fixed bound): the look-back bound in
+// constant memory (read once per tile)
+__constant__ long long g_lookback_cycles = WAIT_CYCLES;
+// the union-find bound of the label pass, handed to each launch as a kernel
+// parameter (Workspace::uf_limit); the pass takes it only in the instance a
+// test selects, so that the normal instance keeps a compile-time bound
+static std::atomic<int> g_host_uf_limit{UF_LIMIT};
 
 // Exact SoS puncture test of one face; V[k] = gradient at the k-th vertex in
 // increasing global-id order.
@@ -980,8 +985,7 @@ __global__ void __launch_bounds__(NT) k_finalize(Field F, Blocking B, Workspace 
 // ----------------------------------------------------------------------------
 // Linking
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ int uf_find(int *parent, int x, unsigned *status) {
-    const int lim = g_uf_limit;
+__device__ __forceinline__ int uf_find(int *parent, int x, unsigned *status, int lim = UF_LIMIT) {
     for (int it = 0; it < lim; ++it) {
         const int p = *(volatile int *)&parent[x];
         if (p == x) return x;
@@ -993,11 +997,10 @@ __device__ __forceinline__ int uf_find(int *parent, int x, unsigned *status) {
     return x;
 }
 
-__device__ __forceinline__ void uf_unite(int *parent, int a, int b, unsigned *status) {
-    const int lim = g_uf_limit;
+__device__ __forceinline__ void uf_unite(int *parent, int a, int b, unsigned *status, int lim = UF_LIMIT) {
     for (int it = 0; it < lim; ++it) {
-        a = uf_find(parent, a, status);
-        b = uf_find(parent, b, status);
+        a = uf_find(parent, a, status, lim);
+        b = uf_find(parent, b, status, lim);
         if (a == b) return;
         if (a < b) { const int t = a; a = b; b = t; }
         // hook the larger root under the smaller: roots stay component minima
@@ -1258,7 +1261,7 @@ __global__ void __launch_bounds__(NT) k_link_survivors(Field F, Blocking B, Work
     }
 }
 
-template <int N>
+template <int N, bool LIM>
 __global__ void __launch_bounds__(NT) k_label(Field F, Workspace W, int check_cells) {
     // a block's records are built in shared memory and stored as one
     // contiguous run of 16-byte words (a record is 56 bytes; a run starts at
@@ -1274,7 +1277,9 @@ __global__ void __launch_bounds__(NT) k_label(Field F, Workspace W, int check_ce
     for (long long i0 = blockIdx.x * (long long)NT; i0 < P; i0 += (long long)gridDim.x * NT) {
         const long long i = i0 + threadIdx.x;
         if (i < P) {
-            const int r = uf_find(W.parent, (int)i, status);
+            // the run-time bound only in the instance a test selects (a
+            // compile-time bound keeps the loop of the normal instance lean)
+            const int r = uf_find(W.parent, (int)i, status, LIM ? W.uf_limit : UF_LIMIT);
             const long long fid = W.face[i];
             const long long lab = W.face[r];
             W.label[i] = lab;
@@ -1681,7 +1686,8 @@ __device__ __forceinline__ long long bsearch_ll(const long long *a, long long n,
     return (lo < n && a[lo] == key) ? lo : -1;
 }
 
-__global__ void __launch_bounds__(NT) k_stream_place(StreamMerge M) {
+__global__ void __launch_bounds__(NT) k_stream_place(const StreamMerge *__restrict__ Mp) {
+    const StreamMerge &M = *Mp;
     if (M.ctr->status & RUN_BAD) return;
     const long long P = M.ctr->punctures;
     const long long k = M.S->k, n_base = M.S->n;
@@ -1716,7 +1722,8 @@ __global__ void __launch_bounds__(NT) k_stream_place(StreamMerge M) {
     }
 }
 
-__global__ void __launch_bounds__(NT) k_stream_unite(StreamMerge M) {
+__global__ void __launch_bounds__(NT) k_stream_unite(const StreamMerge *__restrict__ Mp) {
+    const StreamMerge &M = *Mp;
     if (M.ctr->status & RUN_BAD) return;
     const long long P = M.ctr->punctures;
     const long long n_base = M.S->n;
@@ -1730,7 +1737,8 @@ __global__ void __launch_bounds__(NT) k_stream_unite(StreamMerge M) {
     }
 }
 
-__global__ void __launch_bounds__(NT) k_stream_minima(StreamMerge M) {
+__global__ void __launch_bounds__(NT) k_stream_minima(const StreamMerge *__restrict__ Mp) {
+    const StreamMerge &M = *Mp;
     if (M.ctr->status & RUN_BAD) return;
     const long long P = M.ctr->punctures;
     const long long n_base = M.S->n;
@@ -1757,7 +1765,8 @@ __device__ __forceinline__ void delta_flags(const StreamMerge &M, long long k, l
     }
 }
 
-__global__ void __launch_bounds__(NT) k_delta_count(StreamMerge M) {
+__global__ void __launch_bounds__(NT) k_delta_count(const StreamMerge *__restrict__ Mp) {
+    const StreamMerge &M = *Mp;
     __shared__ long long red[NT / 32 + 1];
     if (M.ctr->status & RUN_BAD) return;
     const long long P = M.ctr->punctures;
@@ -1781,7 +1790,8 @@ __global__ void __launch_bounds__(NT) k_delta_count(StreamMerge M) {
     }
 }
 
-__global__ void __launch_bounds__(NT) k_delta_scan(StreamMerge M) {
+__global__ void __launch_bounds__(NT) k_delta_scan(const StreamMerge *__restrict__ Mp) {
+    const StreamMerge &M = *Mp;
     __shared__ long long red[NT / 32 + 1];
     if (M.ctr->status & RUN_BAD) return;
     const long long P = M.ctr->punctures;
@@ -1802,7 +1812,8 @@ __global__ void __launch_bounds__(NT) k_delta_scan(StreamMerge M) {
     }
 }
 
-__global__ void __launch_bounds__(NT) k_delta_write(StreamMerge M) {
+__global__ void __launch_bounds__(NT) k_delta_write(const StreamMerge *__restrict__ Mp) {
+    const StreamMerge &M = *Mp;
     __shared__ long long red[NT / 32 + 1];
     if (M.ctr->status & RUN_BAD) return;
     const long long P = M.ctr->punctures;
@@ -1836,7 +1847,8 @@ __global__ void __launch_bounds__(NT) k_delta_write(StreamMerge M) {
 
 // after a merged push: the run's incremental detect state becomes the input
 // of the next push (a run that was not merged keeps the old state)
-__global__ void __launch_bounds__(NT) k_state_commit(StreamMerge M) {
+__global__ void __launch_bounds__(NT) k_state_commit(const StreamMerge *__restrict__ Mp) {
+    const StreamMerge &M = *Mp;
     if (M.ctr->status & RUN_BAD) return;
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < M.st_words; i += (long long)gridDim.x * NT)
         M.st_in[i] = M.st_out[i];
@@ -1844,7 +1856,8 @@ __global__ void __launch_bounds__(NT) k_state_commit(StreamMerge M) {
 
 // one thread: the report to the host and the advance of the scalars (after
 // every kernel of the push has read them)
-__global__ void k_stream_advance(StreamMerge M) {
+__global__ void k_stream_advance(const StreamMerge *__restrict__ Mp) {
+    const StreamMerge &M = *Mp;
     const unsigned run_status = M.ctr->status;
     const long long P = M.ctr->punctures;
     M.view->run_status = run_status;
@@ -1937,16 +1950,18 @@ __global__ void __launch_bounds__(NT) k_stream_final(long long n, const int *gsh
     if (threadIdx.x == 0) *count = run;
 }
 
-cudaError_t launch_stream_merge(const StreamMerge &M, cudaStream_t s) {
+cudaError_t launch_stream_merge(const StreamMerge *dM, const StreamMerge &M, long long cap, cudaStream_t s) {
+    // grid-stride kernels over at most cap punctures (the run's capacity)
     const int sg = sparse_grid();
-    k_stream_place<<<sg, NT, 0, s>>>(M);
-    k_stream_unite<<<sg, NT, 0, s>>>(M);
-    k_stream_minima<<<sg, NT, 0, s>>>(M);
-    k_delta_count<<<sg, NT, 0, s>>>(M);
-    k_delta_scan<<<1, NT, 0, s>>>(M);
-    k_delta_write<<<sg, NT, 0, s>>>(M);
-    k_stream_advance<<<1, 1, 0, s>>>(M);
-    if (M.st_words > 0) k_state_commit<<<sg, NT, 0, s>>>(M);
+    const int g = (int)std::max<long long>(1, std::min<long long>(sg, (cap + NT - 1) / NT));
+    k_stream_place<<<g, NT, 0, s>>>(dM);
+    k_stream_unite<<<g, NT, 0, s>>>(dM);
+    k_stream_minima<<<g, NT, 0, s>>>(dM);
+    k_delta_count<<<g, NT, 0, s>>>(dM);
+    k_delta_scan<<<1, NT, 0, s>>>(dM);
+    k_delta_write<<<g, NT, 0, s>>>(dM);
+    k_stream_advance<<<1, 1, 0, s>>>(dM);
+    if (M.st_words > 0) k_state_commit<<<sg, NT, 0, s>>>(dM);
     return cudaGetLastError();
 }
 
@@ -2047,7 +2062,10 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
     if (stream) k_link_survivors<N><<<gsize(resident_grid<k_link_survivors<N>>(), W.scap * (N + 1), NT), NT, 0, s>>>(F, B, W);
     else k_link<N><<<sg, NT, 0, s>>>(F, B, W);
     if (ev) cudaEventRecord(ev[4], s);
-    k_label<N><<<gsize(resident_grid<k_label<N>>(), W.cap, NT), NT, 0, s>>>(F, W, stream ? 1 : 0);
+    if (W.uf_limit < UF_LIMIT)
+        k_label<N, true><<<gsize(resident_grid<k_label<N, true>>(), W.cap, NT), NT, 0, s>>>(F, W, stream ? 1 : 0);
+    else
+        k_label<N, false><<<gsize(resident_grid<k_label<N, false>>(), W.cap, NT), NT, 0, s>>>(F, W, stream ? 1 : 0);
     if (ev) cudaEventRecord(ev[5], s);
     cudaError_t e3 = cudaGetLastError();
     if (e3 != cudaSuccess) g_launch_stage = "scan..label";
@@ -2060,7 +2078,9 @@ cudaError_t launch_pipeline(int ndim, int variant, const Field &F, const Blockin
     cudaError_t e = cudaMemsetAsync(W.ctr, 0, sizeof(RunCounters), s);
     if (e != cudaSuccess) return e;
     g_launch_stage = "launch";
-    return ndim == 2 ? launch_all<2>(variant, F, B, W, s, ev) : launch_all<3>(variant, F, B, W, s, ev);
+    Workspace Wl = W;
+    Wl.uf_limit = uf_limit();
+    return ndim == 2 ? launch_all<2>(variant, F, B, Wl, s, ev) : launch_all<3>(variant, F, B, Wl, s, ev);
 }
 
 }  // namespace ftk
@@ -2379,10 +2399,11 @@ namespace ftk {
 cudaError_t set_wait_limits(long long uf_steps, long long lookback_cycles) {
     const int u = uf_steps > 0 ? (int)std::min<long long>(uf_steps, UF_LIMIT) : UF_LIMIT;
     const long long c = lookback_cycles > 0 ? std::min<long long>(lookback_cycles, WAIT_CYCLES) : WAIT_CYCLES;
-    cudaError_t e = cudaMemcpyToSymbol(g_uf_limit, &u, sizeof(u));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_lookback_cycles, &c, sizeof(c));
-    return e;
+    g_host_uf_limit.store(u);
+    return cudaMemcpyToSymbol(g_lookback_cycles, &c, sizeof(c));
 }
+
+int uf_limit() { return g_host_uf_limit.load(); }
 
 }  // namespace ftk
 

@@ -105,6 +105,8 @@ struct Workspace {
     unsigned long long *tile;       // [scap / LB_TILE] look-back state of the survivor scan
     unsigned long long *seg_tile;   // [nseg / SEG_TILE] look-back state of the segment scan
     long long scap;
+    int uf_limit;                   // union-find bound of the label pass (set at launch; below the
+                                    // default only in tests)
 };
 
 constexpr int LB_TILE = 2048;       // survivors per tile of the survivor scan
@@ -224,7 +226,10 @@ struct StreamMerge {
 };
 constexpr int DELTA_BLOCK = 1024;     // punctures per block of the delta compaction
 
-cudaError_t launch_stream_merge(const StreamMerge &M, cudaStream_t s);
+// the merge kernels read their arguments from dM (device memory, a copy of
+// M), so that the stream's arrays can be reallocated without recapturing a
+// graph that holds them; cap bounds the run's punctures
+cudaError_t launch_stream_merge(const StreamMerge *dM, const StreamMerge &M, long long cap, cudaStream_t s);
 // copies `rows` rows of nx floats from the address in *src (device memory)
 // to dst with row pitch `pitch` (padding as launch_pad_rows)
 cudaError_t launch_stream_copy(const StreamSrc *src, float *dst, int nx, int pitch, long long rows, cudaStream_t s);
@@ -256,6 +261,8 @@ cudaError_t launch_traj_slice(const TrajBuffers &T, long long ntraj, double t0, 
 // bounds of the union-find loops and the look-back waits on the current
 // device (<= 0: the defaults)
 cudaError_t set_wait_limits(long long uf_steps, long long lookback_cycles);
+// the union-find bound in force (handed to every launch)
+int uf_limit();
 
 // filtering: kept sizes / flags per trajectory and their scans (noff[ntraj],
 // nidx[ntraj] = totals); compaction of the kept trajectories with type

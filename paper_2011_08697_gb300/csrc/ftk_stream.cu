@@ -90,15 +90,12 @@ struct ftk_stream {
     uint32_t *st_in = nullptr, *st_out = nullptr;
     long long st_words = 0;
     // one captured push (k >= 2) replayed for every later push
-    cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    uint64_t serial = 0;          // unique per stream opened in this process
-    uint64_t graph_version = 0;   // bumped whenever the captured push is dropped
+    // the merge kernels' arguments for pushes with plan1 / plan2, in device
+    // memory (reallocating the stream's arrays updates them, not the graph)
+    StreamMerge *dM = nullptr;    // [2]
+    bool merge_dirty = true;
 };
-
-namespace {
-std::atomic<uint64_t> g_stream_serial{1};
-}
 
 namespace {
 
@@ -128,10 +125,7 @@ ftk_status grow(T **ptr, long long cap, long long need, long long keep, cudaStre
 
 void drop_graph(ftk_stream *st) {
     if (st->exec) cudaGraphExecDestroy(st->exec);
-    if (st->graph) cudaGraphDestroy(st->graph);
-    if (st->exec || st->graph) ++st->graph_version;
     st->exec = nullptr;
-    st->graph = nullptr;
 }
 
 // reserves `add` more bytes of device memory for the stream: within the
@@ -183,7 +177,7 @@ ftk_status ensure_all(ftk_stream *st, long long cap) {
             return s;
         }
         st->acap = c0;
-        drop_graph(st);
+        st->merge_dirty = true;
     }
     if (cap > st->lcap) {
         const size_t add = (size_t)(grow_cap(cap) - st->lcap) * 8;
@@ -195,7 +189,7 @@ ftk_status ensure_all(ftk_stream *st, long long cap) {
             return s;
         }
         st->lcap = a;
-        drop_graph(st);
+        st->merge_dirty = true;
     }
     const long long nblk = 4 * (cap / DELTA_BLOCK + 1);
     if (nblk > st->bcap) {
@@ -207,7 +201,7 @@ ftk_status ensure_all(ftk_stream *st, long long cap) {
             return s;
         }
         st->bcap = a;
-        drop_graph(st);
+        st->merge_dirty = true;
     }
     if (cap > st->ocap) {
         // the buffer of the last push's parity keeps its ordinal faces
@@ -225,7 +219,7 @@ ftk_status ensure_all(ftk_stream *st, long long cap) {
             }
         }
         st->ocap = a;
-        drop_graph(st);
+        st->merge_dirty = true;
     }
     if (cap > st->dcap) {
         const long long nc = std::max<long long>(cap + cap / 2, 1 << 12);
@@ -238,7 +232,7 @@ ftk_status ensure_all(ftk_stream *st, long long cap) {
         st->h_delta = h;
         cudaHostGetDevicePointer((void **)&st->d_delta, h, 0);
         st->dcap = nc;
-        drop_graph(st);
+        st->merge_dirty = true;
     }
     return FTK_OK;
 }
@@ -267,6 +261,18 @@ StreamMerge merge_args(ftk_stream *st, ftk_plan *pl) {
     return M;
 }
 
+// refreshes the device copies of the merge arguments (before a push, on the
+// stream's CUDA stream, so that the copy precedes the push's kernels)
+ftk_status sync_merge(ftk_stream *st) {
+    if (!st->merge_dirty) return FTK_OK;
+    StreamMerge h[2] = {merge_args(st, st->plan1), merge_args(st, st->plan2)};
+    const cudaError_t e = cudaMemcpyAsync(st->dM, h, sizeof(h), cudaMemcpyHostToDevice, st->cs);
+    if (e != cudaSuccess) return cuda_fail(e, "merge arguments");
+    // the source is pageable: the call returns once h has been staged
+    st->merge_dirty = false;
+    return FTK_OK;
+}
+
 // one push's device work: bring in the slice (host_slice: a host pointer to
 // copy from; otherwise the device address in *dSrc), run the pipeline, merge
 ftk_status enqueue_push(ftk_stream *st, ftk_plan *pl, long long k, const float *host_slice) {
@@ -290,7 +296,9 @@ ftk_status enqueue_push(ftk_stream *st, ftk_plan *pl, long long k, const float *
     if (e != cudaSuccess) return cuda_fail(e, "slice copy");
     ftk_status s = plan_launch(pl, st->d2, st->cs);
     if (s != FTK_OK) return s;
-    if ((e = launch_stream_merge(merge_args(st, pl), st->cs)) != cudaSuccess) return cuda_fail(e, "stream merge launch");
+    if ((e = launch_stream_merge(st->dM + (pl == st->plan1 ? 0 : 1), merge_args(st, pl), pl->W.cap, st->cs)) !=
+        cudaSuccess)
+        return cuda_fail(e, "stream merge launch");
     return FTK_OK;
 }
 
@@ -311,95 +319,19 @@ void capture_push(ftk_stream *st) {
     if (cudaGraphInstantiate(&st->exec, g, 0) != cudaSuccess) {
         cudaGetLastError();
         st->exec = nullptr;
-        cudaGraphDestroy(g);
-        return;
     }
-    st->graph = g;   // kept: batched pushes nest it in a graph of many streams
-}
-
-// Graphs of several streams' steady-state pushes (their captured graphs as
-// children of one graph, so one launch queues them all), cached by the
-// streams' serials and graph versions; a stream's entries go when it closes.
-struct BatchGraph {
-    std::vector<uint64_t> key;   // serial, version of each stream in call order
-    cudaGraphExec_t exec = nullptr;
-    uint64_t last_use = 0;
-};
-std::mutex g_batch_mu;
-std::vector<BatchGraph> g_batches;
-uint64_t g_batch_clock = 0;
-constexpr size_t kMaxBatchGraphs = 8;
-
-void evict_batches(uint64_t serial) {
-    std::lock_guard<std::mutex> lock(g_batch_mu);
-    for (size_t i = 0; i < g_batches.size();) {
-        bool hit = false;
-        for (size_t k = 0; k < g_batches[i].key.size(); k += 2) hit |= g_batches[i].key[k] == serial;
-        if (hit) {
-            cudaGraphExecDestroy(g_batches[i].exec);
-            g_batches.erase(g_batches.begin() + (long)i);
-        } else {
-            ++i;
-        }
-    }
-}
-
-// the executable graph of these streams' captured pushes (nullptr if it
-// cannot be built)
-cudaGraphExec_t batch_exec(ftk_stream *const *v, int n) {
-    std::vector<uint64_t> key;
-    key.reserve(2 * (size_t)n);
-    for (int i = 0; i < n; ++i) {
-        key.push_back(v[i]->serial);
-        key.push_back(v[i]->graph_version);
-    }
-    std::lock_guard<std::mutex> lock(g_batch_mu);
-    for (auto &b : g_batches)
-        if (b.key == key) {
-            b.last_use = ++g_batch_clock;
-            return b.exec;
-        }
-    cudaGraph_t parent = nullptr;
-    if (cudaGraphCreate(&parent, 0) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    bool ok = true;
-    for (int i = 0; i < n && ok; ++i) {
-        cudaGraphNode_t node;
-        ok = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, v[i]->graph) == cudaSuccess;
-    }
-    cudaGraphExec_t exec = nullptr;
-    if (ok) ok = cudaGraphInstantiate(&exec, parent, 0) == cudaSuccess;
-    cudaGraphDestroy(parent);
-    if (!ok) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (g_batches.size() >= kMaxBatchGraphs) {
-        size_t lru = 0;
-        for (size_t i = 1; i < g_batches.size(); ++i)
-            if (g_batches[i].last_use < g_batches[lru].last_use) lru = i;
-        cudaGraphExecDestroy(g_batches[lru].exec);
-        g_batches.erase(g_batches.begin() + (long)lru);
-    }
-    BatchGraph b;
-    b.key = std::move(key);
-    b.exec = exec;
-    b.last_use = ++g_batch_clock;
-    g_batches.push_back(std::move(b));
-    return exec;
+    cudaGraphDestroy(g);
 }
 
 void release(ftk_stream *st) {
     if (!st) return;
     if (st->cs) cudaStreamSynchronize(st->cs);
-    if (st->serial) evict_batches(st->serial);
     drop_graph(st);
     if (st->plan1) ftk_plan_destroy(st->plan1);
     if (st->plan2) ftk_plan_destroy(st->plan2);
     cudaFree(st->d2);
     cudaFree(st->dS);
+    cudaFree(st->dM);
     if (st->hV) cudaFreeHost(st->hV);
     if (st->hSrc) cudaFreeHost(st->hSrc);
     if (st->h_delta) cudaFreeHost(st->h_delta);
@@ -442,7 +374,8 @@ ftk_status stream_footprint(int ndim, int64_t nx, int64_t ny, int64_t nz, const 
     if (ndim == 2) nz = 1;
     PlanSizes a, b;
     ftk_status s;
-    if ((s = plan_sizes(ndim, nx, ny, nz, 1, &prm, &a)) != FTK_OK || (s = plan_sizes(ndim, nx, ny, nz, 2, &prm, &b)) != FTK_OK)
+    if ((s = plan_sizes(ndim, nx, ny, nz, 1, &prm, &a, true)) != FTK_OK ||
+        (s = plan_sizes(ndim, nx, ny, nz, 2, &prm, &b, true)) != FTK_OK)
         return s;
     long long st_words = 0;
     if (ndim == 2 && a.variant != VAR_TILE && b.variant != VAR_TILE && a.B.nyb == b.B.nyb)
@@ -520,9 +453,8 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
     st->slice_verts = (long long)nx * ny * nz;
     st->T = ndim == 2 ? 12 : 60;
     st->tbit = ndim == 2 ? 4 : 8;
-    st->serial = g_stream_serial.fetch_add(1);
-    if ((s = plan_create(ndim, nx, ny, nz, 1, &st->p, nullptr, &st->plan1)) != FTK_OK ||
-        (s = plan_create(ndim, nx, ny, nz, 2, &st->p, nullptr, &st->plan2)) != FTK_OK) {
+    if ((s = plan_create(ndim, nx, ny, nz, 1, &st->p, nullptr, &st->plan1, true)) != FTK_OK ||
+        (s = plan_create(ndim, nx, ny, nz, 2, &st->p, nullptr, &st->plan2, true)) != FTK_OK) {
         release(st);
         give_back();
         return s;
@@ -553,6 +485,7 @@ ftk_status open_stream(ftk_server *srv, int ndim, int64_t nx, int64_t ny, int64_
     if (cudaStreamCreateWithFlags(&st->cs, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&st->d2, sizeof(float) * 2 * st->slice_elems) != cudaSuccess ||
         cudaMalloc(&st->dS, sizeof(StreamDev)) != cudaSuccess ||
+        cudaMalloc(&st->dM, 2 * sizeof(StreamMerge)) != cudaSuccess ||
         cudaMemset(st->dS, 0, sizeof(StreamDev)) != cudaSuccess ||
         cudaHostAlloc(&st->hV, sizeof(StreamView), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostAlloc(&st->hSrc, sizeof(StreamSrc), cudaHostAllocMapped) != cudaSuccess ||
@@ -679,6 +612,7 @@ ftk_status push_begin(ftk_stream *st, const float *slice) {
     }
     ftk_status s = ensure_all(st, pl->W.cap);
     if (s != FTK_OK) return stream_error(st, s, nullptr);
+    if ((s = sync_merge(st)) != FTK_OK) return stream_error(st, s, nullptr);
     cudaError_t e;
     if (on_dev && k >= 2 && !st->exec) capture_push(st);
     if (on_dev && k >= 2 && st->exec) {
@@ -691,13 +625,12 @@ ftk_status push_begin(ftk_stream *st, const float *slice) {
 }
 
 // second half: wait for the push, repair an overflowed run, hand out the delta
-ftk_status push_end(ftk_stream *st, ftk_result **delta, bool synced = false) {
+ftk_status push_end(ftk_stream *st, ftk_result **delta) {
     ftk_plan *pl = st->k == 0 ? st->plan1 : st->plan2;
     ftk_status s;
     cudaError_t e;
     // a blocking-sync event: the waiting thread sleeps instead of spinning
-    if (!synced && (e = cudaEventSynchronize(st->done)) != cudaSuccess)
-        return stream_error(st, FTK_ERR_CUDA, cudaGetErrorString(e));
+    if ((e = cudaEventSynchronize(st->done)) != cudaSuccess) return stream_error(st, FTK_ERR_CUDA, cudaGetErrorString(e));
     StreamView v = read_view(st);
     if (v.run_status & (ST_OVERFLOW | ST_SOVERFLOW | ST_WIDE)) {
         // not merged: repair the run (larger capacity or exact rounding),
@@ -706,7 +639,10 @@ ftk_status push_end(ftk_stream *st, ftk_result **delta, bool synced = false) {
         if ((s = ftk_plan_count(pl, &P)) != FTK_OK) return stream_error(st, s, nullptr);
         if ((s = ensure_all(st, pl->W.cap)) != FTK_OK) return stream_error(st, s, nullptr);
         drop_graph(st);   // the run's capacity changed
-        if ((e = launch_stream_merge(merge_args(st, pl), st->cs)) != cudaSuccess ||
+        st->merge_dirty = true;   // the run's buffers changed with its capacity
+        if ((s = sync_merge(st)) != FTK_OK) return stream_error(st, s, nullptr);
+        if ((e = launch_stream_merge(st->dM + (pl == st->plan1 ? 0 : 1), merge_args(st, pl), pl->W.cap, st->cs)) !=
+                cudaSuccess ||
             (e = cudaEventRecord(st->done, st->cs)) != cudaSuccess || (e = cudaEventSynchronize(st->done)) != cudaSuccess)
             return stream_error(st, FTK_ERR_CUDA, cudaGetErrorString(e));
         v = read_view(st);
@@ -751,42 +687,6 @@ ftk_status ftk_streams_push(int n, ftk_stream *const *streams, const float *cons
         for (int i = 0; i < n; ++i) {
             if (!streams[i] || !slices[i]) return fail(FTK_ERR_ARG, "NULL stream or slice");
             if (!seen.insert(streams[i]).second) return fail(FTK_ERR_ARG, "a stream appears twice in one call");
-        }
-    }
-    // steady state (every stream past its second push, device slices): the
-    // streams' captured pushes as one graph, one launch for the whole call
-    bool batched = n >= 2;
-    for (int i = 0; i < n && batched; ++i)
-        batched = !streams[i]->failed && streams[i]->k >= 2 && is_device_pointer(slices[i]);
-    if (batched) {
-        for (int i = 0; i < n && batched; ++i) {
-            ftk_stream *st = streams[i];
-            st->hSrc->ptr = slices[i];
-            if (ensure_all(st, st->plan2->W.cap) != FTK_OK) {
-                batched = false;   // the per-stream path below reports it
-                break;
-            }
-            if (!st->exec) capture_push(st);
-            batched = st->exec != nullptr;
-        }
-        std::atomic_thread_fence(std::memory_order_seq_cst);
-        cudaGraphExec_t ex = batched ? batch_exec(streams, n) : nullptr;
-        if (ex) {
-            cudaStream_t cs = streams[0]->cs;
-            cudaError_t e;
-            if ((e = cudaGraphLaunch(ex, cs)) != cudaSuccess || (e = cudaEventRecord(streams[0]->done, cs)) != cudaSuccess ||
-                (e = cudaEventSynchronize(streams[0]->done)) != cudaSuccess) {
-                for (int i = 0; i < n; ++i) stream_error(streams[i], FTK_ERR_CUDA, nullptr);
-                return cuda_fail(e, "batched push");
-            }
-            ftk_status first = FTK_OK;
-            std::string first_msg;
-            for (int i = 0; i < n; ++i) {
-                const ftk_status s = push_end(streams[i], &deltas[i], true);
-                if (s != FTK_OK && first == FTK_OK) { first = s; first_msg = ftk_last_error(); }
-            }
-            if (first != FTK_OK) return fail(first, first_msg);
-            return FTK_OK;
         }
     }
     // queue every push first (their device work overlaps on the streams' own
