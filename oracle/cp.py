@@ -416,6 +416,29 @@ def classify(D, Hs) -> int:
     return morse_index(S)
 
 
+def classify_vec(D, Js) -> int:
+    """Type of a zero of a 2D vector field (Sec. 4.1: sources, sinks and
+    saddles from the eigenvalues of the Jacobian): S = sign(D) * sum_k D_k J_k
+    is a positive multiple of the barycentrically interpolated Jacobian (not
+    symmetrised).  Returns the number of its eigenvalues with negative real
+    part: 0 = source, 1 = saddle, 2 = sink; -1 when a real part is zero
+    (det S = 0, or det S > 0 with tr S = 0: a centre)."""
+    tot = sum(D)
+    sgn = 1 if tot > 0 else (-1 if tot < 0 else 0)
+    S = [[0, 0], [0, 0]]
+    for dk, J in zip(D, Js):
+        for a in range(2):
+            for b in range(2):
+                S[a][b] += sgn * dk * int(J[a][b])
+    det = S[0][0] * S[1][1] - S[0][1] * S[1][0]
+    tr = S[0][0] + S[1][1]
+    if det < 0:
+        return 1
+    if det == 0 or tr == 0:
+        return -1
+    return 2 if tr < 0 else 0
+
+
 # ----------------------------------------------------------------------------
 # 7. Linking (Algorithm 1, second pass) with a plain union-find
 # ----------------------------------------------------------------------------
@@ -501,10 +524,13 @@ def link(grid: Grid, punct_ids, cell_filter=None):
 # ----------------------------------------------------------------------------
 # Whole pipeline
 # ----------------------------------------------------------------------------
-def describe_punctures(grid: Grid, G: np.ndarray, H, ids):
+def describe_punctures(grid: Grid, G: np.ndarray, H, ids, classifier=None):
     """Location (Eq. 1), ordinal flag and Morse type (Sec. 4.1) of each
     punctured face in ``ids``; G and H are the gradient / Hessian arrays of
-    the grid's vertices (H may be None: types are then left at -2)."""
+    the grid's vertices (H may be None: types are then left at -2).  For a
+    vector field, G holds the vectors, H their Jacobians and ``classifier``
+    is ``classify_vec``."""
+    classifier = classifier or classify
     n = grid.n
     Gflat = G.reshape(-1, n)
     Hflat = H.reshape(-1, n, n) if H is not None else None
@@ -529,7 +555,7 @@ def describe_punctures(grid: Grid, G: np.ndarray, H, ids):
             off[i, a if a < n else 3] = o
         ordinal[i] = 0 if (chain[-1] & tbit) else 1
         if Hflat is not None:
-            morse[i] = classify(D, [Hflat[g] for g in gids])
+            morse[i] = classifier(D, [Hflat[g] for g in gids])
     return base, off, morse, ordinal
 
 
@@ -554,6 +580,42 @@ def track(f: np.ndarray, shift: int = 20, t_lo: int = 0, t_hi: int | None = None
     ids = scan_faces(G, grid, t_lo, t_hi, threads=threads)
     H = hessian(G, n) if with_types else None
     base, off, morse, ordinal = describe_punctures(grid, G, H, ids)
+    P = len(ids)
+    label = np.full(P, -1, dtype=np.int64)
+    if with_links and P:
+        lab = link(grid, ids)
+        label = np.asarray([lab[int(x)] for x in ids], dtype=np.int64)
+    return dict(face_id=ids, base=base, off=off, morse=morse, ordinal=ordinal,
+                label=label, T=grid.T, grid=grid)
+
+
+def jacobian(V: np.ndarray, n: int) -> np.ndarray:
+    """J[..., a, b] = difference of component a along spatial axis b, with
+    the gradient's rule (central inside, one-sided and doubled at the ends)."""
+    base = V.ndim - 1
+    J = np.empty(V.shape + (n,), dtype=np.int64)
+    for a in range(n):
+        for b in range(n):
+            J[..., a, b] = _fd(V[..., a], base - 1 - b)
+    return J
+
+
+def track_vec(v: np.ndarray, shift: int = 20, with_links: bool = True):
+    """Exact tracking of the zeros of a 2D vector field v (nt, ny, nx, 2)
+    (paper Sec. 4.1: critical points of a vector field, v(x) = 0): each
+    component quantised as in ``quantise``; the puncture predicate, location
+    and linking as for a scalar field's gradient, applied to the vectors
+    themselves; types from the interpolated Jacobian (``classify_vec``).
+    Returns the same arrays as ``track``."""
+    v = np.asarray(v, dtype=np.float32)
+    if v.ndim != 4 or v.shape[-1] != 2:
+        raise ValueError("a 2D vector field has shape (nt, ny, nx, 2)")
+    nt, ny, nx, _ = v.shape
+    grid = Grid((nx, ny), nt)
+    V = quantise(v, shift)
+    ids = scan_faces(V, grid)
+    J = jacobian(V, 2)
+    base, off, morse, ordinal = describe_punctures(grid, V, J, ids, classifier=classify_vec)
     P = len(ids)
     label = np.full(P, -1, dtype=np.int64)
     if with_links and P:

@@ -39,6 +39,8 @@ __all__ = [
     "batch_fields",
     "stream_specs",
     "poisson_arrivals",
+    "linear_vector_field",
+    "vortex_street",
 ]
 
 
@@ -251,4 +253,64 @@ def blob_slices_torch(bs: BlobSet, k0: int, k1: int, device, chunk: int = 16):
         ey = torch.exp(-((ys[None, None, :] - ccy[:, :, None]) ** 2) * inv[None, :, None])   # (K, nb, ny)
         ey = ey * amp[None, :, None]
         out[a - k0: a - k0 + len(ks)] = torch.bmm(ey.transpose(1, 2), ex).to(torch.float32)
+    return out
+
+
+def linear_vector_field(n: int, nt: int, A, c0, d) -> np.ndarray:
+    """v(x, t) = A (x - c0 - d t) on the integer grid {0..n-1}^2, t = 0..nt-1,
+    as a (nt, n, n, 2) float32 array (component 0 = x).  With dyadic A, c0
+    and d every value is exact in float32; the only zero at time t is
+    c0 + d t when A is regular."""
+    A = np.asarray(A, dtype=np.float64)
+    c0 = np.asarray(c0, dtype=np.float64)
+    d = np.asarray(d, dtype=np.float64)
+    idx = np.arange(n, dtype=np.float64)
+    X, Y = np.meshgrid(idx, idx)            # [y][x]
+    out = np.empty((nt, n, n, 2), dtype=np.float32)
+    for k in range(nt):
+        cx, cy = c0 + d * k
+        dx, dy = X - cx, Y - cy
+        out[k, :, :, 0] = A[0, 0] * dx + A[0, 1] * dy
+        out[k, :, :, 1] = A[1, 0] * dx + A[1, 1] * dy
+    return out
+
+
+def vortex_street(nx: int, ny: int, nt: int, nvort: int = 8, nsrc: int = 6, seed: int = 0,
+                  flow: float = 0.3, sigma=(3.0, 6.0), drift: float = 0.5) -> np.ndarray:
+    """A 2D vector field shaped like the wake behind a cylinder (a stand-in
+    for the flow-past-cylinder data, which is not available): a uniform flow
+    along x plus a double row of Gaussian vortices of alternating sign,
+    advected downstream by `drift` cells per step, plus a few Gaussian
+    sources and sinks (gradients of Gaussian bumps) so that every kind of
+    zero occurs.  (nt, ny, nx, 2) float32, component 0 = x, values in FP64
+    cast once."""
+    rng = np.random.default_rng(seed)
+    xs = np.arange(nx, dtype=np.float64)[None, :]
+    ys = np.arange(ny, dtype=np.float64)[:, None]
+    x0 = rng.uniform(0.0, nx, size=nvort)
+    y0 = ny / 2.0 + np.where(np.arange(nvort) % 2 == 0, 1.0, -1.0) * rng.uniform(ny / 8.0, ny / 4.0, size=nvort)
+    gam = np.where(np.arange(nvort) % 2 == 0, 1.0, -1.0) * rng.uniform(0.5, 1.0, size=nvort)
+    sv = rng.uniform(sigma[0], sigma[1], size=nvort)
+    sx = rng.uniform(0.0, nx, size=nsrc)
+    sy = rng.uniform(0.0, ny, size=nsrc)
+    sa = np.where(rng.integers(0, 2, size=nsrc) == 0, -1.0, 1.0) * rng.uniform(0.5, 1.0, size=nsrc)
+    ss = rng.uniform(sigma[0], sigma[1], size=nsrc)
+    out = np.empty((nt, ny, nx, 2), dtype=np.float32)
+    for k in range(nt):
+        u = np.full((ny, nx), flow)
+        w = np.zeros((ny, nx))
+        for i in range(nvort):
+            dx = xs - (x0[i] + drift * k)
+            dy = ys - y0[i]
+            g = np.exp(-(dx * dx + dy * dy) / (2.0 * sv[i] ** 2)) / sv[i]
+            u += -gam[i] * dy * g / sv[i]
+            w += gam[i] * dx * g / sv[i]
+        for j in range(nsrc):
+            dx = xs - sx[j]
+            dy = ys - sy[j]
+            g = np.exp(-(dx * dx + dy * dy) / (2.0 * ss[j] ** 2))
+            u += -sa[j] * dx * g / ss[j]
+            w += -sa[j] * dy * g / ss[j]
+        out[k, :, :, 0] = u
+        out[k, :, :, 1] = w
     return out
