@@ -140,6 +140,29 @@ ftk_status ftk_track_cp2d(const float *f, int64_t nx, int64_t ny, int64_t nt,
 ftk_status ftk_track_cp3d(const float *f, int64_t nx, int64_t ny, int64_t nz, int64_t nt,
                           const ftk_params *p, ftk_result **out, void *cuda_stream);
 
+/* ---------------------------------------------------------------------
+ * Zeros of a time-varying 2D vector field (paper Sec. 4.1: critical points
+ * of a vector field are the points where v = 0; sources, sinks and saddles
+ * are told apart by the eigenvalues of the Jacobian).  v: device or host
+ * pointer to nt slices of ny*nx vertices with the two components
+ * interleaved, v[t][y][x][c] (c = 0: x, c = 1: y).  Each component is
+ * quantised like a scalar sample (F = rint(v * 2^quant_shift)) and takes
+ * the place of the gradient; the mesh, the SoS predicate, the location and
+ * the linking are those of ftk_track_cp2d.  morse_index holds the number
+ * of Jacobian eigenvalues with negative real part (0 source, 1 saddle,
+ * 2 sink), taken exactly from the integer central-difference Jacobian of v
+ * at the face's vertices, weighted by the Cramer numerators; -1 where the
+ * weighted Jacobian has determinant zero, or trace zero with a positive
+ * determinant (a centre: no real-part sign).  Records sorted by face_id.
+ * ftk_plan_create_vec2d makes a plan for such fields: execute, count,
+ * download, trajectories and slices behave as for a scalar plan, with v in
+ * place of f.  Errors as ftk_track_cp2d (FTK_ERR_RANGE when a component
+ * is non-finite or beyond 2^28 after scaling).
+ * ------------------------------------------------------------------- */
+ftk_status ftk_track_vec2d(const float *v, int64_t nx, int64_t ny, int64_t nt,
+                           const ftk_params *p, ftk_result **out, void *cuda_stream);
+ftk_status ftk_plan_create_vec2d(int64_t nx, int64_t ny, int64_t nt, const ftk_params *p, ftk_plan **plan);
+
 /* Result access.  ftk_result_data() entries are sorted by face_id. */
 size_t        ftk_result_count(const ftk_result *r);
 const ftk_cp *ftk_result_data(const ftk_result *r);

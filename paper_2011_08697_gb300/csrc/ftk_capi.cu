@@ -165,7 +165,7 @@ ftk_status choose_blocking(int ndim, const Field &F, Blocking &B, int &variant) 
     const int sms = sm_count();
     // the streaming kernels read rows padded to a multiple of 4 floats
     // (F.pitch, chosen by stream_pitch)
-    if (ndim == 2 && F.pitch % 4 == 0 && F.pitch <= STREAM2_MAX_NX) {
+    if (ndim == 2 && F.comps != 2 && F.pitch % 4 == 0 && F.pitch <= STREAM2_MAX_NX) {
         variant = VAR_STREAM2;
         B.ry = STREAM2_ROWS; B.rz = 1;
         B.nyb = (F.ny + B.ry - 1) / B.ry;
@@ -313,9 +313,10 @@ ftk_status make_result(ftk_plan *pl, ftk_result **out) {
 // Autotuner: measured time chunking per (shape, variant, SM count)
 // ---------------------------------------------------------------------------
 struct TuneKey {
-    int ndim, nx, ny, nz, nt, variant, sms;
+    int ndim, comps, nx, ny, nz, nt, variant, sms;
     bool operator<(const TuneKey &o) const {
-        return std::tie(ndim, nx, ny, nz, nt, variant, sms) < std::tie(o.ndim, o.nx, o.ny, o.nz, o.nt, o.variant, o.sms);
+        return std::tie(ndim, comps, nx, ny, nz, nt, variant, sms) <
+               std::tie(o.ndim, o.comps, o.nx, o.ny, o.nz, o.nt, o.variant, o.sms);
     }
 };
 std::mutex g_tune_mu;
@@ -327,7 +328,7 @@ struct Tuned {
 std::map<TuneKey, Tuned> g_tuned;
 
 TuneKey tune_key(const ftk_plan *pl) {
-    return TuneKey{pl->ndim, pl->F.nx, pl->F.ny, pl->F.nz, pl->F.nt, pl->variant, sm_count()};
+    return TuneKey{pl->ndim, pl->F.comps, pl->F.nx, pl->F.ny, pl->F.nz, pl->F.nt, pl->variant, sm_count()};
 }
 
 void set_chunks(ftk_plan *pl, int ntc) {
@@ -364,7 +365,7 @@ ftk_status ftk::plan_source(ftk_plan *pl, const float *f, bool host, cudaStream_
     const bool misaligned = pl->variant != VAR_TILE && ((uintptr_t)f & 15u) != 0;
     *src = f;
     if (!host && !padded && !misaligned) return FTK_OK;
-    const size_t bytes = (size_t)rows * F.pitch * sizeof(float);
+    const size_t bytes = (size_t)rows * F.pitch * sizeof(float) * (F.comps == 2 ? 2 : 1);
     if (!pl->d_input && cudaMalloc(&pl->d_input, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(FTK_ERR_NOMEM, "device input buffer allocation failed");
@@ -526,7 +527,7 @@ ftk_status ftk::plan_sizes(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t
 }
 
 ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, const ftk_params *p,
-                            RunCounters *ctr, ftk_plan **plan, bool compact) {
+                            RunCounters *ctr, ftk_plan **plan, bool compact, int comps) {
     if (plan) *plan = nullptr;
     if (!plan) return fail(FTK_ERR_ARG, "plan is NULL");
     if (ndim != 2 && ndim != 3) return fail(FTK_ERR_ARG, "ndim must be 2 or 3");
@@ -549,7 +550,8 @@ ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_
     pl->ndim = ndim;
     cudaGetDevice(&pl->device);
     pl->F.nx = (int)nx; pl->F.ny = (int)ny; pl->F.nz = (int)nz; pl->F.nt = (int)nt;
-    pl->F.pitch = stream_pitch(ndim, (int)nx);
+    pl->F.comps = comps == 2 ? 2 : 1;
+    pl->F.pitch = pl->F.comps == 2 ? (int)nx : stream_pitch(ndim, (int)nx);
     pl->F.scale = (float)std::ldexp(1.0, pl->p.quant_shift);
     field_divisors(pl->F);
     pl->nverts = (long long)nx * ny * nz * nt;
@@ -723,11 +725,11 @@ ftk_status ftk_plan_destroy(ftk_plan *pl) {
 }
 
 static ftk_status track_once(int ndim, const float *f, int64_t nx, int64_t ny, int64_t nz, int64_t nt,
-                             const ftk_params *p, ftk_result **out, void *stream) {
+                             const ftk_params *p, ftk_result **out, void *stream, int comps = 1) {
     if (out) *out = nullptr;
     if (!f || !out) return fail(FTK_ERR_ARG, "field and out must be non-NULL");
     ftk_plan *pl = nullptr;
-    ftk_status s = ftk_plan_create(ndim, nx, ny, nz, nt, p, &pl);
+    ftk_status s = plan_create(ndim, nx, ny, nz, nt, p, nullptr, &pl, false, comps);
     if (s != FTK_OK) return s;
     s = ftk_plan_execute(pl, f, stream);
     if (s == FTK_OK) s = ftk_plan_download(pl, out);
@@ -745,6 +747,15 @@ ftk_status ftk_track_cp2d(const float *f, int64_t nx, int64_t ny, int64_t nt, co
 ftk_status ftk_track_cp3d(const float *f, int64_t nx, int64_t ny, int64_t nz, int64_t nt,
                           const ftk_params *p, ftk_result **out, void *stream) {
     return track_once(3, f, nx, ny, nz, nt, p, out, stream);
+}
+
+ftk_status ftk_track_vec2d(const float *v, int64_t nx, int64_t ny, int64_t nt, const ftk_params *p,
+                           ftk_result **out, void *stream) {
+    return track_once(2, v, nx, ny, 1, nt, p, out, stream, 2);
+}
+
+ftk_status ftk_plan_create_vec2d(int64_t nx, int64_t ny, int64_t nt, const ftk_params *p, ftk_plan **plan) {
+    return plan_create(2, nx, ny, 1, nt, p, nullptr, plan, false, 2);
 }
 
 size_t ftk_result_count(const ftk_result *r) { return r ? r->count : 0; }

@@ -60,7 +60,7 @@ ftk_status cuda_fail(cudaError_t e, const char *what);
 bool is_device_pointer(const void *p);
 // plan with its counters at ctr (nullptr: the plan allocates them)
 ftk_status plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, const ftk_params *p,
-                       RunCounters *ctr, ftk_plan **plan, bool compact = false);
+                       RunCounters *ctr, ftk_plan **plan, bool compact = false, int comps = 1);
 // the device field the kernels read (f, or the plan's copy of it queued on s)
 ftk_status plan_source(ftk_plan *pl, const float *f, bool host, cudaStream_t s, const float **src);
 // queue the pipeline on s, reading device field f (no host copies)

@@ -193,6 +193,7 @@ struct TileGeom {
     int WY, WZ;     // word rows / planes
     int tile;       // ints per F tile
     int wtile;      // bytes per word tile
+    int vec;        // 1: the tile holds a 2D vector per vertex (the vectors are the "gradients")
 };
 
 __device__ __forceinline__ int quantise(float f, float scale, unsigned *status) {
@@ -208,6 +209,13 @@ __device__ __forceinline__ int quantise(float f, float scale, unsigned *status) 
 template <int N>
 __device__ __forceinline__ void grad_tile(const int32_t *T, const TileGeom &g, int x, int y, int z,
                                           int ty, int tz, int32_t (&G)[N]) {
+    if (N == 2 && g.vec) {
+        // a vector field: the quantised vector itself takes the gradient's place
+        const int32_t *p = T + ((tz * g.PY + ty) * g.nx + x) * 2;
+        G[0] = p[0];
+        G[1] = p[1];
+        return;
+    }
     const int32_t *row = T + (tz * g.PY + ty) * g.nx;
     G[0] = x == 0 ? 2 * (row[1] - row[0])
          : x == g.nx - 1 ? 2 * (row[x] - row[x - 1])
@@ -237,7 +245,12 @@ __device__ void load_tile(const Field &F, const TileGeom &g, int s, int32_t *T, 
         const int z = N == 3 ? g.z0 - 1 + tz : 0;
         if (y < 0 || y >= g.ny || z < 0 || z >= g.nz) continue;
         const long long idx = (((long long)s * g.nz + z) * g.ny + y) * F.pitch + x;
-        T[i] = quantise(__ldg(F.f + idx), F.scale, status);
+        if (N == 2 && g.vec) {
+            T[2 * i] = quantise(__ldg(F.f + 2 * idx), F.scale, status);
+            T[2 * i + 1] = quantise(__ldg(F.f + 2 * idx + 1), F.scale, status);
+        } else {
+            T[i] = quantise(__ldg(F.f + idx), F.scale, status);
+        }
     }
 }
 
@@ -289,12 +302,12 @@ struct DetectLayout {
 };
 
 template <int N>
-__host__ __device__ inline DetectLayout detect_layout(int nx, int ry, int rz) {
+__host__ __device__ inline DetectLayout detect_layout(int nx, int ry, int rz, int comps = 1) {
     DetectLayout L;
     const int PY = ry + 3, PZ = N == 3 ? rz + 3 : 1;
     const int WY = ry + 1, WZ = N == 3 ? rz + 1 : 1;
     const int RZ = N == 3 ? rz : 1;
-    L.tile = PZ * PY * nx;
+    L.tile = (comps == 2 ? 2 : 1) * PZ * PY * nx;
     L.wtile = WZ * WY * nx;
     L.plane_bits = ry * nx;
     L.plane_words = (L.plane_bits + 31) / 32;
@@ -313,7 +326,7 @@ __global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W)
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int T = MeshDims<N>::T;
     const int rz = N == 3 ? B.rz : 1;
-    const DetectLayout L = detect_layout<N>(F.nx, B.ry, B.rz);
+    const DetectLayout L = detect_layout<N>(F.nx, B.ry, B.rz, F.comps);
     int32_t *Ft = reinterpret_cast<int32_t *>(smem);
     uint8_t *Wt = smem + L.off_words;
     uint32_t *bm = reinterpret_cast<uint32_t *>(smem + L.off_bm);
@@ -335,6 +348,7 @@ __global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W)
     g.PY = B.ry + 3; g.PZ = N == 3 ? B.rz + 3 : 1;
     g.WY = B.ry + 1; g.WZ = N == 3 ? B.rz + 1 : 1;
     g.tile = L.tile; g.wtile = L.wtile;
+    g.vec = F.comps == 2 ? 1 : 0;
 
     const int t_begin = tci * B.tc;
     const int t_end = min(F.nt, t_begin + B.tc);
@@ -590,6 +604,7 @@ __device__ __forceinline__ int qat(const Field &F, long long i) {
 // grid, m_a (f[hi_a] - f[lo_a]) where m_a = 2 at an end, else 1.  a must be a
 // compile-time constant after unrolling (p.c[a]).
 __device__ __forceinline__ int grad_at(const Field &F, const Pt &p, long long ip, int a) {
+    if (F.comps == 2) return qat(F, 2 * ip + a);   // a vector field: component a itself
     const int n = ext_of(F, a);
     const long long st = vstride(F, a);
     const long long lo = p.c[a] > 0 ? ip - st : ip;
@@ -753,8 +768,84 @@ constexpr int8_t MORSE_PENDING = -2;   // 3D: left to the exact classification
 // location and Morse index of one puncture.  In 3D with FILTER_ONLY the
 // index comes from the floating-point filter, or MORSE_PENDING when the
 // filter cannot certify it (the exact evaluation then runs separately).
+// Jacobian of a 2D vector field at p (element offset ip): J_ab = difference
+// of component a along axis b with the gradient's rule (central inside,
+// one-sided and doubled at either end)
+__device__ __forceinline__ void jac_vec2(const Field &F, const Pt &p, long long ip, long long (&J)[2][2]) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int n = ext_of(F, b);
+        const long long st = vstride(F, b);
+        const long long lo = p.c[b] > 0 ? ip - st : ip;
+        const long long hi = p.c[b] + 1 < n ? ip + st : ip;
+        const int m = (p.c[b] == 0 || p.c[b] == n - 1) ? 2 : 1;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) J[a][b] = (long long)m * (qat(F, 2 * hi + a) - qat(F, 2 * lo + a));
+    }
+}
+
+// Location and type of a zero of a 2D vector field (paper Sec. 4.1: sources,
+// sinks and saddles from the Jacobian's eigenvalues).  S = sign(D) sum_k D_k
+// J_k, a positive multiple of the interpolated Jacobian (not symmetrised):
+// type = number of eigenvalues with negative real part (0 source, 1 saddle,
+// 2 sink), -1 when one is zero (det S = 0, or det S > 0 and tr S = 0).
+// |V| <= 2^28: D_k < 2^58, |J| < 2^31, entries of S < 2^91 in int128, det S
+// compared exactly by cmp_prod128.
+__device__ void locate_classify_vec2(const Field &F, long long fid, float4 &off, int8_t &morse) {
+    int tt;
+    const Pt base = decode_face<2>(F, fid, tt);
+    const uint8_t *ch = mesh<2>().face[tt];
+    int32_t V[3][2];
+    long long J[3][2][2];
+    const long long ib = vindex(F, base);
+#pragma unroll
+    for (int k = 0; k <= 2; ++k) {
+        const Pt vk = k == 0 ? base : add_mask<2>(base, ch[k - 1]);
+        const long long ik = k == 0 ? ib : ib + mask_offset<2>(F, ch[k - 1]);
+        V[k][0] = grad_at(F, vk, ik, 0);
+        V[k][1] = grad_at(F, vk, ik, 1);
+        jac_vec2(F, vk, ik, J[k]);
+    }
+    long long D[3], Dsum = 0;
+#pragma unroll
+    for (int k = 0; k <= 2; ++k) {
+        const int j0 = k == 0 ? 1 : 0, j1 = k == 2 ? 1 : 2;
+        const long long d = (long long)V[j0][0] * V[j1][1] - (long long)V[j0][1] * V[j1][0];
+        D[k] = (k & 1) ? -d : d;
+        Dsum += D[k];
+    }
+    float mu[3];
+#pragma unroll
+    for (int k = 0; k <= 2; ++k) mu[k] = Dsum == 0 ? 1.0f / 3 : (float)D[k] / (float)Dsum;
+    float o[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k = 1; k <= 2; ++k)
+#pragma unroll
+        for (int a = 0; a <= 2; ++a)
+            if ((ch[k - 1] >> a) & 1) o[a] += mu[k];
+    off = make_float4(o[0], o[1], 0.0f, o[2]);
+    __int128 S[2][2] = {{0, 0}, {0, 0}};
+#pragma unroll
+    for (int k = 0; k <= 2; ++k) {
+        const __int128 w = Dsum < 0 ? -(__int128)D[k] : (__int128)D[k];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) S[a][b] += w * (__int128)J[k][a][b];
+    }
+    const int d = cmp_prod128(S[0][0], S[1][1], S[0][1], S[1][0]);   // sign of det S
+    const __int128 tr = S[0][0] + S[1][1];
+    morse = (int8_t)(d < 0 ? 1 : d == 0 || tr == 0 ? -1 : tr < 0 ? 2 : 0);
+}
+
 template <int N, bool FILTER_ONLY = false>
 __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8_t &morse) {
+    if constexpr (N == 2) {
+        if (F.comps == 2) {
+            locate_classify_vec2(F, fid, off, morse);
+            return;
+        }
+    }
     constexpr int BW = N == 2 ? 8 : 16;
     int tt;
     const Pt base = decode_face<N>(F, fid, tt);
@@ -1619,7 +1710,7 @@ cudaError_t raise_smem_cap(const void *kernel, size_t smem, bool capturing) {
 }
 
 size_t detect_smem_bytes(int ndim, const Field &F, const Blocking &B) {
-    const DetectLayout L = ndim == 2 ? detect_layout<2>(F.nx, B.ry, B.rz) : detect_layout<3>(F.nx, B.ry, B.rz);
+    const DetectLayout L = ndim == 2 ? detect_layout<2>(F.nx, B.ry, B.rz, F.comps) : detect_layout<3>(F.nx, B.ry, B.rz);
     return (size_t)L.total;
 }
 

@@ -71,6 +71,7 @@ EXPORTS = [
     "ftk_plan_trajectories", "ftk_traj_count", "ftk_traj_offsets", "ftk_traj_points", "ftk_traj_closed",
     "ftk_traj_free", "ftk_plan_slice", "ftk_slice_count", "ftk_slice_data", "ftk_slice_free",
     "ftk_debug_set_wait_limits", "ftk_plan_trajectories_filtered",
+    "ftk_track_vec2d", "ftk_plan_create_vec2d",
 ]
 
 
@@ -104,6 +105,8 @@ def lib():
         "ftk_result_data": (vp, [vp]),
         "ftk_result_free": (None, [vp]),
         "ftk_plan_create": (i32, [i32, i64, i64, i64, i64, ctypes.POINTER(ftk_params), pp]),
+        "ftk_track_vec2d": (i32, [vp, i64, i64, i64, ctypes.POINTER(ftk_params), pp, vp]),
+        "ftk_plan_create_vec2d": (i32, [i64, i64, i64, ctypes.POINTER(ftk_params), pp]),
         "ftk_plan_execute": (i32, [vp, vp, vp]),
         "ftk_plan_count": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ftk_plan_download": (i32, [vp, pp]),
@@ -242,12 +245,40 @@ def ftk_track_cp3d(f, params: ftk_params | None = None, stream=None) -> np.ndarr
     return _take_result(out)
 
 
+def ftk_track_vec2d(v, params: ftk_params | None = None, stream=None) -> np.ndarray:
+    """Zeros of a 2D vector field v of shape (nt, ny, nx, 2) (components
+    interleaved per vertex); morse_index = eigenvalues of the Jacobian with
+    negative real part (0 source, 1 saddle, 2 sink, -1 degenerate)."""
+    ptr, keep, shape = _field_ptr(v)
+    if len(shape) != 4 or shape[3] != 2:
+        raise ValueError("2D vector field must have shape (nt, ny, nx, 2)")
+    nt, ny, nx, _ = shape
+    out = ctypes.c_void_p()
+    p = params if params is not None else make_params()
+    _check(lib().ftk_track_vec2d(ptr, nx, ny, nt, ctypes.byref(p), ctypes.byref(out), _stream_ptr(stream)))
+    del keep
+    return _take_result(out)
+
+
 class Plan:
     """Device workspace for repeated tracking of fields of one shape
-    (``ftk_plan_*``)."""
+    (``ftk_plan_*``); with ``vec2d`` a plan for 2D vector fields of shape
+    (nt, ny, nx, 2) (``ftk_plan_create_vec2d``)."""
 
-    def __init__(self, shape, params: ftk_params | None = None):
+    def __init__(self, shape, params: ftk_params | None = None, vec2d: bool = False):
         shape = tuple(int(s) for s in shape)
+        if vec2d:
+            if len(shape) != 4 or shape[3] != 2:
+                raise ValueError("vector plan shape must be (nt, ny, nx, 2)")
+            nt, ny, nx, _ = shape
+            self.shape = shape
+            self.ndim = 2
+            self._p = params if params is not None else make_params()
+            h = ctypes.c_void_p()
+            _check(lib().ftk_plan_create_vec2d(nx, ny, nt, ctypes.byref(self._p), ctypes.byref(h)))
+            self._h = h
+            self._keep = None
+            return
         if len(shape) == 3:
             nt, ny, nx = shape
             nz, ndim = 1, 2
@@ -370,6 +401,10 @@ class Plan:
 # C-ABI names for the plan calls
 def ftk_plan_create(shape, params=None) -> Plan:
     return Plan(shape, params)
+
+
+def ftk_plan_create_vec2d(shape, params=None) -> Plan:
+    return Plan(shape, params, vec2d=True)
 
 
 def ftk_plan_execute(plan: Plan, f, stream=None):
