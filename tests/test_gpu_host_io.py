@@ -82,7 +82,9 @@ def test_stream_growth_is_charged_to_the_budget(F):
             pushed += 1
             assert tight.used() <= fp
     assert e.value.status == 6, e.value
-    assert pushed >= 2
+    # the footprint charged at open covers the first push; the union-find
+    # slots of the punctures kept from it make the next one grow
+    assert pushed >= 1
     assert tight.used() <= fp
     s.close(False)
     assert tight.used() == 0
