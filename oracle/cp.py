@@ -44,6 +44,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(HERE, "libftk_oracle.so")
 _SRC = os.path.join(HERE, "ftk_oracle.c")
+_SRCS = [_SRC, os.path.join(HERE, "iso_oracle.c")]
 
 RANGE_LIMIT = 1 << 28   # |F| must not exceed 2^28, so |G|, |H| <= 2^30 / 2^31
 
@@ -59,11 +60,12 @@ _lib = None
 
 
 def build_clib(force: bool = False) -> str:
-    """Compile ftk_oracle.c into libftk_oracle.so next to it (gcc, -O2, with
-    OpenMP when the compiler has it; the scan then runs on several threads)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    """Compile ftk_oracle.c and iso_oracle.c into libftk_oracle.so next to
+    them (gcc, -O2, with OpenMP when the compiler has it; the scan then runs
+    on several threads)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(x) for x in _SRCS):
         tmp = _SO + f".{os.getpid()}.tmp"
-        base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp]
+        base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", *_SRCS, "-o", tmp]
         if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], stdout=subprocess.DEVNULL,
                           stderr=subprocess.DEVNULL).returncode != 0:
             subprocess.check_call(base)
@@ -96,6 +98,12 @@ def clib():
         lib.oracle_test_faces.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, i32p,
                                           i64p, ctypes.c_int64, i8p]
         lib.oracle_test_faces.restype = None
+        f64p = ctypes.POINTER(ctypes.c_double)
+        lib.oracle_iso_edges.argtypes = [ctypes.c_int, i64p, f64p, ctypes.c_double, i64p, ctypes.c_int64]
+        lib.oracle_iso_edges.restype = ctypes.c_int64
+        lib.oracle_iso_link.argtypes = [ctypes.c_int, i64p, f64p, ctypes.c_double, i64p, ctypes.c_int64,
+                                        i64p, i64p]
+        lib.oracle_iso_link.restype = ctypes.c_int
         _lib = lib
     return _lib
 
