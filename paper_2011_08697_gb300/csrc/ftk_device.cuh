@@ -359,8 +359,43 @@ __host__ __device__ __forceinline__ int sos_zero_sign(const int32_t (&M)[3][3]) 
     return -1;
 }
 
+// true iff every entry lies in [-2^20, 2^20): then a 3x3 determinant is
+// exact in int64 (2x2 minors below 2^41, each entry-times-minor product at
+// most 2^61, their sum below 3 * 2^61 < 2^63)
+template <int R, int C>
+__host__ __device__ __forceinline__ bool entries_fit20(const int32_t (&V)[R][C]) {
+    unsigned acc = 0;
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < C; ++j) acc |= (unsigned)(V[i][j] + (1 << 20));
+    return acc < (1u << 21);
+}
+
+// sign of det M for entries in [-2^20, 2^20), the expansion of det_exact in int64
+__host__ __device__ __forceinline__ int det3_sign64(const int32_t (&M)[3][3]) {
+    const int64_t m0 = (int64_t)M[1][1] * M[2][2] - (int64_t)M[1][2] * M[2][1];
+    const int64_t m1 = (int64_t)M[0][1] * M[2][2] - (int64_t)M[0][2] * M[2][1];
+    const int64_t m2 = (int64_t)M[0][1] * M[1][2] - (int64_t)M[0][2] * M[1][1];
+    const int64_t d = (int64_t)M[0][0] * m0 - (int64_t)M[1][0] * m1 + (int64_t)M[2][0] * m2;
+    return (d > 0) - (d < 0);
+}
+
+// SoS sign of a 3x3 determinant whose entries are known to fit (or not) the
+// int64 range of det3_sign64
+__host__ __device__ __forceinline__ int sos_det_sign3(const int32_t (&M)[3][3], bool fit20) {
+    if (fit20) {
+        const int s = det3_sign64(M);
+        return s != 0 ? s : sos_zero_sign(M);
+    }
+    const __int128 d = det_exact(M);
+    if (d != 0) return d > 0 ? 1 : -1;
+    return sos_zero_sign(M);
+}
+
 template <int N>
 __host__ __device__ __forceinline__ int sos_det_sign(const int32_t (&M)[N][N]) {
+    if constexpr (N == 3) return sos_det_sign3(M, entries_fit20(M));
     const __int128 d = det_exact(M);
     if (d != 0) return d > 0 ? 1 : -1;
     return sos_zero_sign(M);

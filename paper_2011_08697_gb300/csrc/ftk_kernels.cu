@@ -838,6 +838,143 @@ __device__ void locate_classify_vec2(const Field &F, long long fid, float4 &off,
     morse = (int8_t)(d < 0 ? 1 : d == 0 || tr == 0 ? -1 : tr < 0 ? 2 : 0);
 }
 
+// 3D location (Eq. 1) and Morse index of a punctured face from its vertices'
+// gradients V[k] and symmetrised Hessians HS[k] (k in chain order; ch = the
+// face's chain).  FILTER_ONLY: MORSE_PENDING where neither exact int128 nor
+// the certified FP32 filter decides (the multiword evaluation is left to a
+// later pass).
+template <bool FILTER_ONLY>
+__device__ void locate_classify3_from(const uint8_t *ch, const int32_t (&V)[4][3], const long long (&HS)[4][3][3],
+                                      float4 &off, int8_t &morse) {
+    constexpr int N = 3, BW = 16;
+    __int128 D[N + 1];
+    __int128 Dsum = 0;
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        int32_t M[N][N];
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j <= N; ++j) {
+            if (j == k) continue;
+#pragma unroll
+            for (int r = 0; r < N; ++r) M[c][r] = V[j][r];
+            ++c;
+        }
+        const __int128 d = det_exact(M);
+        D[k] = ((N + k) & 1) ? -d : d;
+        Dsum += D[k];
+    }
+    float mu[N + 1];
+    if (Dsum == 0) {
+#pragma unroll
+        for (int k = 0; k <= N; ++k) mu[k] = 1.0f / (N + 1);
+    } else {
+        const float fd = i128_to_float(Dsum);
+#pragma unroll
+        for (int k = 0; k <= N; ++k) mu[k] = i128_to_float(D[k]) / fd;
+    }
+    float o[N + 1];
+#pragma unroll
+    for (int a = 0; a <= N; ++a) o[a] = 0.0f;
+#pragma unroll
+    for (int k = 1; k <= N; ++k)
+#pragma unroll
+        for (int a = 0; a <= N; ++a)
+            if ((ch[k - 1] >> a) & 1) o[a] += mu[k];
+    off = make_float4(o[0], o[1], o[2], o[N]);
+
+    // S = sign(D) sum_k D_k (H_k + H_k^T), exact
+    const int sg = sgn128(Dsum);
+    {
+        // S exactly in int128 (|w| < 2^93, |h| < 2^34) and in FP32 from
+        // weights scaled by one power of two (the index is unchanged by a
+        // positive scale).  Small S (every entry < 2^40, e.g. near-flat,
+        // quantised regions): tr, m2 and det exactly in int128 (products
+        // < 2^121).  Otherwise the FP32 filter, and the multiword evaluation
+        // below only when the filter cannot certify every sign.
+        __int128 wmax = 0;
+        for (int k = 0; k <= N; ++k) {
+            const __int128 w = D[k] < 0 ? -D[k] : D[k];
+            if (w > wmax) wmax = w;
+        }
+        const int wbits = i128_bits(wmax);
+        __int128 Si[3][3];
+        float Sd[3][3], Ad[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                Si[a][b] = 0;
+                Sd[a][b] = Ad[a][b] = 0.0f;
+            }
+        for (int k = 0; k <= N; ++k) {
+            const __int128 w = sg < 0 ? -D[k] : D[k];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = a; b < 3; ++b) Si[a][b] += w * (__int128)HS[k][a][b];
+            s_fp32_step<3>(ldexpf(i128_to_float(w), 1 - wbits), HS[k], Sd, Ad);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < a; ++b) Si[a][b] = Si[b][a];
+        s_fp32_symmetrise<3>(Sd, Ad);
+        const __int128 LIM = (__int128)1 << 40;
+        // the int128 sums cannot wrap: 4 terms of |w| < 2^wbits, |h| < 2^35
+        bool small = wbits <= 88;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a; b < 3; ++b) small &= Si[a][b] < LIM && Si[a][b] > -LIM;
+        if (small) {
+            const __int128 tr = Si[0][0] + Si[1][1] + Si[2][2];
+            const __int128 m2 = Si[0][0] * Si[1][1] - Si[0][1] * Si[0][1] + Si[0][0] * Si[2][2] -
+                                Si[0][2] * Si[0][2] + Si[1][1] * Si[2][2] - Si[1][2] * Si[1][2];
+            const __int128 det = Si[0][0] * (Si[1][1] * Si[2][2] - Si[1][2] * Si[1][2]) -
+                                 Si[0][1] * (Si[0][1] * Si[2][2] - Si[1][2] * Si[0][2]) +
+                                 Si[0][2] * (Si[0][1] * Si[1][2] - Si[1][1] * Si[0][2]);
+            if (det == 0) {
+                morse = -1;
+                return;
+            }
+            const int sgn3[3] = {sgn128(tr), sgn128(m2), sgn128(det)};
+            int prev = 1, changes = 0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                if (sgn3[i] != 0) {
+                    if (sgn3[i] != prev) ++changes;
+                    prev = sgn3[i];
+                }
+            morse = (int8_t)changes;
+            return;
+        }
+        int m = 0;
+        if (morse_filter3(Sd, Ad, m)) {
+            morse = (int8_t)m;
+            return;
+        }
+        if constexpr (FILTER_ONLY) {
+            morse = MORSE_PENDING;
+            return;
+        }
+    }
+    if constexpr (!FILTER_ONLY) {
+        BigInt<BW> S[N][N];
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int b = 0; b < N; ++b) S[a][b] = big_from<BW>(0);
+        for (int k = 0; k <= N; ++k) {
+            const __int128 w = sg < 0 ? -D[k] : D[k];
+            for (int a = 0; a < N; ++a)
+                for (int b = 0; b < N; ++b)
+                    S[a][b] = big_add(S[a][b], big_from<BW>(w * (__int128)HS[k][a][b]));
+        }
+        morse = (int8_t)morse_from_S<N, BW>(S);
+    }
+}
+
 template <int N, bool FILTER_ONLY = false>
 __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8_t &morse) {
     if constexpr (N == 2) {
@@ -846,7 +983,6 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
             return;
         }
     }
-    constexpr int BW = N == 2 ? 8 : 16;
     int tt;
     const Pt base = decode_face<N>(F, fid, tt);
     const uint8_t *ch = mesh<N>().face[tt];
@@ -859,12 +995,7 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
     for (int k = 0; k <= N; ++k) {
         v[k] = k == 0 ? base : add_mask<N>(base, ch[k - 1]);
         iv[k] = k == 0 ? ib : ib + mask_offset<N>(F, ch[k - 1]);
-        if constexpr (N == 2) {
-            hess_sym<N, true>(F, v[k], iv[k], HS2[k], V[k]);
-        } else {
-#pragma unroll
-            for (int a = 0; a < N; ++a) V[k][a] = grad_at(F, v[k], iv[k], a);
-        }
+        if constexpr (N == 2) hess_sym<N, true>(F, v[k], iv[k], HS2[k], V[k]);
     }
     if constexpr (N == 2) {
         // |G| <= 2^30: the 2x2 determinants (< 2^61) and their sum fit in int64
@@ -922,134 +1053,10 @@ __device__ void locate_classify(const Field &F, long long fid, float4 &off, int8
         morse = (int8_t)(d < 0 ? 1 : d > 0 ? (tr < 0 ? 2 : 0) : -1);
         return;
     } else {
-    __int128 D[N + 1];
-    __int128 Dsum = 0;
+        long long HS3[4][3][3];
 #pragma unroll
-    for (int k = 0; k <= N; ++k) {
-        int32_t M[N][N];
-        int c = 0;
-#pragma unroll
-        for (int j = 0; j <= N; ++j) {
-            if (j == k) continue;
-#pragma unroll
-            for (int r = 0; r < N; ++r) M[c][r] = V[j][r];
-            ++c;
-        }
-        const __int128 d = det_exact(M);
-        D[k] = ((N + k) & 1) ? -d : d;
-        Dsum += D[k];
-    }
-    float mu[N + 1];
-    if (Dsum == 0) {
-#pragma unroll
-        for (int k = 0; k <= N; ++k) mu[k] = 1.0f / (N + 1);
-    } else {
-        const float fd = i128_to_float(Dsum);
-#pragma unroll
-        for (int k = 0; k <= N; ++k) mu[k] = i128_to_float(D[k]) / fd;
-    }
-    float o[N + 1];
-#pragma unroll
-    for (int a = 0; a <= N; ++a) o[a] = 0.0f;
-#pragma unroll
-    for (int k = 1; k <= N; ++k)
-#pragma unroll
-        for (int a = 0; a <= N; ++a)
-            if ((ch[k - 1] >> a) & 1) o[a] += mu[k];
-    off = make_float4(o[0], o[1], N == 3 ? o[2] : 0.0f, o[N]);
-
-    // S = sign(D) sum_k D_k (H_k + H_k^T), exact
-    const int sg = sgn128(Dsum);
-    {
-        // S exactly in int128 (|w| < 2^93, |h| < 2^34) and in FP32 from
-        // weights scaled by one power of two (the index is unchanged by a
-        // positive scale).  Small S (every entry < 2^40, e.g. near-flat,
-        // quantised regions): tr, m2 and det exactly in int128 (products
-        // < 2^121).  Otherwise the FP32 filter, and the multiword evaluation
-        // below only when the filter cannot certify every sign.
-        __int128 wmax = 0;
-        for (int k = 0; k <= N; ++k) {
-            const __int128 w = D[k] < 0 ? -D[k] : D[k];
-            if (w > wmax) wmax = w;
-        }
-        const int wbits = i128_bits(wmax);
-        __int128 Si[3][3];
-        float Sd[3][3], Ad[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                Si[a][b] = 0;
-                Sd[a][b] = Ad[a][b] = 0.0f;
-            }
-        for (int k = 0; k <= N; ++k) {
-            const __int128 w = sg < 0 ? -D[k] : D[k];
-            long long HS[N][N];
-            hess_sym<N>(F, v[k], iv[k], HS);
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = a; b < 3; ++b) Si[a][b] += w * (__int128)HS[a][b];
-            s_fp32_step<3>(ldexpf(i128_to_float(w), 1 - wbits), HS, Sd, Ad);
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < a; ++b) Si[a][b] = Si[b][a];
-        s_fp32_symmetrise<3>(Sd, Ad);
-        const __int128 LIM = (__int128)1 << 40;
-        // the int128 sums cannot wrap: 4 terms of |w| < 2^wbits, |h| < 2^35
-        bool small = wbits <= 88;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = a; b < 3; ++b) small &= Si[a][b] < LIM && Si[a][b] > -LIM;
-        if (small) {
-            const __int128 tr = Si[0][0] + Si[1][1] + Si[2][2];
-            const __int128 m2 = Si[0][0] * Si[1][1] - Si[0][1] * Si[0][1] + Si[0][0] * Si[2][2] -
-                                Si[0][2] * Si[0][2] + Si[1][1] * Si[2][2] - Si[1][2] * Si[1][2];
-            const __int128 det = Si[0][0] * (Si[1][1] * Si[2][2] - Si[1][2] * Si[1][2]) -
-                                 Si[0][1] * (Si[0][1] * Si[2][2] - Si[1][2] * Si[0][2]) +
-                                 Si[0][2] * (Si[0][1] * Si[1][2] - Si[1][1] * Si[0][2]);
-            if (det == 0) {
-                morse = -1;
-                return;
-            }
-            const int sgn3[3] = {sgn128(tr), sgn128(m2), sgn128(det)};
-            int prev = 1, changes = 0;
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-                if (sgn3[i] != 0) {
-                    if (sgn3[i] != prev) ++changes;
-                    prev = sgn3[i];
-                }
-            morse = (int8_t)changes;
-            return;
-        }
-        int m = 0;
-        if (morse_filter3(Sd, Ad, m)) {
-            morse = (int8_t)m;
-            return;
-        }
-        if (FILTER_ONLY) {
-            morse = MORSE_PENDING;
-            return;
-        }
-    }
-    BigInt<BW> S[N][N];
-#pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int b = 0; b < N; ++b) S[a][b] = big_from<BW>(0);
-    for (int k = 0; k <= N; ++k) {
-        long long HS[N][N];
-        hess_sym<N>(F, v[k], iv[k], HS);
-        const __int128 w = sg < 0 ? -D[k] : D[k];
-        for (int a = 0; a < N; ++a)
-            for (int b = 0; b < N; ++b)
-                S[a][b] = big_add(S[a][b], big_from<BW>(w * (__int128)HS[a][b]));
-    }
-    morse = (int8_t)morse_from_S<N, BW>(S);
+        for (int k = 0; k <= 3; ++k) hess_sym<3, true>(F, v[k], iv[k], HS3[k], V[k]);
+        locate_classify3_from<FILTER_ONLY>(ch, V, HS3, off, morse);
     }   // N == 3
 }
 
@@ -1494,39 +1501,82 @@ __global__ void __launch_bounds__(NT) k_survive_eval_thread(Field F, Workspace W
         W.surv_mask[s] = eval_cube<N>(F, W.surv[s]);
 }
 
-// one warp per surviving cube (grid-stride over the survivor list): lanes
-// 0..2^(N+1)-1 load the corner gradients, then the face types are split over
-// the lanes; bit tt of the mask = face type tt punctured
-template <int N>
-__global__ void __launch_bounds__(NT) k_survive_eval(Field F, Workspace W) {
-    constexpr int D = N + 1;
-    constexpr int NCRN = 1 << D;
-    constexpr int T = MeshDims<N>::T;
+// index (from 0) of the n-th set bit of m; n < popc(m)
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
+    int p = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (n >= c) {
+            n -= c;
+            m >>= w;
+            p += w;
+        }
+    }
+    return p;
+}
+
+// Exact SoS test of a 3D face whose three components each change sign over
+// its vertices (the sign test that could exclude it has already failed):
+// (-1)^k sign det(V without vertex k) equal for k = 0..3, int64 determinants
+// when every entry fits
+__device__ __forceinline__ bool face_punctured3_mixed(const int32_t (&V)[4][3]) {
+    const bool fit = entries_fit20(V);
+    int ref = 0;
+#pragma unroll
+    for (int k = 0; k <= 3; ++k) {
+        int32_t M[3][3];
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j <= 3; ++j) {
+            if (j == k) continue;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) M[c][r] = V[j][r];
+            ++c;
+        }
+        const int s = sos_det_sign3(M, fit);
+        const int val = (k & 1) ? -s : s;
+        if (k == 0) ref = val;
+        else if (val != ref) return false;
+    }
+    return true;
+}
+
+// 3D: two surviving cubes per warp per step (grid-stride over pairs of the
+// survivor list).  Lanes 0-15 load the 16 corner gradients of the first
+// cube, lanes 16-31 those of the second; three ballots give every corner's
+// sign pattern.  A face whose corners agree in the sign of one component
+// cannot be punctured (zero counts as positive); the faces of both cubes that
+// pass this test are gathered and handed out one per lane for the exact SoS
+// test.  Bit tt of a cube's mask = face type tt punctured.
+__global__ void __launch_bounds__(NT) k_survive_eval3(Field F, Workspace W) {
+    constexpr int N = 3, D = 4, T = MeshDims<3>::T;
     constexpr int WPB = NT / 32;
-    __shared__ int32_t Gs[WPB][NCRN][N];
+    constexpr uint32_t ALL = 0xffffffffu;
+    __shared__ int32_t Gs[WPB][2][16][3];
+    __shared__ uint32_t fch[T];   // face chains m_1 | m_2 << 8 | m_3 << 16
+    for (int i = threadIdx.x; i < T; i += NT)
+        fch[i] = mesh<3>().face[i][0] | (uint32_t)mesh<3>().face[i][1] << 8 | (uint32_t)mesh<3>().face[i][2] << 16;
+    __syncthreads();
     clear_scan_states(W);
     if (W.ctr->status & ST_SOVERFLOW) return;
     const long long ns = (long long)W.ctr->survivors;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * WPB;
-    // lane l evaluates face types l and l + 32 of every cube: their chains
-    // and corner masks are read once (per-lane indices into constant memory
-    // would serialise inside the loop)
-    constexpr int NF = (T + 31) / 32;
-    int chs[NF][N];
-    uint32_t Ms[NF];
+    const int half = lane >> 4, c = lane & 15;
+    // face types lane and lane + 32: corner masks and last chain masks
+    uint32_t Ms[2], last[2];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
+    for (int f = 0; f < 2; ++f) {
         const int tt = f * 32 + lane;
-        Ms[f] = 1u;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            chs[f][k] = tt < T ? mesh<N>().face[tt][k] : 0;
-            Ms[f] |= 1u << chs[f][k];
-        }
+        const uint32_t ch = tt < T ? fch[tt] : 0u;
+        Ms[f] = tt < T ? (1u | 1u << (ch & 0xff) | 1u << ((ch >> 8) & 0xff) | 1u << (ch >> 16)) : 0u;
+        last[f] = ch >> 16;
     }
-    for (long long s = (long long)blockIdx.x * WPB + warp; s < ns; s += stride) {
-        const long long g = W.surv[s];
+    const long long stride = (long long)gridDim.x * WPB * 2;
+    for (long long s0 = ((long long)blockIdx.x * WPB + warp) * 2; s0 < ns; s0 += stride) {
+        const long long s = s0 + half;
+        const bool have = s < ns;
+        const long long g = have ? W.surv[s] : 0;
         const Pt b = decode_vertex(F, g);
         int inside = 0;   // bit a: axis a can step +1
 #pragma unroll
@@ -1535,47 +1585,67 @@ __global__ void __launch_bounds__(NT) k_survive_eval(Field F, Workspace W) {
             const int ext = a == N ? F.nt : ext_of(F, a);
             if (b.c[slot] + 1 < ext) inside |= 1 << a;
         }
+        if (!have) inside = 0;   // no face of a missing second cube is tested
         int32_t gc[N] = {};
-        if (lane < NCRN && !(lane & ~inside)) {
-            const Pt p = add_mask<N>(b, lane);
-            const long long ip = vindex(F, b) + mask_offset<N>(F, lane);
+        const bool corner = have && !(c & ~inside);
+        if (corner) {
+            const Pt p = add_mask<N>(b, c);
+            const long long ip = vindex(F, b) + mask_offset<N>(F, c);
 #pragma unroll
             for (int r = 0; r < N; ++r) gc[r] = grad_at(F, p, ip, r);
         }
-        if (lane < NCRN)
 #pragma unroll
-            for (int r = 0; r < N; ++r) Gs[warp][lane][r] = gc[r];
-        // bit c of neg[r]: component r is negative at corner c (the corner
-        // index is its axis mask); a face whose corners all agree in the sign
-        // of one component cannot be punctured (zero counts as positive)
+        for (int r = 0; r < N; ++r) Gs[warp][half][c][r] = gc[r];
         uint32_t neg[N];
 #pragma unroll
-        for (int r = 0; r < N; ++r) neg[r] = __ballot_sync(0xffffffffu, lane < NCRN && gc[r] < 0);
+        for (int r = 0; r < N; ++r) neg[r] = __ballot_sync(ALL, corner && gc[r] < 0);
+        const int ins[2] = {__shfl_sync(ALL, inside, 0), __shfl_sync(ALL, inside, 16)};
         __syncwarp();
-        unsigned long long m = 0;
+        // candidate lists: (cube q, face types 32 f + bit)
+        uint32_t cand[4];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            const int tt = f * 32 + lane;
-            bool pun = false;
-            if (tt < T) {
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
                 const uint32_t M = Ms[f];
-                bool mixed = true;
+                bool mixed = M != 0 && !(last[f] & ~ins[q]);
 #pragma unroll
-                for (int r = 0; r < N; ++r) mixed &= (neg[r] & M) != 0 && (neg[r] & M) != M;
-                if (mixed && !(chs[f][N - 1] & ~inside)) {
-                    int32_t V[N + 1][N];
-#pragma unroll
-                    for (int k = 0; k <= N; ++k) {
-                        const int c = k == 0 ? 0 : chs[f][k - 1];
-#pragma unroll
-                        for (int r = 0; r < N; ++r) V[k][r] = Gs[warp][c][r];
-                    }
-                    pun = face_punctured<N>(V);
+                for (int r = 0; r < N; ++r) {
+                    const uint32_t nq = (neg[r] >> (16 * q)) & M;
+                    mixed &= nq != 0 && nq != M;
                 }
+                cand[2 * q + f] = __ballot_sync(ALL, mixed);
             }
-            m |= (unsigned long long)__ballot_sync(0xffffffffu, pun) << (32 * f);
+        const int n0 = __popc(cand[0]), n1 = __popc(cand[1]), n2 = __popc(cand[2]);
+        const int total = n0 + n1 + n2 + __popc(cand[3]);
+        uint32_t mk[4] = {0u, 0u, 0u, 0u};   // punctured masks: cube 0 lo/hi, cube 1 lo/hi
+        for (int j0 = 0; j0 < total; j0 += 32) {
+            const int j = j0 + lane;
+            int list = -1, bit = 0;
+            if (j < total) {
+                int n = j;
+                list = n < n0 ? 0 : n < n0 + n1 ? 1 : n < n0 + n1 + n2 ? 2 : 3;
+                n -= list == 0 ? 0 : list == 1 ? n0 : list == 2 ? n0 + n1 : n0 + n1 + n2;
+                bit = nth_set_bit(list == 0 ? cand[0] : list == 1 ? cand[1] : list == 2 ? cand[2] : cand[3], n);
+            }
+            bool pun = false;
+            if (list >= 0) {
+                const int q = list >> 1;
+                const uint32_t ch = fch[(list & 1) * 32 + bit];
+                const int cr[4] = {0, (int)(ch & 0xff), (int)((ch >> 8) & 0xff), (int)(ch >> 16)};
+                int32_t V[4][3];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int r = 0; r < N; ++r) V[k][r] = Gs[warp][q][cr[k]][r];
+                pun = face_punctured3_mixed(V);
+            }
+#pragma unroll
+            for (int l = 0; l < 4; ++l) mk[l] |= __reduce_or_sync(ALL, pun && list == l ? 1u << bit : 0u);
         }
-        if (lane == 0) W.surv_mask[s] = m;
+        if (have && c == 0)
+            W.surv_mask[s] = half ? (unsigned long long)mk[2] | (unsigned long long)mk[3] << 32
+                                  : (unsigned long long)mk[0] | (unsigned long long)mk[1] << 32;
         __syncwarp();
     }
 }
@@ -1668,6 +1738,57 @@ __global__ void __launch_bounds__(NT) k_locate(Field F, Workspace W) {
             const unsigned long long q = atomicAdd(&W.ctr->pending, 1ull);
             W.label[q] = i;
         }
+    }
+}
+
+// 3D, four lanes per puncture: lane k of a group loads vertex k's samples
+// (gradient and symmetrised Hessian, all loads issued together), the
+// group's first lane locates and classifies the face from them
+__global__ void __launch_bounds__(NT) k_locate3(Field F, Workspace W) {
+    __shared__ int32_t Vs[NT][3];
+    __shared__ long long Hs[NT][6];   // HS_00, 01, 02, 11, 12, 22
+    if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
+    const long long P = W.ctr->punctures;
+    const int k = threadIdx.x & 3, g0 = threadIdx.x & ~3;
+    for (long long i0 = (long long)blockIdx.x * (NT / 4); i0 < P; i0 += (long long)gridDim.x * (NT / 4)) {
+        const long long i = i0 + (threadIdx.x >> 2);
+        const bool have = i < P;
+        int tt = 0;
+        if (have) {
+            const Pt base = decode_face<3>(F, W.face[i], tt);
+            const int m = k == 0 ? 0 : mesh<3>().face[tt][k - 1];
+            const Pt v = add_mask<3>(base, m);
+            long long HS[3][3];
+            int32_t G[3];
+            hess_sym<3, true>(F, v, vindex(F, base) + mask_offset<3>(F, m), HS, G);
+            Vs[threadIdx.x][0] = G[0]; Vs[threadIdx.x][1] = G[1]; Vs[threadIdx.x][2] = G[2];
+            Hs[threadIdx.x][0] = HS[0][0]; Hs[threadIdx.x][1] = HS[0][1]; Hs[threadIdx.x][2] = HS[0][2];
+            Hs[threadIdx.x][3] = HS[1][1]; Hs[threadIdx.x][4] = HS[1][2]; Hs[threadIdx.x][5] = HS[2][2];
+        }
+        __syncwarp();
+        if (have && k == 0) {
+            int32_t V[4][3];
+            long long HS[4][3][3];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) V[q][r] = Vs[g0 + q][r];
+                const long long *h = Hs[g0 + q];
+                HS[q][0][0] = h[0]; HS[q][0][1] = HS[q][1][0] = h[1]; HS[q][0][2] = HS[q][2][0] = h[2];
+                HS[q][1][1] = h[3]; HS[q][1][2] = HS[q][2][1] = h[4]; HS[q][2][2] = h[5];
+            }
+            float4 o;
+            int8_t mo;
+            locate_classify3_from<true>(mesh<3>().face[tt], V, HS, o, mo);
+            W.off[i] = o;
+            W.morse[i] = mo;
+            if (mo == MORSE_PENDING) {
+                // W.label is free until k_label: the list of pending punctures
+                const unsigned long long q = atomicAdd(&W.ctr->pending, 1ull);
+                W.label[q] = i;
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -2127,7 +2248,7 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
     if (stream) {
         if constexpr (N == 2)
             k_survive_eval_thread<N><<<gsize(resident_grid<k_survive_eval_thread<N>>(), W.scap, NT), NT, 0, s>>>(F, W);
-        else k_survive_eval<N><<<gsize(sg * 2, W.scap, NT / 32), NT, 0, s>>>(F, W);
+        else k_survive_eval3<<<gsize(sg * 2, W.scap, NT / 16), NT, 0, s>>>(F, W);
         k_survive_scan<<<gsize(sg, W.scap, LB_TILE), NT, 0, s>>>(W);
     }
     {
@@ -2141,7 +2262,7 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
         k_emit<N><<<gsize(resident_grid<k_emit<N>>(), W.scap, NT), NT, 0, s>>>(F, B, W);
         // few, long-running threads in 3D: small blocks spread them over every SM
         if constexpr (N == 3) {
-            k_locate<N><<<gsize(sg * 2, W.cap, 64), 64, 0, s>>>(F, W);
+            k_locate3<<<gsize(sg * 2, W.cap, NT / 4), NT, 0, s>>>(F, W);
             k_classify_exact<N><<<gsize(sg, W.cap, NT), NT, 0, s>>>(F, W);
         } else {
             k_locate<N><<<gsize(resident_grid<k_locate<N>>(), W.cap, NT), NT, 0, s>>>(F, W);

@@ -56,7 +56,8 @@ def test_random_matrices(shim):
     rng = np.random.default_rng(5)
     for _ in range(20000):
         n = int(rng.integers(2, 4))
-        lim = int(rng.choice([2, 3, 1000, 1 << 29]))
+        # 2^20 and 2^20 + 1: either side of the int64 fast path's entry range
+        lim = int(rng.choice([2, 3, 1000, 1 << 20, (1 << 20) + 1, 1 << 29]))
         m = rng.integers(-lim, lim + 1, size=n * n)
         # rank-deficient cases: a repeated or zero column
         if rng.random() < 0.3:
