@@ -791,6 +791,99 @@ def _measure_plain(wl, args, dev, dist, world, rank, local):
     )
 
 
+ISO_LEVEL = 0.25        # isovalue of the isovolume line: level sets around the positive blobs
+ISO_SAMPLE_SLICES = 3   # slices of the bit-exact / CPU-baseline sample of the isovolume line
+
+
+def edge_count(dims, nt):
+    """Number of 1-simplices (edges) of the Kuhn spacetime mesh of the grid:
+    sum over nonempty axis masks m of prod_a (N_a - m_a)."""
+    ext = tuple(dims) + (nt,)
+    d = len(ext)
+    total = 0
+    for m in range(1, 1 << d):
+        cnt = 1
+        for a in range(d):
+            cnt *= ext[a] - ((m >> a) & 1)
+        total += cnt
+    return total
+
+
+def _measure_iso(args, dev, world):
+    """Isovolume tracking (Sec. 6.1) of the 128^3 x 16 blob field at
+    f = ISO_LEVEL: K timed plan executions (L2 flushed between them), the
+    dense edge-bit pass against HBM, a bit-exact comparison with the oracle
+    on the first ISO_SAMPLE_SLICES slices, and the oracle's time there."""
+    import torch
+    from paper_2011_08697_gb300 import ftk
+    W = WORKLOADS["blobs3d"]
+    f_np = make_field("blobs3d", seed=0)
+    nverts = f_np.size
+    edges = edge_count(W["dims"], W["nt"])
+    x = torch.from_numpy(f_np).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    plan = ftk.IsoPlan(f_np.shape)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 1)):
+            plan.execute(x, ISO_LEVEL, stream)
+        P = plan.count()
+        res = plan.download()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stages = []
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            plan.execute(x, ISO_LEVEL, stream)
+            ends[k].record(stream)
+            plan.count()
+            stages.append(plan.stage_times())
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    tot_ms = sum(step_ms)
+    names = ["edge_bits", "emit", "cell_pass", "label"]
+    st = {n: statistics.mean(s[i] for s in stages) for i, n in enumerate(names)}
+    bits_ms = st["edge_bits"]
+    alg_bytes = 4.0 * nverts + nverts / 8.0      # the field once, one bit per vertex out
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (bits_ms / 1e3) / 1e9
+    step_mean = tot_ms / args.steps
+    # bit-exact against the oracle on the first slices (the whole pipeline
+    # run on that sub-field), and the oracle's time there
+    from oracle import iso as oiso
+    sub = np.ascontiguousarray(f_np[:ISO_SAMPLE_SLICES])
+    got = ftk.ftk_track_iso3d(torch.from_numpy(sub).to(dev), ISO_LEVEL)
+    t0 = time.perf_counter()
+    ref = oiso.track_iso(sub, ISO_LEVEL)
+    dt = time.perf_counter() - t0
+    ok = bool(np.array_equal(got["edge_id"], ref["edge_id"]) and np.array_equal(got["label"], ref["label"])
+              and np.array_equal(got["base"].astype(np.int64), ref["base"])
+              and np.array_equal(got["ordinal"].astype(bool), ref["ordinal"]))
+    err = float(np.max(np.abs(got["off"].astype(np.float64) - ref["off"]))) if len(ref["edge_id"]) else 0.0
+    sub_edges = edge_count(W["dims"], ISO_SAMPLE_SLICES)
+    plan.close()
+    return {
+        "workload": f"isovolume_f={ISO_LEVEL}_" + W["name"], "metric": "spacetime edges tested/s",
+        "value": weak_value(edges, world, args.steps, tot_ms), "unit": "edges/s",
+        "ms_per_step": step_mean, "edges_per_step": edges, "intersected_edges": int(P),
+        "pieces": int(len(np.unique(res["label"]))), "stages_ms": st,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_iso_bits",
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": bits_ms,
+                     "whole_step_frac": (alg_bytes / (step_mean / 1e3) / 1e9) / peak},
+        "bit_exact_sample": {"ok": ok, "slices": ISO_SAMPLE_SLICES, "intersected_edges": int(len(ref["edge_id"])),
+                             "max_offset_err": err,
+                             "compared": "edge ids, labels, base vertices, ordinal flags: equal; offsets <= 1e-5"},
+        "cpu_baseline": {"value": sub_edges / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"the first {ISO_SAMPLE_SLICES} slices of the workload ({sub_edges} edges)",
+                         "seconds": dt},
+        "gpu_launches": 4 * args.steps,
+    }
+
+
 def gpu_arm(args):
     import torch
     from paper_2011_08697_gb300 import build as _b, ftk
@@ -805,6 +898,9 @@ def gpu_arm(args):
     extra = None
     if args.with_2d and wl == "blobs3d":
         extra = _measure_plain("spiral2d", args, dev, dist, world, rank, local)
+    iso_line = None
+    if args.with_iso and wl == "blobs3d" and world == 1:
+        iso_line = _measure_iso(args, dev, world)
 
     if rank == 0:
         W = m["W"]
@@ -821,7 +917,8 @@ def gpu_arm(args):
             "p50_step_ms": statistics.median(m["step_ms"]), "p99_step_ms": m["p99"],
             "punctures": m["P"], "trajectories": int(len(np.unique(m["res"]["label"]))),
             "stages_ms": m["stages"], "plan": m["desc"], "roofline": m["roofline"],
-            "e2e": m["e2e"], "gpu_launches": m["gpu_launches"] + (extra["gpu_launches"] if extra else 0),
+            "e2e": m["e2e"], "gpu_launches": m["gpu_launches"] + (extra["gpu_launches"] if extra else 0)
+            + (iso_line["gpu_launches"] if iso_line else 0),
             "clocks": m["clocks"],
         }
         if extra is not None:
@@ -834,6 +931,8 @@ def gpu_arm(args):
                 "roofline": extra["roofline"], "e2e": extra["e2e"], "clocks": extra["clocks"],
                 "gpu_launches": extra["gpu_launches"],
             }
+        if iso_line is not None:
+            line["isovolume"] = iso_line
         if world == 1:
             # the oracle on the full workload, all host cores: the bit-exact
             # check and the all-core CPU baseline in one run
@@ -865,6 +964,8 @@ def main():
     ap.add_argument("--workload", choices=list(WORKLOADS), default="blobs3d")
     ap.add_argument("--no-2d", dest="with_2d", action="store_false",
                     help="blobs3d: skip the 2D spiral workload reported beside it")
+    ap.add_argument("--no-iso", dest="with_iso", action="store_false",
+                    help="blobs3d: skip the isovolume line reported beside it")
     ap.add_argument("--duration", type=float, default=60.0, help="serve2d: Poisson phase seconds")
     ap.add_argument("--sat-pushes", type=int, default=24, help="serve2d: saturated pushes per stream")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="serve2d: admission budget")

@@ -330,6 +330,75 @@ ftk_status ftk_stream_footprint(int ndim, int64_t nx, int64_t ny, int64_t nz, co
                                 uint64_t *bytes);
 
 /* ---------------------------------------------------------------------
+ * Isovolume tracking (paper Sec. 6.1; Algorithm 1, right column): the level
+ * set f = c of a time-varying scalar field, reconstructed on the same
+ * simplicial spacetime mesh as an (n-1)-dimensional object in n + 1
+ * dimensions (a surface swept through time in 3D + time).
+ *
+ *   1. edge pass: every 1-simplex (v, v + bits(m)) of the mesh -- base
+ *      vertex v, nonempty axis mask m -- is tested.  The test is the 1-D
+ *      case of the critical-point predicate on w = f - c (Sec. 6.1), whose
+ *      symbolic perturbation is a positive infinitesimal: a vertex is above
+ *      iff f >= c, and an edge is intersected iff its vertices disagree.
+ *      The comparison of a float32 sample with the double isovalue is
+ *      exact.
+ *   2. location: mu = w(v) / (w(v) - w(v + m)), the crossing of the
+ *      linear interpolant, in FP32 with w formed by an exact two-sum
+ *      against the isovalue split into two floats (|error| < 1e-6 of the
+ *      edge length).
+ *   3. cell pass: every (n+1)-simplex (a pentachoron in 3D + time, a
+ *      tetrahedron in 2D + time) unites its intersected edges -- 4 or 6,
+ *      3 or 4 (Sec. 6.1 cases I and II); each connected piece of the
+ *      isovolume is labelled by the smallest edge id it contains.  With
+ *      nt = 1 there are no cells and every edge is its own piece.
+ *
+ * Edge id = g * (2^(n+1) - 1) + (m - 1), g the base vertex's global id
+ * (as for faces), m's bits: 0 = x, 1 = y, 2 = z (3D), last = t.  Records
+ * are sorted by edge id.  Non-finite samples -> FTK_ERR_RANGE; more than
+ * 2^31 - 1 intersected edges -> FTK_ERR_RANGE.  Layout, ownership and
+ * errors as for the critical-point calls; the isovalue must not be NaN.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    int64_t edge_id;
+    int64_t label;       /* smallest edge id of the connected piece */
+    int32_t base[4];     /* x, y, z, t of the edge's lower vertex (z = 0 in 2D) */
+    float off[4];        /* intersection point minus base (x, y, z, t) */
+    uint8_t ordinal;     /* 1: the edge lies inside one time slice */
+    uint8_t ndim;        /* 2 or 3 */
+    uint8_t reserved[6];
+} ftk_iso_point;         /* 56 bytes */
+
+typedef struct ftk_iso_result ftk_iso_result;
+typedef struct ftk_iso_plan ftk_iso_plan;
+
+ftk_status ftk_track_iso2d(const float *f, int64_t nx, int64_t ny, int64_t nt, double isovalue,
+                           ftk_iso_result **out, void *cuda_stream);
+ftk_status ftk_track_iso3d(const float *f, int64_t nx, int64_t ny, int64_t nz, int64_t nt, double isovalue,
+                           ftk_iso_result **out, void *cuda_stream);
+size_t ftk_iso_result_count(const ftk_iso_result *r);
+const ftk_iso_point *ftk_iso_result_data(const ftk_iso_result *r);
+void ftk_iso_result_free(ftk_iso_result *r);
+
+/* Plans keep the device workspace of one shape (nz = 1 for ndim = 2) and
+ * the last run's records in device memory.  execute queues the pipeline on
+ * cuda_stream (a host field is copied before it returns); count waits for
+ * it, grows the capacities and runs again if the records did not fit, and
+ * checks the run's status; download / download_into copy the records
+ * (download_into: into a caller buffer of cap records, FTK_ERR_NOMEM if it
+ * is too small, *n set either way); device_records gives their device
+ * address (valid until the next execute). */
+ftk_status ftk_iso_plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, ftk_iso_plan **plan);
+ftk_status ftk_iso_plan_execute(ftk_iso_plan *plan, const float *f, double isovalue, void *cuda_stream);
+ftk_status ftk_iso_plan_count(ftk_iso_plan *plan, int64_t *n);
+ftk_status ftk_iso_plan_download(ftk_iso_plan *plan, ftk_iso_result **out);
+ftk_status ftk_iso_plan_download_into(ftk_iso_plan *plan, ftk_iso_point *dst, int64_t cap, int64_t *n);
+ftk_status ftk_iso_plan_device_records(ftk_iso_plan *plan, const ftk_iso_point **records, int64_t *n);
+/* device times (ms) of the last run's four stages -- edge bits (the dense
+ * pass), edge emission, cell pass, labels -- into ms[0..min(cap, 4)) */
+ftk_status ftk_iso_plan_stage_times(ftk_iso_plan *plan, float *ms, int cap, int *n);
+ftk_status ftk_iso_plan_destroy(ftk_iso_plan *plan);
+
+/* ---------------------------------------------------------------------
  * Tracking without device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- code that
  * runs inside a host application which has already reserved the device's

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libftk_gb300.so")
-SOURCES = ["ftk_kernels.cu", "ftk_capi.cu", "ftk_noalloc.cu", "ftk_batch.cu", "ftk_stream.cu", "ftk_detect2.cu", "ftk_detect3.cu", "ftk_traj.cu"]
+SOURCES = ["ftk_kernels.cu", "ftk_capi.cu", "ftk_noalloc.cu", "ftk_batch.cu", "ftk_stream.cu", "ftk_detect2.cu", "ftk_detect3.cu", "ftk_traj.cu",
+           "ftk_iso.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

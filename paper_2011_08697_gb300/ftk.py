@@ -72,7 +72,17 @@ EXPORTS = [
     "ftk_traj_free", "ftk_plan_slice", "ftk_slice_count", "ftk_slice_data", "ftk_slice_free",
     "ftk_debug_set_wait_limits", "ftk_plan_trajectories_filtered",
     "ftk_track_vec2d", "ftk_plan_create_vec2d",
+    "ftk_track_iso2d", "ftk_track_iso3d", "ftk_iso_result_count", "ftk_iso_result_data", "ftk_iso_result_free",
+    "ftk_iso_plan_create", "ftk_iso_plan_execute", "ftk_iso_plan_count", "ftk_iso_plan_download",
+    "ftk_iso_plan_download_into", "ftk_iso_plan_device_records", "ftk_iso_plan_destroy",
+    "ftk_iso_plan_stage_times",
 ]
+
+ISO_DTYPE = np.dtype([
+    ("edge_id", "<i8"), ("label", "<i8"), ("base", "<i4", (4,)), ("off", "<f4", (4,)),
+    ("ordinal", "u1"), ("ndim", "u1"), ("reserved", "u1", (6,)),
+])
+assert ISO_DTYPE.itemsize == 56
 
 
 class ftk_traj_filter(ctypes.Structure):
@@ -147,6 +157,19 @@ def lib():
         "ftk_slice_count": (i64, [vp]),
         "ftk_slice_data": (vp, [vp]),
         "ftk_slice_free": (None, [vp]),
+        "ftk_track_iso2d": (i32, [vp, i64, i64, i64, ctypes.c_double, pp, vp]),
+        "ftk_track_iso3d": (i32, [vp, i64, i64, i64, i64, ctypes.c_double, pp, vp]),
+        "ftk_iso_result_count": (ctypes.c_size_t, [vp]),
+        "ftk_iso_result_data": (vp, [vp]),
+        "ftk_iso_result_free": (None, [vp]),
+        "ftk_iso_plan_create": (i32, [i32, i64, i64, i64, i64, pp]),
+        "ftk_iso_plan_execute": (i32, [vp, vp, ctypes.c_double, vp]),
+        "ftk_iso_plan_count": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "ftk_iso_plan_download": (i32, [vp, pp]),
+        "ftk_iso_plan_download_into": (i32, [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)]),
+        "ftk_iso_plan_device_records": (i32, [vp, pp, ctypes.POINTER(ctypes.c_int64)]),
+        "ftk_iso_plan_destroy": (i32, [vp]),
+        "ftk_iso_plan_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -622,5 +645,122 @@ class Stream:
     def __del__(self):
         try:
             self.close(False)
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Isovolume tracking (ftk_track_iso2d / ftk_track_iso3d, ftk_iso_plan_*)
+# ---------------------------------------------------------------------------
+class _IsoResultOwner:
+    """Frees an ftk_iso_result when the array viewing its records is released."""
+
+    def __init__(self, rp):
+        self.rp = rp
+
+    def __del__(self):
+        try:
+            lib().ftk_iso_result_free(self.rp)
+        except Exception:
+            pass
+
+
+def _take_iso_result(rp) -> np.ndarray:
+    L = lib()
+    owner = _IsoResultOwner(rp)
+    n = L.ftk_iso_result_count(rp)
+    if n == 0:
+        return np.empty(0, dtype=ISO_DTYPE)
+    raw = (ctypes.c_char * (n * ISO_DTYPE.itemsize)).from_address(L.ftk_iso_result_data(rp))
+    raw.owner = owner
+    return np.frombuffer(raw, dtype=ISO_DTYPE)
+
+
+def ftk_track_iso2d(f, isovalue: float, stream=None) -> np.ndarray:
+    """Intersected edges of the level set f = isovalue of a 2D field
+    (nt, ny, nx), sorted by edge id, with crossing points and piece labels."""
+    ptr, keep, shape = _field_ptr(f)
+    if len(shape) != 3:
+        raise ValueError("2D field must have shape (nt, ny, nx)")
+    nt, ny, nx = shape
+    out = ctypes.c_void_p()
+    _check(lib().ftk_track_iso2d(ptr, nx, ny, nt, float(isovalue), ctypes.byref(out), _stream_ptr(stream)))
+    del keep
+    return _take_iso_result(out)
+
+
+def ftk_track_iso3d(f, isovalue: float, stream=None) -> np.ndarray:
+    """As ftk_track_iso2d for a 3D field (nt, nz, ny, nx)."""
+    ptr, keep, shape = _field_ptr(f)
+    if len(shape) != 4:
+        raise ValueError("3D field must have shape (nt, nz, ny, nx)")
+    nt, nz, ny, nx = shape
+    out = ctypes.c_void_p()
+    _check(lib().ftk_track_iso3d(ptr, nx, ny, nz, nt, float(isovalue), ctypes.byref(out), _stream_ptr(stream)))
+    del keep
+    return _take_iso_result(out)
+
+
+class IsoPlan:
+    """Device workspace for repeated isovolume tracking of fields of one
+    shape (``ftk_iso_plan_*``)."""
+
+    def __init__(self, shape):
+        shape = tuple(int(s) for s in shape)
+        if len(shape) == 3:
+            nt, ny, nx = shape
+            nz, ndim = 1, 2
+        elif len(shape) == 4:
+            nt, nz, ny, nx = shape
+            ndim = 3
+        else:
+            raise ValueError("shape must be (nt, ny, nx) or (nt, nz, ny, nx)")
+        self.shape = shape
+        self.ndim = ndim
+        h = ctypes.c_void_p()
+        _check(lib().ftk_iso_plan_create(ndim, nx, ny, nz, nt, ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+
+    def execute(self, f, isovalue: float, stream=None):
+        ptr, keep, shape = _field_ptr(f)
+        if tuple(shape) != self.shape:
+            raise ValueError(f"field shape {shape} != plan shape {self.shape}")
+        self._keep = keep
+        _check(lib().ftk_iso_plan_execute(self._h, ptr, float(isovalue), _stream_ptr(stream)))
+
+    def count(self) -> int:
+        c = ctypes.c_int64()
+        _check(lib().ftk_iso_plan_count(self._h, ctypes.byref(c)))
+        return c.value
+
+    def download(self) -> np.ndarray:
+        out = ctypes.c_void_p()
+        _check(lib().ftk_iso_plan_download(self._h, ctypes.byref(out)))
+        return _take_iso_result(out)
+
+    def download_into(self, buf: np.ndarray) -> np.ndarray:
+        if buf.dtype != ISO_DTYPE or not buf.flags.c_contiguous:
+            raise ValueError("buffer must be a contiguous ISO_DTYPE array")
+        c = ctypes.c_int64()
+        _check(lib().ftk_iso_plan_download_into(self._h, ctypes.c_void_p(buf.ctypes.data), len(buf),
+                                                ctypes.byref(c)))
+        return buf[: c.value]
+
+    def stage_times(self):
+        """Device ms of the last run: [edge bits, emission, cell pass, labels]."""
+        buf = (ctypes.c_float * 4)()
+        n = ctypes.c_int()
+        _check(lib().ftk_iso_plan_stage_times(self._h, buf, 4, ctypes.byref(n)))
+        return list(buf[: n.value])
+
+    def close(self):
+        if self._h:
+            _check(lib().ftk_iso_plan_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
