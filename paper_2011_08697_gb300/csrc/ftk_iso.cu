@@ -13,11 +13,16 @@
 //                edge of its own); the edges are written in id order with
 //                their crossing points, and every owner's first edge index
 //                and edge mask.
-//   k_iso_link   per owner whose unit cube lies in the grid: the cube's
+//   k_iso_pieces per owner whose unit cube lies in the grid: the cube's
 //                cells (pentachora / tetrahedra, one per ordering of the
-//                axes) unite their intersected edges -- first in a small
-//                union-find over the cube's 3^d - 2^d edge slots, then one
-//                global union (lock-free) per edge of each local piece.
+//                axes) unite their intersected edges in a small union-find
+//                over the cube's 3^d - 2^d edge slots; each local piece is
+//                represented by its smallest edge (global unions only for a
+//                cube with several pieces); every edge records the
+//                representative of its piece in its home cube.
+//   k_iso_join   per such cube and axis: the pieces of two face-adjacent
+//                cubes that share an intersected edge are united (lock-free
+//                global union-find over edge indices).
 //   k_iso_label  label = smallest edge id of the piece; host-layout records.
 #include <cuda_runtime.h>
 
@@ -60,7 +65,14 @@ struct IsoGrid {
     long long rows;      // nt * nz * ny
     float c_up;          // smallest float >= isovalue: f >= c  <=>  f >= c_up
     float c_hi, c_lo;    // isovalue ~= c_hi + c_lo
+    int small;           // every vertex id, edge id and item index < 2^31: FastDiv below
+    FastDiv dW, dVC, dX, dY, dYZ, dE;   // by W, ceil(nx / 128), nx, ny, ny * nz, 2^d - 1
 };
+
+// n / d with the plan's fixed divisors (FastDiv when the grid is small)
+__device__ __forceinline__ long long iso_div(const IsoGrid &G, long long n, const FastDiv &f, long long d) {
+    return G.small ? (long long)fdiv((unsigned)n, f) : n / d;
+}
 
 struct IsoCtr {
     unsigned status;
@@ -80,6 +92,9 @@ struct IsoWork {
     long long *own_g;              // [ocap] vertex id of each owner
     int *own_first;                // [ocap] its first edge index
     uint16_t *own_mask;            // [ocap] its intersected edge masks (bit m - 1)
+    uint16_t *own_cb;              // [ocap] above bits of the corners of its unit cube
+    int *own_rep;                  // [ocap] representative edge of its cube's piece (-1: several pieces)
+    int *edge_rep;                 // [cap] representative of each edge's piece in its home cube
     long long *id;                 // [cap] edge ids, sorted
     float4 *off;                   // [cap] crossing point - base vertex (x, y, z, t)
     int *parent;                   // [cap] union-find
@@ -131,11 +146,44 @@ struct IsoTables {
     }
 };
 
+// For every cell and every above/below pattern of its d + 1 vertices (bit k
+// = vertex k of the cell's chain above), the set of the cube's edge slots
+// the cell intersects: the slots of its vertex pairs that disagree.
+template <int N>
+struct IsoCellMasks {
+    static constexpr int D = N + 1, NCELL = IsoTables<N>::NCELL, NP = 1 << (D + 1);
+    uint64_t lo[NCELL][NP];   // slots 0-63
+    uint32_t hi[NCELL][NP];   // slot 64 (3D)
+    __host__ __device__ constexpr IsoCellMasks() : lo{}, hi{} {
+        const IsoTables<N> t;
+        for (int p = 0; p < NCELL; ++p)
+            for (int pat = 0; pat < NP; ++pat) {
+                uint64_t l = 0;
+                uint32_t h = 0;
+                for (int i = 0; i <= D; ++i)
+                    for (int j = i + 1; j <= D; ++j) {
+                        if (((pat >> i) ^ (pat >> j)) & 1) {
+                            const int sl = t.slot[t.chain[p][i]][t.chain[p][j]];
+                            if (sl < 64) l |= 1ull << sl;
+                            else h |= 1u;
+                        }
+                    }
+                lo[p][pat] = l;
+                hi[p][pat] = h;
+            }
+    }
+};
+
 __constant__ IsoTables<2> c_iso2 = IsoTables<2>();
 __constant__ IsoTables<3> c_iso3 = IsoTables<3>();
 template <int N> __device__ __forceinline__ const IsoTables<N> &iso_tables();
 template <> __device__ __forceinline__ const IsoTables<2> &iso_tables<2>() { return c_iso2; }
 template <> __device__ __forceinline__ const IsoTables<3> &iso_tables<3>() { return c_iso3; }
+__constant__ IsoCellMasks<2> c_cmask2 = IsoCellMasks<2>();
+__constant__ IsoCellMasks<3> c_cmask3 = IsoCellMasks<3>();
+template <int N> __device__ __forceinline__ const IsoCellMasks<N> &iso_cell_masks();
+template <> __device__ __forceinline__ const IsoCellMasks<2> &iso_cell_masks<2>() { return c_cmask2; }
+template <> __device__ __forceinline__ const IsoCellMasks<3> &iso_cell_masks<3>() { return c_cmask3; }
 
 // element offset of the step along edge mask m from a vertex (bit N = t)
 template <int N>
@@ -160,38 +208,77 @@ __device__ __forceinline__ float iso_w(float v, float c_hi, float c_lo) {
 }
 
 // ---------------------------------------------------------------------------
-// k_iso_bits: one warp per group of 8 consecutive (row, word) items; all
-// loads of a group are issued before its ballots
+// k_iso_bits: rows whose length is a multiple of 4 floats (and a 16-byte
+// aligned field) take 16-byte loads -- lane l holds columns 4l .. 4l+3 of a
+// 128-column chunk, eight lanes build one word from their 4-bit nibbles --
+// other rows one float per lane.  A warp takes U consecutive items (chunks
+// or words) per step and issues all their loads before any comparison.
 // ---------------------------------------------------------------------------
+template <bool VEC>
 __global__ void __launch_bounds__(INT) k_iso_bits(IsoGrid G, IsoWork W) {
-    constexpr int U = 8;
-    const long long items = G.rows * G.W;
+    constexpr int U = VEC ? 4 : 8;
+    const int per_row = VEC ? (G.nx + 127) / 128 : G.W;   // items per row
+    const long long items = G.rows * per_row;
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * INT) >> 5;
     bool bad = false;
     for (long long it0 = (((long long)blockIdx.x * INT + threadIdx.x) >> 5) * U; it0 < items; it0 += nwarps * U) {
-        long long row = it0 / G.W;
-        int k = (int)(it0 - row * G.W);
-        float v[U];
-        bool in[U];
+        long long row = iso_div(G, it0, VEC ? G.dVC : G.dW, per_row);
+        int k = (int)(it0 - row * per_row);
+        if (VEC) {
+            float4 v[U];
+            bool in[U];
+            long long rw[U];
+            int kk[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int x = k * 32 + lane;
-            in[u] = it0 + u < items && x < G.nx;
-            v[u] = in[u] ? __ldg(G.f + row * G.nx + x) : 0.0f;
-            if (++k == G.W) {
-                k = 0;
-                ++row;
+            for (int u = 0; u < U; ++u) {
+                const int x = k * 128 + lane * 4;
+                in[u] = it0 + u < items && x < G.nx;
+                v[u] = in[u] ? __ldg(reinterpret_cast<const float4 *>(G.f + row * G.nx + x)) : make_float4(0, 0, 0, 0);
+                rw[u] = row;
+                kk[u] = k;
+                if (++k == per_row) {
+                    k = 0;
+                    ++row;
+                }
             }
-        }
-        uint32_t mine = 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            bad |= in[u] && !(fabsf(v[u]) <= FLT_MAX);
-            const uint32_t w = __ballot_sync(ALL, in[u] && v[u] >= G.c_up);
-            if (lane == u) mine = w;
+            for (int u = 0; u < U; ++u) {
+                const float4 a = v[u];
+                bad |= in[u] && !(fabsf(a.x) <= FLT_MAX && fabsf(a.y) <= FLT_MAX && fabsf(a.z) <= FLT_MAX &&
+                                  fabsf(a.w) <= FLT_MAX);
+                uint32_t w = 0;
+                if (in[u])
+                    w = ((a.x >= G.c_up) | (a.y >= G.c_up) << 1 | (a.z >= G.c_up) << 2 | (a.w >= G.c_up) << 3)
+                        << (4 * (lane & 7));
+                w |= __shfl_xor_sync(ALL, w, 1);
+                w |= __shfl_xor_sync(ALL, w, 2);
+                w |= __shfl_xor_sync(ALL, w, 4);
+                const int word = kk[u] * 4 + (lane >> 3);
+                if ((lane & 7) == 0 && it0 + u < items && word < G.W) W.bits[rw[u] * G.W + word] = w;
+            }
+        } else {
+            float v[U];
+            bool in[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int x = k * 32 + lane;
+                in[u] = it0 + u < items && x < G.nx;
+                v[u] = in[u] ? __ldg(G.f + row * G.nx + x) : 0.0f;
+                if (++k == per_row) {
+                    k = 0;
+                    ++row;
+                }
+            }
+            uint32_t mine = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                bad |= in[u] && !(fabsf(v[u]) <= FLT_MAX);
+                const uint32_t w = __ballot_sync(ALL, in[u] && v[u] >= G.c_up);
+                if (lane == u) mine = w;
+            }
+            if (lane < U && it0 + lane < items) W.bits[it0 + lane] = mine;
         }
-        if (lane < U && it0 + lane < items) W.bits[it0 + lane] = mine;
     }
     if (__any_sync(ALL, bad) && lane == 0) atomicOr(&W.ctr->status, IST_RANGE);
 }
@@ -203,9 +290,9 @@ __device__ __forceinline__ void iso_item_words(const IsoGrid &G, const uint32_t 
                                                uint32_t (&X)[(1 << (N + 1)) - 1]) {
     constexpr int D = N + 1, E = (1 << D) - 1;
     const long long ny = G.ny, nz = G.nz;
-    const long long t = row / (ny * nz);
+    const long long t = iso_div(G, row, G.dYZ, ny * nz);
     const long long rz = row - t * ny * nz;
-    const int z = (int)(rz / ny), y = (int)(rz - (long long)z * ny);
+    const int z = (int)iso_div(G, rz, G.dY, ny), y = (int)(rz - (long long)z * ny);
     const int x0 = 32 * k;
     // columns that can step +x, and columns inside the grid
     const int lx = G.nx - 1 - x0, lin = G.nx - x0;
@@ -230,6 +317,21 @@ __device__ __forceinline__ void iso_item_words(const IsoGrid &G, const uint32_t 
             X[m - 1] = (A ^ B) & vin;
         }
     }
+}
+
+// index (from 0) of the n-th set bit of m; n < popc(m)
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
+    int p = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (n >= c) {
+            n -= c;
+            m >>= w;
+            p += w;
+        }
+    }
+    return p;
 }
 
 // block-wide exclusive scan of unsigned 64-bit values
@@ -308,6 +410,10 @@ __global__ void __launch_bounds__(INT) k_iso_emit(IsoGrid G, IsoWork W) {
     constexpr int D = N + 1, E = (1 << D) - 1;
     __shared__ unsigned long long red[INT / 32 + 1];
     __shared__ unsigned long long sh[2];
+    __shared__ uint32_t sX[E][INT];
+    __shared__ uint32_t s_own[INT];
+    __shared__ int s_wex[INT];
+    __shared__ long long s_e0[INT], s_o0[INT], s_g0[INT];
     const long long items = G.rows * G.W;
     const long long ntiles = (items + INT - 1) / INT;
     unsigned *status = &W.ctr->status;
@@ -322,7 +428,7 @@ __global__ void __launch_bounds__(INT) k_iso_emit(IsoGrid G, IsoWork W) {
         long long row = 0;
         int k = 0;
         if (have) {
-            row = it / G.W;
+            row = iso_div(G, it, G.dW, G.W);
             k = (int)(it - row * G.W);
             iso_item_words<N>(G, W.bits, row, k, X);
         } else {
@@ -358,36 +464,64 @@ __global__ void __launch_bounds__(INT) k_iso_emit(IsoGrid G, IsoWork W) {
             W.obits[it] = own;
             W.item_own[it] = (int)o0;
         }
-        if (have && own) {
-            const bool fits = e0 + ne <= W.cap && o0 + no <= W.ocap;
-            if (!fits) atomicOr(status, IST_OVERFLOW);
-            const long long g0 = row * G.nx + 32 * k;
-            uint32_t rest = own;
-            while (fits && rest) {
-                const int b = __ffs(rest) - 1;
-                rest &= rest - 1;
-                const long long g = g0 + b;
-                const float w0 = iso_w(__ldg(G.f + g), G.c_hi, G.c_lo);
-                uint32_t mask = 0;
-                const long long first = e0;
+        // the block's owners (vertices with an intersected edge of their
+        // own) are handed out one per thread, in order: the item of owner j
+        // is found among the items' exclusive owner counts, its vertex is
+        // the rank-th set bit of the item's owner word, its first edge
+        // follows the item's edges of the vertices left of it
 #pragma unroll
-                for (int m = 1; m <= E; ++m) {
-                    if (!((X[m - 1] >> b) & 1u)) continue;
-                    mask |= 1u << (m - 1);
-                    const float w1 = iso_w(__ldg(G.f + g + iso_step<N>(G, m)), G.c_hi, G.c_lo);
-                    const float den = w0 - w1;
-                    float mu = den != 0.0f ? w0 / den : 0.0f;
-                    mu = fminf(fmaxf(mu, 0.0f), 1.0f);
-                    W.id[e0] = g * E + (m - 1);
-                    W.off[e0] = make_float4((m & 1) ? mu : 0.0f, ((m >> 1) & 1) ? mu : 0.0f,
-                                            N == 3 && ((m >> 2) & 1) ? mu : 0.0f, ((m >> N) & 1) ? mu : 0.0f);
-                    W.parent[e0] = (int)e0;
-                    ++e0;
-                }
-                W.own_g[o0] = g;
-                W.own_first[o0] = (int)first;
-                W.own_mask[o0] = (uint16_t)mask;
-                ++o0;
+        for (int m = 0; m < E; ++m) sX[m][threadIdx.x] = X[m];
+        s_own[threadIdx.x] = own;
+        s_e0[threadIdx.x] = e0;
+        s_o0[threadIdx.x] = o0;
+        s_g0[threadIdx.x] = row * G.nx + 32 * k;
+        s_wex[threadIdx.x] = (int)(ex >> 31);   // owners of the tile before the item
+        __syncthreads();
+        const int btot = (int)(tot >> 31);
+        for (int j = threadIdx.x; j < btot; j += INT) {
+            int lo = 0, hi = INT - 1;   // last item whose exclusive count is <= j
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_wex[mid] <= j) lo = mid;
+                else hi = mid - 1;
+            }
+            const int src = lo;
+            const int r = j - s_wex[src];
+            const uint32_t ow = s_own[src];
+            const int b = nth_set_bit(ow, r);
+            const uint32_t below = (1u << b) - 1u;
+            uint32_t mask = 0;
+            int pre = 0;
+#pragma unroll
+            for (int m = 1; m <= E; ++m) {
+                const uint32_t xm = sX[m - 1][src];
+                pre += __popc(xm & below);
+                mask |= ((xm >> b) & 1u) << (m - 1);
+            }
+            long long e = s_e0[src] + pre;
+            const long long oi = s_o0[src] + r;
+            if (e + __popc(mask) > W.cap || oi >= W.ocap) {
+                atomicOr(status, IST_OVERFLOW);
+                continue;
+            }
+            const long long g = s_g0[src] + b;
+            const float w0 = iso_w(__ldg(G.f + g), G.c_hi, G.c_lo);
+            W.own_g[oi] = g;
+            W.own_first[oi] = (int)e;
+            W.own_mask[oi] = (uint16_t)mask;
+#pragma unroll
+            for (int m = 1; m <= E; ++m) {
+                if (!((mask >> (m - 1)) & 1u)) continue;
+                const float w1 = iso_w(__ldg(G.f + g + iso_step<N>(G, m)), G.c_hi, G.c_lo);
+                const float den = w0 - w1;
+                float mu = den != 0.0f ? w0 / den : 0.0f;
+                mu = fminf(fmaxf(mu, 0.0f), 1.0f);
+                W.id[e] = g * E + (m - 1);
+                W.off[e] = make_float4((m & 1) ? mu : 0.0f, ((m >> 1) & 1) ? mu : 0.0f,
+                                       N == 3 && ((m >> 2) & 1) ? mu : 0.0f, ((m >> N) & 1) ? mu : 0.0f);
+                W.parent[e] = (int)e;
+                W.edge_rep[e] = (int)e;
+                ++e;
             }
         }
         __syncthreads();
@@ -406,127 +540,329 @@ __device__ __forceinline__ int iso_find(int *parent, int x, unsigned *status) {
     return x;
 }
 
-__device__ __forceinline__ void iso_unite(int *parent, int a, int b, unsigned *status) {
+// unites x with the tree whose root was `root` (possibly stale); returns the
+// root of the union (the smaller of the two roots)
+__device__ __forceinline__ int iso_unite_root(int *parent, int x, int root, unsigned *status) {
+    int a = iso_find(parent, x, status);
+    int b = iso_find(parent, root, status);
     for (int it = 0; it < ISO_UF_LIMIT; ++it) {
-        a = iso_find(parent, a, status);
-        b = iso_find(parent, b, status);
-        if (a == b) return;
+        if (a == b) return a;
         if (a < b) { const int t = a; a = b; b = t; }
-        // the larger root under the smaller: roots stay component minima
         const int old = atomicCAS(&parent[a], a, b);
-        if (old == a) return;
-        a = old;
+        if (old == a) return b;
+        a = iso_find(parent, old, status);
+        b = iso_find(parent, b, status);
     }
     atomicOr(status, IST_TIMEOUT);
+    return b;
 }
 
-// ---------------------------------------------------------------------------
-// k_iso_link: one thread per owner whose unit cube lies in the grid
-// ---------------------------------------------------------------------------
+// Cube of owner s: coordinates of its base vertex, whether the unit cube lies
+// in the grid, and the axes along which it is the last cube (ub)
+struct IsoCube {
+    long long row;
+    int x, y, z, t;
+    bool inside;
+    int ub;
+};
 template <int N>
-__global__ void __launch_bounds__(INT) k_iso_link(IsoGrid G, IsoWork W) {
+__device__ __forceinline__ IsoCube iso_cube(const IsoGrid &G, long long g) {
+    IsoCube q;
+    q.row = iso_div(G, g, G.dX, G.nx);
+    q.x = (int)(g - q.row * G.nx);
+    const long long t = iso_div(G, q.row, G.dYZ, (long long)G.ny * G.nz);
+    const long long rz = q.row - t * G.ny * G.nz;
+    q.z = (int)iso_div(G, rz, G.dY, G.ny);
+    q.y = (int)(rz - (long long)q.z * G.ny);
+    q.t = (int)t;
+    q.inside = q.x + 1 < G.nx && q.y + 1 < G.ny && (N != 3 || q.z + 1 < G.nz) && q.t + 1 < G.nt;
+    q.ub = (q.x + 2 == G.nx ? 1 : 0) | (q.y + 2 == G.ny ? 2 : 0) | (N == 3 && q.z + 2 == G.nz ? 4 : 0) |
+           (q.t + 2 == G.nt ? 1 << N : 0);
+    return q;
+}
+
+// above bits of the cube's corners (bit a = corner a, a = axis mask)
+template <int N>
+__device__ __forceinline__ uint32_t iso_corners(const IsoGrid &G, const uint32_t *bits, const IsoCube &q) {
+    constexpr int NC = 1 << (N + 1);
+    uint32_t cb = 0;
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        const long long r2 = q.row + iso_row_step<N>(G, a);
+        const int xa = q.x + (a & 1);
+        cb |= ((bits[r2 * G.W + (xa >> 5)] >> (xa & 31)) & 1u) << a;
+    }
+    return cb;
+}
+
+// owner index of vertex (row, x): the item's owners before it plus the
+// owners among the item's vertices left of it
+__device__ __forceinline__ long long iso_owner(const IsoGrid &G, const IsoWork &W, long long row, int x) {
+    const long long item = row * G.W + (x >> 5);
+    return W.item_own[item] + __popc(W.obits[item] & ((1u << (x & 31)) - 1u));
+}
+
+// Cell pass, first kernel: one thread per owner whose unit cube lies in the
+// grid.  Each cell of the cube intersects a set of the cube's edge slots
+// (read from a table by the cell's above/below pattern); sets that overlap
+// belong to one local piece, so the pieces are the unions of overlapping
+// cell sets (kept as up to four disjoint slot masks).  Each piece is
+// represented by its smallest edge index.  A cube with one piece (nearly
+// every cube) stores that representative; a cube with several unites each
+// edge with its piece's representative in the global union-find and stores
+// -1 (more than four pieces: every cell's edges are united directly).  Every
+// edge whose home cube this is -- the cube based at its lower vertex, or the
+// last cube along an axis where that vertex is on the grid's upper face --
+// records the representative of its piece.
+template <int N>
+__global__ void __launch_bounds__(INT, 2) k_iso_pieces(IsoGrid G, IsoWork W) {
     using Tb = IsoTables<N>;
-    constexpr int D = N + 1, NC = 1 << D, NS = Tb::NS, NCELL = Tb::NCELL;
-    __shared__ uint8_t s_slot[NC][NC];
+    using Cm = IsoCellMasks<N>;
+    constexpr int D = N + 1, NC = 1 << D, NS = Tb::NS, NCELL = Tb::NCELL, NP = Cm::NP;
+    constexpr int K = 4;   // local pieces kept as masks
     __shared__ uint8_t s_sa[NS], s_sb[NS];
     __shared__ uint8_t s_chain[NCELL][D + 1];
-    __shared__ uint8_t lp[NS][INT];   // per-thread local union-find over the cube's edge slots
-    for (int i = threadIdx.x; i < NC * NC; i += INT) s_slot[i / NC][i % NC] = iso_tables<N>().slot[i / NC][i % NC];
+    __shared__ uint64_t s_lo[NCELL][NP];
+    __shared__ uint32_t s_hi[NCELL][NP];
+    __shared__ int s_cf[NC][INT];        // per thread: first edge of each corner's owner
+    __shared__ uint16_t s_cm[NC][INT];   // and its edge mask
+    const int me = threadIdx.x;
     for (int i = threadIdx.x; i < NS; i += INT) {
         s_sa[i] = iso_tables<N>().sa[i];
         s_sb[i] = iso_tables<N>().sb[i];
     }
     for (int i = threadIdx.x; i < NCELL * (D + 1); i += INT)
         s_chain[i / (D + 1)][i % (D + 1)] = iso_tables<N>().chain[i / (D + 1)][i % (D + 1)];
+    for (int i = threadIdx.x; i < NCELL * NP; i += INT) {
+        s_lo[i / NP][i % NP] = iso_cell_masks<N>().lo[i / NP][i % NP];
+        s_hi[i / NP][i % NP] = iso_cell_masks<N>().hi[i / NP][i % NP];
+    }
     __syncthreads();
     if (W.ctr->status & (IST_OVERFLOW | IST_RANGE | IST_BIG)) return;
     const long long no = W.ctr->owners;
     unsigned *status = &W.ctr->status;
-    const int me = threadIdx.x;
     for (long long s = blockIdx.x * (long long)INT + threadIdx.x; s < no; s += (long long)gridDim.x * INT) {
-        const long long g = W.own_g[s];
-        const long long row = g / G.nx;
-        const int x = (int)(g - row * G.nx);
-        const long long t = row / ((long long)G.ny * G.nz);
-        const long long rz = row - t * G.ny * G.nz;
-        const int z = (int)(rz / G.ny), y = (int)(rz - (long long)z * G.ny);
-        if (x + 1 >= G.nx || y + 1 >= G.ny || (N == 3 && z + 1 >= G.nz) || t + 1 >= G.nt) continue;
-        // above bits of the cube's corners (corner index = axis mask)
-        uint32_t cb = 0;
-#pragma unroll
-        for (int a = 0; a < NC; ++a) {
-            const long long r2 = row + iso_row_step<N>(G, a);
-            const int xa = x + (a & 1);
-            cb |= ((W.bits[r2 * G.W + (xa >> 5)] >> (xa & 31)) & 1u) << a;
-        }
-        // local union-find over the intersected edge slots, through the cells
-        uint64_t hit_lo = 0;   // slots 0-63
-        uint32_t hit_hi = 0;   // slot 64 (3D)
+        const IsoCube q = iso_cube<N>(G, W.own_g[s]);
+        if (!q.inside) continue;
+        const uint32_t cb = iso_corners<N>(G, W.bits, q);
+        W.own_cb[s] = (uint16_t)cb;
+        uint64_t clo[K] = {};
+        uint32_t chi[K] = {};
+        bool used[K] = {};
+        bool many = false;
+        uint64_t hlo = 0;   // every intersected slot
+        uint32_t hhi = 0;
 #pragma unroll 1
         for (int p = 0; p < NCELL; ++p) {
-            int c[D + 1];
-            uint32_t cm = 0;
+            int pat = 0;
 #pragma unroll
-            for (int q = 0; q <= D; ++q) {
-                c[q] = s_chain[p][q];
-                cm |= 1u << c[q];
-            }
-            const uint32_t up = cb & cm;
-            if (up == 0 || up == cm) continue;
-            int first = -1;
+            for (int k = 0; k <= D; ++k) pat |= ((cb >> s_chain[p][k]) & 1) << k;
+            if (pat == 0 || pat == NP - 1) continue;
+            const uint64_t slo = s_lo[p][pat];
+            const uint32_t shi = s_hi[p][pat];
+            hlo |= slo;
+            hhi |= shi;
+            // merge every piece the cell's set touches into the first such
+            int tgt = -1;
 #pragma unroll
-            for (int i = 0; i <= D; ++i)
-#pragma unroll
-                for (int j = i + 1; j <= D; ++j) {
-                    if (((cb >> c[i]) ^ (cb >> c[j])) & 1u) {
-                        const int sl = s_slot[c[i]][c[j]];
-                        const bool seen = sl < 64 ? (hit_lo >> sl) & 1ull : hit_hi & 1u;
-                        if (!seen) {
-                            lp[sl][me] = (uint8_t)sl;
-                            if (sl < 64) hit_lo |= 1ull << sl;
-                            else hit_hi |= 1u;
-                        }
-                        if (first < 0) {
-                            first = sl;
-                        } else {
-                            // local union: the larger root under the smaller
-                            int ra = first, rb = sl;
-                            while (lp[ra][me] != ra) ra = lp[ra][me];
-                            while (lp[rb][me] != rb) rb = lp[rb][me];
-                            if (ra != rb) {
-                                if (ra < rb) lp[rb][me] = (uint8_t)ra;
-                                else lp[ra][me] = (uint8_t)rb;
-                            }
-                        }
-                    }
+            for (int c = 0; c < K; ++c) {
+                if (!used[c] || !((clo[c] & slo) | (chi[c] & shi))) continue;
+                if (tgt < 0) {
+                    tgt = c;
+                    clo[c] |= slo;
+                    chi[c] |= shi;
                 }
-        }
-        // one global union per edge of each local piece, with its local root;
-        // edge indices through the owner lists of the edges' lower corners
-        int cfirst[NC];
-        uint32_t cmask[NC];
-        uint32_t have = 0;
-        auto gidx = [&](int sl) -> int {
-            const int a = s_sa[sl], b = s_sb[sl];
-            if (!((have >> a) & 1u)) {
-                const long long r2 = row + iso_row_step<N>(G, a);
-                const int xa = x + (a & 1);
-                const long long item = r2 * G.W + (xa >> 5);
-                const int bit = xa & 31;
-                const long long o = W.item_own[item] + __popc(W.obits[item] & ((1u << bit) - 1u));
-                cfirst[a] = W.own_first[o];
-                cmask[a] = W.own_mask[o];
-                have |= 1u << a;
             }
-            const int m = a ^ b;
-            return cfirst[a] + __popc(cmask[a] & ((1u << (m - 1)) - 1u));
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                if (!used[c] || c == tgt || !((clo[c] & slo) | (chi[c] & shi))) continue;
+#pragma unroll
+                for (int d = 0; d < K; ++d)
+                    if (d == tgt) {
+                        clo[d] |= clo[c];
+                        chi[d] |= chi[c];
+                    }
+                used[c] = false;
+            }
+            if (tgt < 0) {
+                bool placed = false;
+#pragma unroll
+                for (int c = 0; c < K; ++c)
+                    if (!used[c] && !placed) {
+                        used[c] = true;
+                        clo[c] = slo;
+                        chi[c] = shi;
+                        placed = true;
+                    }
+                many |= !placed;
+            }
+        }
+        int npieces = 0;
+#pragma unroll
+        for (int c = 0; c < K; ++c) npieces += used[c];
+        // edge indices through the owner lists of the edges' lower corners,
+        // looked up for every such corner at once
+        uint32_t need = 0;
+        for (uint64_t r = hlo; r; r &= r - 1) need |= 1u << s_sa[__ffsll((long long)r) - 1];
+        if (hhi) need |= 1u << s_sa[64];
+        int cbase[NC];
+        uint32_t cob[NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            if (!((need >> a) & 1u)) continue;
+            const int xa = q.x + (a & 1);
+            const long long item = (q.row + iso_row_step<N>(G, a)) * G.W + (xa >> 5);
+            cob[a] = W.obits[item] & ((1u << (xa & 31)) - 1u);
+            cbase[a] = W.item_own[item];
+        }
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            if (!((need >> a) & 1u)) continue;
+            const long long o = cbase[a] + __popc(cob[a]);
+            s_cf[a][me] = W.own_first[o];
+            s_cm[a][me] = W.own_mask[o];
+        }
+        auto gidx = [&](int sl) -> int {
+            const int a = s_sa[sl], m = a ^ s_sb[sl];
+            return s_cf[a][me] + __popc((uint32_t)s_cm[a][me] & ((1u << (m - 1)) - 1u));
         };
-        for (int sl = 0; sl < NS; ++sl) {
-            const bool hit = sl < 64 ? (hit_lo >> sl) & 1ull : hit_hi & 1u;
-            if (!hit) continue;
-            int r = sl;
-            while (lp[r][me] != r) r = lp[r][me];
-            if (r != sl) iso_unite(W.parent, gidx(sl), gidx(r), status);
+        auto home = [&](int sl) -> bool { return !(s_sa[sl] & ~q.ub); };
+        if (many) {
+            // more local pieces than masks kept: every cell's edges united
+            // directly; each edge represents itself
+            W.own_rep[s] = -1;
+#pragma unroll 1
+            for (int p = 0; p < NCELL; ++p) {
+                int pat = 0;
+#pragma unroll
+                for (int k = 0; k <= D; ++k) pat |= ((cb >> s_chain[p][k]) & 1) << k;
+                if (pat == 0 || pat == NP - 1) continue;
+                uint64_t slo = s_lo[p][pat];
+                int first = -1;
+                for (; slo; slo &= slo - 1) {
+                    const int gi = gidx(__ffsll((long long)slo) - 1);
+                    if (first < 0) first = gi;
+                    else iso_unite_root(W.parent, gi, first, status);
+                }
+                if (s_hi[p][pat]) {
+                    const int gi = gidx(64);
+                    if (first >= 0) iso_unite_root(W.parent, gi, first, status);
+                }
+            }
+            for (uint64_t r = hlo; r; r &= r - 1) {
+                const int sl = __ffsll((long long)r) - 1;
+                if (home(sl)) W.edge_rep[gidx(sl)] = gidx(sl);
+            }
+            if (hhi && home(64)) W.edge_rep[gidx(64)] = gidx(64);
+            continue;
+        }
+        if (npieces == 1) {
+            int rep = INT32_MAX;
+            for (uint64_t r = hlo; r; r &= r - 1) rep = min(rep, gidx(__ffsll((long long)r) - 1));
+            if (hhi) rep = min(rep, gidx(64));
+            W.own_rep[s] = rep;
+            for (uint64_t r = hlo; r; r &= r - 1) {
+                const int sl = __ffsll((long long)r) - 1;
+                if (home(sl)) W.edge_rep[gidx(sl)] = rep;
+            }
+            if (hhi && home(64)) W.edge_rep[gidx(64)] = rep;
+            continue;
+        }
+        // several pieces: the smallest edge index of each, then every edge
+        // united with it
+        W.own_rep[s] = -1;
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            if (!used[c]) continue;
+            int rep = INT32_MAX;
+            for (uint64_t r = clo[c]; r; r &= r - 1) rep = min(rep, gidx(__ffsll((long long)r) - 1));
+            if (chi[c]) rep = min(rep, gidx(64));
+            for (uint64_t r = clo[c]; r; r &= r - 1) {
+                const int sl = __ffsll((long long)r) - 1;
+                const int gi = gidx(sl);
+                if (gi != rep) iso_unite_root(W.parent, gi, rep, status);
+                if (home(sl)) W.edge_rep[gi] = rep;
+            }
+            if (chi[c]) {
+                const int gi = gidx(64);
+                if (gi != rep) iso_unite_root(W.parent, gi, rep, status);
+                if (home(64)) W.edge_rep[gi] = rep;
+            }
+        }
+    }
+}
+
+// Cell pass, second kernel: one thread per owner whose cube lies in the
+// grid.  For each axis a with a next cube along a, if the common face has
+// intersected edges the two cubes' pieces through them are joined: two
+// one-piece cubes unite their representatives; a one-piece cube and a
+// several-piece cube unite the representative with each shared intersected
+// edge (the other cube has united those with its own pieces).  The cubes
+// holding any one edge are joined face to face through cubes that all hold
+// it, so this connects every pair of pieces that share an edge.
+template <int N>
+__global__ void __launch_bounds__(INT) k_iso_join(IsoGrid G, IsoWork W) {
+    using Tb = IsoTables<N>;
+    constexpr int D = N + 1, NC = 1 << D, NS = Tb::NS;
+    __shared__ uint8_t s_sa[NS], s_sb[NS];
+    for (int i = threadIdx.x; i < NS; i += INT) {
+        s_sa[i] = iso_tables<N>().sa[i];
+        s_sb[i] = iso_tables<N>().sb[i];
+    }
+    __syncthreads();
+    if (W.ctr->status & (IST_OVERFLOW | IST_RANGE | IST_BIG)) return;
+    const long long no = W.ctr->owners;
+    unsigned *status = &W.ctr->status;
+    for (long long s = blockIdx.x * (long long)INT + threadIdx.x; s < no; s += (long long)gridDim.x * INT) {
+        const IsoCube q = iso_cube<N>(G, W.own_g[s]);
+        if (!q.inside) continue;
+        const uint32_t cb = W.own_cb[s];
+        const int rep = W.own_rep[s];
+        int cur = rep;   // root of rep's tree after the unions so far
+        // the next cube along each axis whose common face has an intersected
+        // edge (its base vertex then owns one): all looked up at once
+        uint32_t act = 0;
+        int rep2s[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            uint32_t fm = 0;                          // corners on the face x_a = +1
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if ((c >> a) & 1) fm |= 1u << c;
+            const uint32_t fc = cb & fm;
+            if (!((q.ub >> a) & 1) && fc != 0 && fc != fm) act |= 1u << a;
+        }
+        long long nown[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if ((act >> a) & 1) nown[a] = iso_owner(G, W, q.row + iso_row_step<N>(G, 1 << a), q.x + (a == 0));
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if ((act >> a) & 1) rep2s[a] = W.own_rep[nown[a]];
+#pragma unroll 1
+        for (int a = 0; a < D; ++a) {
+            if (!((act >> a) & 1)) continue;
+            int rep2 = 0;
+#pragma unroll
+            for (int b = 0; b < D; ++b)
+                if (b == a) rep2 = rep2s[b];
+            if (rep >= 0 && rep2 >= 0) {
+                cur = iso_unite_root(W.parent, rep2, cur, status);
+                continue;
+            }
+            if (rep < 0 && rep2 < 0) continue;
+            // one side has several pieces: unite the other side's
+            // representative with every intersected edge of the face
+            const int one = rep >= 0 ? rep : rep2;
+            for (int sl = 0; sl < NS; ++sl) {
+                const int ca = s_sa[sl], cbb = s_sb[sl];
+                if (!((ca >> a) & 1) || !(((cb >> ca) ^ (cb >> cbb)) & 1u)) continue;   // sb has bit a too
+                const int xa = q.x + (ca & 1);
+                const long long o = iso_owner(G, W, q.row + iso_row_step<N>(G, ca), xa);
+                const int m = ca ^ cbb;
+                const int e = W.own_first[o] + __popc((uint32_t)W.own_mask[o] & ((1u << (m - 1)) - 1u));
+                iso_unite_root(W.parent, e, one, status);
+            }
         }
     }
 }
@@ -538,35 +874,53 @@ __global__ void __launch_bounds__(INT) k_iso_link(IsoGrid G, IsoWork W) {
 template <int N>
 __global__ void __launch_bounds__(INT) k_iso_label(IsoGrid G, IsoWork W) {
     constexpr int D = N + 1, E = (1 << D) - 1;
+    // a block's records are built in shared memory and stored as one
+    // contiguous run of 16-byte words (INT records of 56 bytes start on a
+    // 16-byte boundary)
+    static_assert(sizeof(ftk_iso_point) == 56 && (INT * sizeof(ftk_iso_point)) % 16 == 0, "record layout");
+    __shared__ __align__(16) ftk_iso_point recs[INT];
     if (W.ctr->status & (IST_OVERFLOW | IST_RANGE | IST_BIG)) return;
     const long long P = W.ctr->edges;
     unsigned *status = &W.ctr->status;
-    for (long long i = blockIdx.x * (long long)INT + threadIdx.x; i < P; i += (long long)gridDim.x * INT) {
-        const int r = iso_find(W.parent, (int)i, status);
-        const long long id = W.id[i];
-        const long long g = id / E;
-        const int m = (int)(id - g * E) + 1;
-        const long long row = g / G.nx;
-        const int x = (int)(g - row * G.nx);
-        const long long tt = row / ((long long)G.ny * G.nz);
-        const long long rz = row - tt * G.ny * G.nz;
-        const int z = (int)(rz / G.ny), y = (int)(rz - (long long)z * G.ny);
-        ftk_iso_point p;
-        p.edge_id = id;
-        p.label = W.id[r];
-        p.base[0] = x;
-        p.base[1] = y;
-        p.base[2] = z;
-        p.base[3] = (int)tt;
-        const float4 o = W.off[i];
-        p.off[0] = o.x;
-        p.off[1] = o.y;
-        p.off[2] = o.z;
-        p.off[3] = o.w;
-        p.ordinal = ((m >> N) & 1) ? 0 : 1;
-        p.ndim = (uint8_t)N;
-        for (int q = 0; q < 6; ++q) p.reserved[q] = 0;
-        W.rec[i] = p;
+    for (long long i0 = blockIdx.x * (long long)INT; i0 < P; i0 += (long long)gridDim.x * INT) {
+        const long long i = i0 + threadIdx.x;
+        if (i < P) {
+            const int r = iso_find(W.parent, W.edge_rep[i], status);
+            const long long id = W.id[i];
+            const long long g = iso_div(G, id, G.dE, E);
+            const int m = (int)(id - g * E) + 1;
+            const long long row = iso_div(G, g, G.dX, G.nx);
+            const int x = (int)(g - row * G.nx);
+            const long long tt = iso_div(G, row, G.dYZ, (long long)G.ny * G.nz);
+            const long long rz = row - tt * G.ny * G.nz;
+            const int z = (int)iso_div(G, rz, G.dY, G.ny), y = (int)(rz - (long long)z * G.ny);
+            ftk_iso_point &p = recs[threadIdx.x];
+            p.edge_id = id;
+            p.label = W.id[r];
+            p.base[0] = x;
+            p.base[1] = y;
+            p.base[2] = z;
+            p.base[3] = (int)tt;
+            const float4 o = W.off[i];
+            p.off[0] = o.x;
+            p.off[1] = o.y;
+            p.off[2] = o.z;
+            p.off[3] = o.w;
+            p.ordinal = ((m >> N) & 1) ? 0 : 1;
+            p.ndim = (uint8_t)N;
+            for (int q = 0; q < 6; ++q) p.reserved[q] = 0;
+        }
+        __syncthreads();
+        const long long n = P - i0 < INT ? P - i0 : INT;
+        const int nbytes = (int)n * (int)sizeof(ftk_iso_point);
+        const uint4 *src = reinterpret_cast<const uint4 *>(recs);
+        uint4 *dst = reinterpret_cast<uint4 *>(W.rec + i0);
+        for (int k = threadIdx.x; k < nbytes / 16; k += INT) dst[k] = src[k];
+        if ((nbytes & 15) && threadIdx.x == 0) {   // odd count: the last 8 bytes
+            const int k = nbytes / 8 - 1;
+            reinterpret_cast<unsigned long long *>(W.rec + i0)[k] = reinterpret_cast<const unsigned long long *>(recs)[k];
+        }
+        __syncthreads();
     }
 }
 
@@ -613,6 +967,9 @@ void iso_free_caps(IsoWork &W) {
     cudaFree(W.own_g);
     cudaFree(W.own_first);
     cudaFree(W.own_mask);
+    cudaFree(W.own_cb);
+    cudaFree(W.own_rep);
+    cudaFree(W.edge_rep);
     cudaFree(W.id);
     cudaFree(W.off);
     cudaFree(W.parent);
@@ -620,6 +977,9 @@ void iso_free_caps(IsoWork &W) {
     W.own_g = nullptr;
     W.own_first = nullptr;
     W.own_mask = nullptr;
+    W.own_cb = nullptr;
+    W.own_rep = nullptr;
+    W.edge_rep = nullptr;
     W.id = nullptr;
     W.off = nullptr;
     W.parent = nullptr;
@@ -634,6 +994,9 @@ ftk_status iso_alloc_caps(IsoWork &W, long long cap, long long ocap) {
     if (cudaMalloc(&W.own_g, sizeof(long long) * ocap) != cudaSuccess ||
         cudaMalloc(&W.own_first, sizeof(int) * ocap) != cudaSuccess ||
         cudaMalloc(&W.own_mask, sizeof(uint16_t) * ocap) != cudaSuccess ||
+        cudaMalloc(&W.own_cb, sizeof(uint16_t) * ocap) != cudaSuccess ||
+        cudaMalloc(&W.own_rep, sizeof(int) * ocap) != cudaSuccess ||
+        cudaMalloc(&W.edge_rep, sizeof(int) * cap) != cudaSuccess ||
         cudaMalloc(&W.id, sizeof(long long) * cap) != cudaSuccess ||
         cudaMalloc(&W.off, sizeof(float4) * cap) != cudaSuccess ||
         cudaMalloc(&W.parent, sizeof(int) * cap) != cudaSuccess ||
@@ -686,9 +1049,13 @@ ftk_status iso_launch(ftk_iso_plan *pl, const float *dev_f, cudaStream_t s) {
     ISO_CUDA(cudaMemsetAsync(W.tile, 0, sizeof(unsigned long long) * (size_t)pl->ntiles, s));
     const int sms = num_sms();
     const long long items = pl->items;
-    const unsigned gb = (unsigned)std::max<long long>(1, std::min<long long>((items + 63) / 64, (long long)sms * 8));
+    // 16-byte loads when every row starts on a 16-byte boundary
+    const bool vec = pl->G.nx % 4 == 0 && (reinterpret_cast<uintptr_t>(dev_f) & 15) == 0;
+    const long long bitems = vec ? pl->G.rows * ((pl->G.nx + 127) / 128) : items;
+    const unsigned gb = (unsigned)std::max<long long>(1, std::min<long long>((bitems + 31) / 32, (long long)sms * 8));
     ISO_CUDA(cudaEventRecord(pl->ev[0], s));
-    k_iso_bits<<<gb, INT, 0, s>>>(pl->G, W);
+    if (vec) k_iso_bits<true><<<gb, INT, 0, s>>>(pl->G, W);
+    else k_iso_bits<false><<<gb, INT, 0, s>>>(pl->G, W);
     ISO_CUDA(cudaEventRecord(pl->ev[1], s));
     const unsigned ge = (unsigned)std::max<long long>(1, std::min<long long>(pl->ntiles, (long long)sms * 4));
     const unsigned gl = (unsigned)std::max<long long>(1, std::min<long long>((W.ocap + INT - 1) / INT, (long long)sms * 8));
@@ -696,13 +1063,15 @@ ftk_status iso_launch(ftk_iso_plan *pl, const float *dev_f, cudaStream_t s) {
     if (pl->ndim == 2) {
         k_iso_emit<2><<<ge, INT, 0, s>>>(pl->G, W);
         ISO_CUDA(cudaEventRecord(pl->ev[2], s));
-        k_iso_link<2><<<gl, INT, 0, s>>>(pl->G, W);
+        k_iso_pieces<2><<<gl, INT, 0, s>>>(pl->G, W);
+        k_iso_join<2><<<gl, INT, 0, s>>>(pl->G, W);
         ISO_CUDA(cudaEventRecord(pl->ev[3], s));
         k_iso_label<2><<<gL, INT, 0, s>>>(pl->G, W);
     } else {
         k_iso_emit<3><<<ge, INT, 0, s>>>(pl->G, W);
         ISO_CUDA(cudaEventRecord(pl->ev[2], s));
-        k_iso_link<3><<<gl, INT, 0, s>>>(pl->G, W);
+        k_iso_pieces<3><<<gl, INT, 0, s>>>(pl->G, W);
+        k_iso_join<3><<<gl, INT, 0, s>>>(pl->G, W);
         ISO_CUDA(cudaEventRecord(pl->ev[3], s));
         k_iso_label<3><<<gL, INT, 0, s>>>(pl->G, W);
     }
@@ -759,6 +1128,15 @@ ftk_status iso_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, 
     G.rows = (long long)nt * nz * ny;
     pl->nverts = G.rows * nx;
     pl->items = G.rows * G.W;
+    const int E = (1 << (ndim + 1)) - 1;
+    G.small = (double)pl->nverts * E < 2147483648.0 ? 1 : 0;
+    G.dW = make_fastdiv((unsigned)G.W);
+    G.dVC = make_fastdiv((unsigned)((nx + 127) / 128));
+    G.dX = make_fastdiv((unsigned)nx);
+    G.dY = make_fastdiv((unsigned)ny);
+    G.dYZ = make_fastdiv((unsigned)(ny * nz <= INT32_MAX ? ny * nz : 1));
+    G.dE = make_fastdiv((unsigned)E);
+    if (ny * nz > INT32_MAX) G.small = 0;
     pl->ntiles = (pl->items + INT - 1) / INT;
     IsoWork &W = pl->W;
     auto bad = [&](const char *what) {
