@@ -652,11 +652,12 @@ __global__ void __launch_bounds__(INT, 2) k_iso_pieces(IsoGrid G, IsoWork W) {
         bool many = false;
         uint64_t hlo = 0;   // every intersected slot
         uint32_t hhi = 0;
-#pragma unroll 1
+        constexpr Tb TT{};   // the cell chains as compile-time constants of the unrolled loop
+#pragma unroll
         for (int p = 0; p < NCELL; ++p) {
             int pat = 0;
 #pragma unroll
-            for (int k = 0; k <= D; ++k) pat |= ((cb >> s_chain[p][k]) & 1) << k;
+            for (int k = 0; k <= D; ++k) pat |= ((cb >> TT.chain[p][k]) & 1) << k;
             if (pat == 0 || pat == NP - 1) continue;
             const uint64_t slo = s_lo[p][pat];
             const uint32_t shi = s_hi[p][pat];
