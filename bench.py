@@ -168,17 +168,21 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(wl: str):
-    """DRAM bytes per detect launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None): the hash covers the
-    kernel file's device code, everything before its host-side marker."""
+def profiled_traffic(wl: str, src_file: str | None = None, name: str | None = None):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary profiles/<name>_traffic.txt, if it was taken on the current
+    kernel source (else None): the hash covers the kernel file's device code,
+    everything before its host-side marker."""
     import hashlib
-    src_file = "ftk_detect3.cu" if wl == "blobs3d" else "ftk_detect2.cu"
+    if src_file is None:
+        src_file = "ftk_detect3.cu" if wl == "blobs3d" else "ftk_detect2.cu"
+    if name is None:
+        name = f"detect_{wl}"
     src = os.path.join(ROOT, "paper_2011_08697_gb300", "csrc", src_file)
     text = open(src, "rb").read()
-    mark = text.find(b"// ---- host side: launch configuration ----")
+    mark = text.find(b"// ---- host side")
     sha = hashlib.sha256(text if mark < 0 else text[:mark]).hexdigest()[:16]
-    path = os.path.join(ROOT, "profiles", f"detect_{wl}_traffic.txt")
+    path = os.path.join(ROOT, "profiles", f"{name}_traffic.txt")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -871,7 +875,8 @@ def _measure_iso(args, dev, world):
         "ms_per_step": step_mean, "edges_per_step": edges, "intersected_edges": int(P),
         "pieces": int(len(np.unique(res["label"]))), "stages_ms": st,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_iso_bits",
+                     "frac": achieved / peak, "traffic": profiled_traffic("blobs3d", "ftk_iso.cu", "iso_bits_blobs3d"),
+                     "kernel": "k_iso_bits",
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": bits_ms,
                      "whole_step_frac": (alg_bytes / (step_mean / 1e3) / 1e9) / peak},
         "bit_exact_sample": {"ok": ok, "slices": ISO_SAMPLE_SLICES, "intersected_edges": int(len(ref["edge_id"])),

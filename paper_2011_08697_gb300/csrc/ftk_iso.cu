@@ -938,6 +938,7 @@ int num_sms() {
 }  // namespace
 }  // namespace ftk
 
+// ---- host side: plans and the C ABI ----
 using namespace ftk;
 
 struct ftk_iso_plan {
