@@ -95,6 +95,7 @@ struct IsoWork {
     uint16_t *own_cb;              // [ocap] above bits of the corners of its unit cube
     int *own_rep;                  // [ocap] representative edge of its cube's piece (-1: several pieces)
     int *edge_rep;                 // [cap] representative of each edge's piece in its home cube
+    const uint32_t *piece1;        // [2^(2^d) / 32] one-piece cube patterns (built with the plan)
     long long *id;                 // [cap] edge ids, sorted
     float4 *off;                   // [cap] crossing point - base vertex (x, y, z, t)
     int *parent;                   // [cap] union-find
@@ -113,7 +114,9 @@ struct IsoTables {
     uint8_t slot[NC][NC];
     uint8_t sa[NS], sb[NS];
     uint8_t chain[NCELL][D + 1];
-    __host__ __device__ constexpr IsoTables() : slot{}, sa{}, sb{}, chain{} {
+    uint64_t elo[NC];   // slots 0-63 incident to corner c
+    uint32_t ehi[NC];   // slot 64 (3D)
+    __host__ __device__ constexpr IsoTables() : slot{}, sa{}, sb{}, chain{}, elo{}, ehi{} {
         int s = 0;
         for (int a = 0; a < NC; ++a)
             for (int b = 0; b < NC; ++b) slot[a][b] = 255;
@@ -123,6 +126,13 @@ struct IsoTables {
                     slot[a][b] = (uint8_t)s;
                     sa[s] = (uint8_t)a;
                     sb[s] = (uint8_t)b;
+                    if (s < 64) {
+                        elo[a] |= 1ull << s;
+                        elo[b] |= 1ull << s;
+                    } else {
+                        ehi[a] |= 1u;
+                        ehi[b] |= 1u;
+                    }
                     ++s;
                 }
         int tuples = 1;
@@ -602,6 +612,94 @@ __device__ __forceinline__ long long iso_owner(const IsoGrid &G, const IsoWork &
     return W.item_own[item] + __popc(W.obits[item] & ((1u << (x & 31)) - 1u));
 }
 
+// Local pieces of a unit cube with above bits cb: the intersected slot set
+// of each cell (tables lo / hi by the cell's above/below pattern); sets that
+// overlap belong to one piece, kept as up to K disjoint slot masks (many:
+// more pieces than that); h* = every intersected slot.
+template <int N, int K = 4>
+__device__ __forceinline__ void iso_merge_cells(uint32_t cb, const uint64_t (*lo)[1 << (N + 2)],
+                                                const uint32_t (*hi)[1 << (N + 2)], uint64_t (&clo)[K],
+                                                uint32_t (&chi)[K], bool (&used)[K], bool &many, uint64_t &hlo,
+                                                uint32_t &hhi) {
+    using Tb = IsoTables<N>;
+    constexpr int D = N + 1, NCELL = Tb::NCELL, NP = 1 << (D + 1);
+    constexpr Tb TT{};   // the cell chains as compile-time constants of the unrolled loop
+#pragma unroll
+    for (int p = 0; p < NCELL; ++p) {
+        int pat = 0;
+#pragma unroll
+        for (int k = 0; k <= D; ++k) pat |= ((cb >> TT.chain[p][k]) & 1) << k;
+        if (pat == 0 || pat == NP - 1) continue;
+        const uint64_t slo = lo[p][pat];
+        const uint32_t shi = hi[p][pat];
+        hlo |= slo;
+        hhi |= shi;
+        // merge every piece the cell's set touches into the first such
+        int tgt = -1;
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            if (!used[c] || !((clo[c] & slo) | (chi[c] & shi))) continue;
+            if (tgt < 0) {
+                tgt = c;
+                clo[c] |= slo;
+                chi[c] |= shi;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            if (!used[c] || c == tgt || !((clo[c] & slo) | (chi[c] & shi))) continue;
+#pragma unroll
+            for (int d = 0; d < K; ++d)
+                if (d == tgt) {
+                    clo[d] |= clo[c];
+                    chi[d] |= chi[c];
+                }
+            used[c] = false;
+        }
+        if (tgt < 0) {
+            bool placed = false;
+#pragma unroll
+            for (int c = 0; c < K; ++c)
+                if (!used[c] && !placed) {
+                    used[c] = true;
+                    clo[c] = slo;
+                    chi[c] = shi;
+                    placed = true;
+                }
+            many |= !placed;
+        }
+    }
+}
+
+// bit cb of piece1 = a unit cube whose corners have above bits cb holds one
+// piece of the level set (one thread per pattern; 2^(2^d) patterns)
+template <int N>
+__global__ void __launch_bounds__(INT) k_iso_piece_table(uint32_t *piece1) {
+    using Cm = IsoCellMasks<N>;
+    constexpr int NCELL = IsoTables<N>::NCELL, NP = Cm::NP, NPAT = 1 << (1 << (N + 1));
+    __shared__ uint64_t s_lo[NCELL][NP];
+    __shared__ uint32_t s_hi[NCELL][NP];
+    for (int i = threadIdx.x; i < NCELL * NP; i += INT) {
+        s_lo[i / NP][i % NP] = iso_cell_masks<N>().lo[i / NP][i % NP];
+        s_hi[i / NP][i % NP] = iso_cell_masks<N>().hi[i / NP][i % NP];
+    }
+    __syncthreads();
+    const int cb = blockIdx.x * INT + threadIdx.x;
+    bool one = false;
+    if (cb < NPAT) {
+        uint64_t clo[4] = {};
+        uint32_t chi[4] = {};
+        bool used[4] = {};
+        bool many = false;
+        uint64_t hlo = 0;
+        uint32_t hhi = 0;
+        iso_merge_cells<N>((uint32_t)cb, s_lo, s_hi, clo, chi, used, many, hlo, hhi);
+        one = !many && (used[0] + used[1] + used[2] + used[3]) == 1;
+    }
+    const uint32_t w = __ballot_sync(ALL, one);
+    if ((threadIdx.x & 31) == 0 && cb < NPAT) piece1[cb >> 5] = w;
+}
+
 // Cell pass, first kernel: one thread per owner whose unit cube lies in the
 // grid.  Each cell of the cube intersects a set of the cube's edge slots
 // (read from a table by the cell's above/below pattern); sets that overlap
@@ -646,57 +744,26 @@ __global__ void __launch_bounds__(INT, 2) k_iso_pieces(IsoGrid G, IsoWork W) {
         if (!q.inside) continue;
         const uint32_t cb = iso_corners<N>(G, W.bits, q);
         W.own_cb[s] = (uint16_t)cb;
+        const bool single = (W.piece1[cb >> 5] >> (cb & 31)) & 1u;
         uint64_t clo[K] = {};
         uint32_t chi[K] = {};
         bool used[K] = {};
         bool many = false;
         uint64_t hlo = 0;   // every intersected slot
         uint32_t hhi = 0;
-        constexpr Tb TT{};   // the cell chains as compile-time constants of the unrolled loop
+        if (single) {
+            // one piece: the intersected slots are those with exactly one
+            // corner above, the XOR of the above corners' incidence masks
+            constexpr Tb TT{};
 #pragma unroll
-        for (int p = 0; p < NCELL; ++p) {
-            int pat = 0;
-#pragma unroll
-            for (int k = 0; k <= D; ++k) pat |= ((cb >> TT.chain[p][k]) & 1) << k;
-            if (pat == 0 || pat == NP - 1) continue;
-            const uint64_t slo = s_lo[p][pat];
-            const uint32_t shi = s_hi[p][pat];
-            hlo |= slo;
-            hhi |= shi;
-            // merge every piece the cell's set touches into the first such
-            int tgt = -1;
-#pragma unroll
-            for (int c = 0; c < K; ++c) {
-                if (!used[c] || !((clo[c] & slo) | (chi[c] & shi))) continue;
-                if (tgt < 0) {
-                    tgt = c;
-                    clo[c] |= slo;
-                    chi[c] |= shi;
+            for (int a = 0; a < NC; ++a)
+                if ((cb >> a) & 1u) {
+                    hlo ^= TT.elo[a];
+                    hhi ^= TT.ehi[a];
                 }
-            }
-#pragma unroll
-            for (int c = 0; c < K; ++c) {
-                if (!used[c] || c == tgt || !((clo[c] & slo) | (chi[c] & shi))) continue;
-#pragma unroll
-                for (int d = 0; d < K; ++d)
-                    if (d == tgt) {
-                        clo[d] |= clo[c];
-                        chi[d] |= chi[c];
-                    }
-                used[c] = false;
-            }
-            if (tgt < 0) {
-                bool placed = false;
-#pragma unroll
-                for (int c = 0; c < K; ++c)
-                    if (!used[c] && !placed) {
-                        used[c] = true;
-                        clo[c] = slo;
-                        chi[c] = shi;
-                        placed = true;
-                    }
-                many |= !placed;
-            }
+            used[0] = true;
+        } else {
+            iso_merge_cells<N>(cb, s_lo, s_hi, clo, chi, used, many, hlo, hhi);
         }
         int npieces = 0;
 #pragma unroll
@@ -1020,6 +1087,7 @@ void iso_destroy(ftk_iso_plan *pl) {
     cudaFree(pl->W.obits);
     cudaFree(pl->W.item_own);
     cudaFree(pl->W.tile);
+    cudaFree(const_cast<uint32_t *>(pl->W.piece1));
     cudaFree(pl->d_input);
     if (pl->h_ctr) cudaFreeHost(pl->h_ctr);
     if (pl->copy_ev) cudaEventDestroy(pl->copy_ev);
@@ -1158,6 +1226,18 @@ ftk_status iso_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t nt, 
         return bad("event creation failed");
     for (cudaEvent_t &e : pl->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return bad("event creation failed");
+    {
+        // the one-piece cube patterns, computed once for the plan
+        const int npat = 1 << (1 << (ndim + 1));
+        uint32_t *tab = nullptr;
+        if (cudaMalloc(&tab, sizeof(uint32_t) * (npat / 32)) != cudaSuccess)
+            return bad("device allocation of the piece table failed");
+        W.piece1 = tab;
+        if (ndim == 2) k_iso_piece_table<2><<<(npat + INT - 1) / INT, INT>>>(tab);
+        else k_iso_piece_table<3><<<(npat + INT - 1) / INT, INT>>>(tab);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess)
+            return bad("the piece table kernel failed");
+    }
     const long long cap0 = std::max<long long>(65536, pl->nverts / 16);
     const long long ocap0 = std::max<long long>(65536, pl->nverts / 64);
     if (iso_alloc_caps(W, cap0, ocap0) != FTK_OK) return bad("device allocation of the isovolume capacity failed");
