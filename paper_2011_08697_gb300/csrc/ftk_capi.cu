@@ -163,6 +163,8 @@ ftk_status choose_blocking(int ndim, const Field &F, Blocking &B, int &variant) 
     static const int cand2[] = {16, 8, 4, 2, 1};
     static const int cand3[][2] = {{8, 4}, {8, 2}, {4, 4}, {4, 2}, {2, 2}, {2, 1}, {1, 1}};
     const int sms = sm_count();
+    B.nxb = 1;
+    B.wx = F.nx;
     // the streaming kernels read rows padded to a multiple of 4 floats
     // (F.pitch, chosen by stream_pitch)
     if (ndim == 2 && F.comps != 2 && F.pitch % 4 == 0 && F.pitch <= STREAM2_MAX_NX) {
@@ -198,12 +200,22 @@ ftk_status choose_blocking(int ndim, const Field &F, Blocking &B, int &variant) 
             if (detect_smem_bytes(3, F, B) <= kSmemBudget) { ok = true; break; }
         }
     }
-    if (!ok) return fail(FTK_ERR_ARG, "grid rows too wide for the detect tile (nx too large)");
+    if (!ok) {
+        // rows too wide for one tile: one row (and plane) per unit, the row
+        // cut into windows of wx cube columns, the widest multiple of 32
+        // that fits; segments become (t, z, y, window), still in face-id order
+        B.ry = 1; B.rz = 1;
+        B.nxb = 2;
+        B.wx = std::min(F.nx, 1 << 16) & ~31;
+        while (B.wx >= 32 && detect_smem_bytes(ndim, F, B) > kSmemBudget) B.wx -= 32;
+        if (B.wx < 32) return fail(FTK_ERR_ARG, "no x window of the detect tile fits shared memory");
+        B.nxb = (F.nx + B.wx - 1) / B.wx;
+    }
     B.nyb = (F.ny + B.ry - 1) / B.ry;
     B.nzb = ndim == 3 ? (F.nz + B.rz - 1) / B.rz : 1;
     // enough units to fill the GPU: split time into chunks if the spatial
     // blocks alone are too few
-    const long long spatial = (long long)B.nyb * B.nzb;
+    const long long spatial = (long long)B.nyb * B.nzb * B.nxb;
     const long long want = 4LL * sms;
     long long chunks = spatial >= want ? 1 : (want + spatial - 1) / spatial;
     chunks = std::min<long long>(chunks, F.nt);
@@ -520,7 +532,7 @@ ftk_status ftk::plan_sizes(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_t
     s = choose_blocking(ndim, out->F, out->B, out->variant);
     if (s != FTK_OK) return s;
     const long long nverts = (long long)nx * ny * nz * nt;
-    out->nseg = (long long)nt * nz * out->B.nyb;
+    out->nseg = segment_count(out->F, out->B);
     out->cap = initial_cap(prm, nverts, compact);
     out->scap = out->variant != VAR_TILE ? initial_scap(nverts, compact) : 0;
     return FTK_OK;
@@ -557,7 +569,7 @@ ftk_status ftk::plan_create(int ndim, int64_t nx, int64_t ny, int64_t nz, int64_
     pl->nverts = (long long)nx * ny * nz * nt;
     s = choose_blocking(ndim, pl->F, pl->B, pl->variant);
     if (s != FTK_OK) { delete pl; return s; }
-    pl->W.nseg = (long long)nt * nz * pl->B.nyb;   // segments (t, z, y-block)
+    pl->W.nseg = segment_count(pl->F, pl->B);   // segments (t, z, y-block[, x-window])
     pl->timing = (pl->p.flags & 1u) != 0;
 
     Workspace &W = pl->W;
@@ -704,7 +716,7 @@ ftk_status ftk_plan_describe(ftk_plan *pl, ftk_plan_desc *d) {
     d->kernels_per_execute = pl->variant == VAR_TILE ? 5 : pl->ndim == 3 ? 9 : 8;
     d->rows_per_unit = pl->B.ry;
     d->slices_per_unit = pl->B.tc;
-    d->detect_units = (int64_t)pl->B.ntc * pl->B.nyb * pl->B.nzb;
+    d->detect_units = (int64_t)pl->B.ntc * pl->B.nyb * pl->B.nzb * std::max(1, pl->B.nxb);
     d->capacity = pl->W.cap;
     return FTK_OK;
 }

@@ -45,18 +45,21 @@ namespace ftk {
 
 namespace {
 
-constexpr int S3_NW = 4;                  // consumer warps
 constexpr int S3_RPW = 4;                 // G rows per consumer warp
 constexpr int S3_NS = 6;                  // smem ring slots (plane chunks)
-constexpr int S3_THREADS = (S3_NW + 2) * 32;
 constexpr float S3_RANGE = 268435456.0f;  // 2^28
 constexpr uint32_t ALL = 0xffffffffu;
 
 __host__ __device__ inline int s3_round16(int v) { return (v + 15) & ~15; }
 // 128-column chunks per row (a power of two, so that the warps split evenly)
-__host__ __device__ inline int s3_chunks(int nx) { return nx <= 128 ? 1 : nx <= 256 ? 2 : 4; }
+__host__ __device__ inline int s3_chunks(int nx) { return nx <= 128 ? 1 : nx <= 256 ? 2 : nx <= 512 ? 4 : 8; }
+// consumer warps: four, stacked in y over the chunks, or one per chunk for
+// rows of eight chunks
+__host__ __device__ constexpr int s3_nw_of(int xc) { return xc > 4 ? xc : 4; }
+__host__ __device__ inline int s3_nw(int nx) { return s3_nw_of(s3_chunks(nx)); }
+__host__ __device__ inline int s3_threads(int nx) { return (s3_nw(nx) + 2) * 32; }
 // G rows per unit: the consumer warps of one chunk stacked in y (ry + 1)
-__host__ __device__ inline int s3_grows(int nx) { return S3_NW / s3_chunks(nx) * S3_RPW; }
+__host__ __device__ inline int s3_grows(int nx) { return s3_nw(nx) / s3_chunks(nx) * S3_RPW; }
 
 struct S3Layout {
     int slot_floats, ring, bars, abort, xy, xx, ts, bm, rw, cnt, total;
@@ -71,7 +74,7 @@ __host__ __device__ inline S3Layout s3_layout(int nx, int ry, int rz) {
     L.bars = L.ring + ns * L.slot_floats * 4;
     L.abort = L.bars + (2 * ns + 4) * 8;
     L.xy = s3_round16(L.abort + 4);                // [2][warps][32] z-paired words of a warp's first G row
-    L.xx = L.xy + 2 * S3_NW * 32 * 4;              // [2][gr][xc] y-paired words of a chunk's first column
+    L.xx = L.xy + 2 * s3_nw(nx) * 32 * 4;          // [2][gr][xc] y-paired words of a chunk's first column
     L.ts = s3_round16(L.xx + 2 * gr * xc * 4);     // [rz][ry][xc][32] cube words of the previous slice
     L.bm = L.ts + rz * ry * xc * 32 * 4;
     L.rw = (ry * nx + 31) / 32;                    // bitmap words per cube plane
@@ -132,7 +135,9 @@ struct PlaneRegs {
 };
 
 template <bool EXACT, int XC>
-__global__ void __launch_bounds__(S3_THREADS, 2) k_detect3_stream(Field F, Blocking B, Workspace W) {
+__global__ void __launch_bounds__((s3_nw_of(XC) + 2) * 32, XC > 4 ? 1 : 2)
+    k_detect3_stream(Field F, Blocking B, Workspace W) {
+    constexpr int S3_NW = s3_nw_of(XC);    // consumer warps
     extern __shared__ __align__(128) unsigned char smem[];
     // the sweep covers the padded row (pitch columns, the padding repeating
     // column nx-1); survivors are the grid's (columns < nxl)
@@ -470,14 +475,15 @@ void *s3_kernel(int nx) {
     const int xc = s3_chunks(nx);
     if (xc == 1) return (void *)k_detect3_stream<EXACT, 1>;
     if (xc == 2) return (void *)k_detect3_stream<EXACT, 2>;
-    return (void *)k_detect3_stream<EXACT, 4>;
+    if (xc == 4) return (void *)k_detect3_stream<EXACT, 4>;
+    return (void *)k_detect3_stream<EXACT, 8>;
 }
 
 }  // namespace
 
 // ---- host side: launch configuration ----
 size_t stream3_smem_bytes(int nx, const Blocking &B) { return (size_t)s3_layout(nx, B.ry, B.rz).total; }
-int stream3_threads() { return S3_THREADS; }
+int stream3_threads(int nx) { return s3_threads(nx); }
 int stream3_ry(int nx) { return s3_grows(nx) - 1; }
 
 int stream3_ctas_per_sm(int nx, const Blocking &B) {
@@ -485,7 +491,7 @@ int stream3_ctas_per_sm(int nx, const Blocking &B) {
     const size_t smem = stream3_smem_bytes(nx, B);
     const void *k = s3_kernel<false>(nx);
     raise_smem_cap(k, smem, false);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, S3_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, s3_threads(nx), smem);
     return n > 0 ? n : 1;
 }
 
@@ -506,7 +512,7 @@ cudaError_t launch_detect3(int variant, const Field &F, const Blocking &B, const
     Blocking Ba = B;
     Workspace Wa = W;
     void *args[] = {&Fa, &Ba, &Wa};
-    return cudaLaunchKernel(k, dim3(units), dim3(S3_THREADS), args, smem, s);
+    return cudaLaunchKernel(k, dim3(units), dim3(s3_threads(F.pitch)), args, smem, s);
 }
 
 }  // namespace ftk

@@ -189,7 +189,9 @@ __device__ long long warp_lookback(unsigned long long *tile_state, long long t, 
 // ----------------------------------------------------------------------------
 struct TileGeom {
     int nx, ny, nz;
-    int y0, z0;
+    int x0, y0, z0;
+    int ncx, nvx;   // cubes and word columns of the unit's x window (from x0)
+    int tw, ww;     // tile and word row strides: tile column j is x0 - 1 + j, word column j is x0 + j
     int PY, PZ;     // tile rows / planes (with halo)
     int WY, WZ;     // word rows / planes
     int tile;       // ints per F tile
@@ -210,41 +212,44 @@ __device__ __forceinline__ int quantise(float f, float scale, unsigned *status) 
 template <int N>
 __device__ __forceinline__ void grad_tile(const int32_t *T, const TileGeom &g, int x, int y, int z,
                                           int ty, int tz, int32_t (&G)[N]) {
+    const int lx = x - g.x0 + 1;    // tile column of x
     if (N == 2 && g.vec) {
         // a vector field: the quantised vector itself takes the gradient's place
-        const int32_t *p = T + ((tz * g.PY + ty) * g.nx + x) * 2;
+        const int32_t *p = T + ((tz * g.PY + ty) * g.tw + lx) * 2;
         G[0] = p[0];
         G[1] = p[1];
         return;
     }
-    const int32_t *row = T + (tz * g.PY + ty) * g.nx;
-    G[0] = x == 0 ? 2 * (row[1] - row[0])
-         : x == g.nx - 1 ? 2 * (row[x] - row[x - 1])
-         : row[x + 1] - row[x - 1];
-    const int32_t *up = row + g.nx, *dn = row - g.nx;
-    G[1] = y == 0 ? 2 * (up[x] - row[x])
-         : y == g.ny - 1 ? 2 * (row[x] - dn[x])
-         : up[x] - dn[x];
+    const int32_t *row = T + (tz * g.PY + ty) * g.tw;
+    G[0] = x == 0 ? 2 * (row[lx + 1] - row[lx])
+         : x == g.nx - 1 ? 2 * (row[lx] - row[lx - 1])
+         : row[lx + 1] - row[lx - 1];
+    const int32_t *up = row + g.tw, *dn = row - g.tw;
+    G[1] = y == 0 ? 2 * (up[lx] - row[lx])
+         : y == g.ny - 1 ? 2 * (row[lx] - dn[lx])
+         : up[lx] - dn[lx];
     if (N == 3) {
-        const int ps = g.PY * g.nx;
+        const int ps = g.PY * g.tw;
         const int32_t *fw = row + ps, *bk = row - ps;
-        G[N - 1] = z == 0 ? 2 * (fw[x] - row[x])
-                 : z == g.nz - 1 ? 2 * (row[x] - bk[x])
-                 : fw[x] - bk[x];
+        G[N - 1] = z == 0 ? 2 * (fw[lx] - row[lx])
+                 : z == g.nz - 1 ? 2 * (row[lx] - bk[lx])
+                 : fw[lx] - bk[lx];
     }
 }
 
 template <int N>
 __device__ void load_tile(const Field &F, const TileGeom &g, int s, int32_t *T, unsigned *status) {
     const int rows = g.PZ * g.PY;
-    for (int i = threadIdx.x; i < rows * g.nx; i += NT) {
-        const int x = i % g.nx;
-        const int r = i / g.nx;
+    // samples of the window's cubes and their gradients' neighbours
+    const int xlo = max(g.x0 - 1, 0), xhi = min(g.nx, g.x0 + g.ncx + 2);
+    for (int i = threadIdx.x; i < rows * g.tw; i += NT) {
+        const int x = g.x0 - 1 + i % g.tw;
+        const int r = i / g.tw;
         const int ty = r % g.PY;
         const int tz = r / g.PY;
         const int y = g.y0 - 1 + ty;
         const int z = N == 3 ? g.z0 - 1 + tz : 0;
-        if (y < 0 || y >= g.ny || z < 0 || z >= g.nz) continue;
+        if (x < xlo || x >= xhi || y < 0 || y >= g.ny || z < 0 || z >= g.nz) continue;
         const long long idx = (((long long)s * g.nz + z) * g.ny + y) * F.pitch + x;
         if (N == 2 && g.vec) {
             T[2 * i] = quantise(__ldg(F.f + 2 * idx), F.scale, status);
@@ -257,9 +262,10 @@ __device__ void load_tile(const Field &F, const TileGeom &g, int s, int32_t *T, 
 
 template <int N>
 __device__ void make_words(const TileGeom &g, const int32_t *T, uint8_t *Wd) {
-    for (int i = threadIdx.x; i < g.WZ * g.WY * g.nx; i += NT) {
-        const int x = i % g.nx;
-        const int r = i / g.nx;
+    for (int i = threadIdx.x; i < g.WZ * g.WY * g.nvx; i += NT) {
+        const int j = i % g.nvx;
+        const int x = g.x0 + j;
+        const int r = i / g.nvx;
         const int wy = r % g.WY;
         const int wz = r / g.WY;
         const int y = g.y0 + wy;
@@ -270,7 +276,7 @@ __device__ void make_words(const TileGeom &g, const int32_t *T, uint8_t *Wd) {
         uint32_t w = 0;
 #pragma unroll
         for (int c = 0; c < N; ++c) w |= ((uint32_t)(G[c] < 0) << (2 * c)) | ((uint32_t)(G[c] >= 0) << (2 * c + 1));
-        Wd[i] = (uint8_t)w;
+        Wd[r * g.ww + j] = (uint8_t)w;
     }
 }
 
@@ -303,14 +309,17 @@ struct DetectLayout {
 };
 
 template <int N>
-__host__ __device__ inline DetectLayout detect_layout(int nx, int ry, int rz, int comps = 1) {
+__host__ __device__ inline DetectLayout detect_layout(int wx, int ry, int rz, int comps = 1) {
+    // wx: cube columns per unit (the row, or its window); the tile holds
+    // wx + 3 sample columns (one left of the window, two right), the word
+    // tile wx + 1
     DetectLayout L;
     const int PY = ry + 3, PZ = N == 3 ? rz + 3 : 1;
     const int WY = ry + 1, WZ = N == 3 ? rz + 1 : 1;
     const int RZ = N == 3 ? rz : 1;
-    L.tile = (comps == 2 ? 2 : 1) * PZ * PY * nx;
-    L.wtile = WZ * WY * nx;
-    L.plane_bits = ry * nx;
+    L.tile = (comps == 2 ? 2 : 1) * PZ * PY * (wx + 3);
+    L.wtile = WZ * WY * (wx + 1);
+    L.plane_bits = ry * wx;
     L.plane_words = (L.plane_bits + 31) / 32;
     L.flag_words = (L.plane_bits * MeshDims<N>::T + 31) / 32;
     L.off_words = 2 * L.tile * 4;
@@ -327,7 +336,8 @@ __global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W)
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int T = MeshDims<N>::T;
     const int rz = N == 3 ? B.rz : 1;
-    const DetectLayout L = detect_layout<N>(F.nx, B.ry, B.rz, F.comps);
+    const int wx = B.nxb > 1 ? B.wx : F.nx;
+    const DetectLayout L = detect_layout<N>(wx, B.ry, B.rz, F.comps);
     int32_t *Ft = reinterpret_cast<int32_t *>(smem);
     uint8_t *Wt = smem + L.off_words;
     uint32_t *bm = reinterpret_cast<uint32_t *>(smem + L.off_bm);
@@ -339,11 +349,19 @@ __global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W)
     int u = blockIdx.x;
     const int tci = u % B.ntc;
     u /= B.ntc;
+    const int nxb = B.nxb > 1 ? B.nxb : 1;
+    const int xb = u % nxb;
+    u /= nxb;
     const int yb = u % B.nyb;
     const int zb = u / B.nyb;
 
     TileGeom g;
     g.nx = F.nx; g.ny = F.ny; g.nz = F.nz;
+    g.x0 = xb * wx;
+    g.ncx = min(F.nx - g.x0, wx);
+    g.nvx = min(F.nx - g.x0, g.ncx + 1);
+    g.tw = wx + 3;
+    g.ww = wx + 1;
     g.y0 = yb * B.ry;
     g.z0 = N == 3 ? zb * B.rz : 0;
     g.PY = B.ry + 3; g.PZ = N == 3 ? B.rz + 3 : 1;
@@ -374,9 +392,10 @@ __global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W)
 
         // ---- exact cube cull ------------------------------------------------
         bool any = false;
-        for (int i = threadIdx.x; i < rz * B.ry * g.nx; i += NT) {
-            const int x = i % g.nx;
-            const int r = i / g.nx;
+        for (int i = threadIdx.x; i < rz * B.ry * g.ncx; i += NT) {
+            const int j = i % g.ncx;
+            const int x = g.x0 + j;
+            const int r = i / g.ncx;
             const int ly = r % B.ry;
             const int lz = r / B.ry;
             const int y = g.y0 + ly, z = g.z0 + lz;
@@ -387,13 +406,13 @@ __global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W)
                 const uint8_t *wb = Wt + (cur ^ ds) * L.wtile;
                 for (int dz = 0; dz <= ez; ++dz)
                     for (int dy = 0; dy <= ey; ++dy) {
-                        const uint8_t *wr = wb + ((lz + dz) * g.WY + ly + dy) * g.nx + x;
+                        const uint8_t *wr = wb + ((lz + dz) * g.WY + ly + dy) * g.ww + j;
                         m &= wr[0];
                         if (ex) m &= wr[1];
                     }
             }
             if (m == 0u) {
-                const int idx = ly * g.nx + x;
+                const int idx = ly * g.ncx + j;
                 atomicOr(&bm[lz * L.plane_words + (idx >> 5)], 1u << (idx & 31));
                 any = true;
             }
@@ -404,7 +423,7 @@ __global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W)
         for (int lz = 0; lz < rz; ++lz) {
             const int z = g.z0 + lz;
             if (z >= g.nz) break;
-            const long long seg = ((long long)t * g.nz + z) * B.nyb + yb;
+            const long long seg = (((long long)t * g.nz + z) * B.nyb + yb) * nxb + xb;
             if (!any_all) {
                 if (threadIdx.x == 0) { W.seg_cnt[seg] = 0; W.seg_stage[seg] = 0; }
                 continue;
@@ -430,7 +449,7 @@ __global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W)
             for (int c = threadIdx.x; c < ncand; c += NT) {
                 const int v = sv[c / T];
                 const int tt = c % T;
-                const int ly = v / g.nx, x = v % g.nx;
+                const int ly = v / g.ncx, x = g.x0 + v % g.ncx;
                 if (eval_face<N>(g, T0, T1, has_next, x, g.y0 + ly, z, ly, lz, tt))
                     atomicOr(&flags[c >> 5], 1u << (c & 31));
             }
@@ -459,7 +478,7 @@ __global__ void __launch_bounds__(NT) k_detect(Field F, Blocking B, Workspace W)
                     bits &= bits - 1;
                     const int c = i * 32 + b;
                     const int v = sv[c / T];
-                    const int ly = v / g.nx, x = v % g.nx;
+                    const int ly = v / g.ncx, x = g.x0 + v % g.ncx;
                     const long long gid = (((long long)t * g.nz + z) * g.ny + g.y0 + ly) * g.nx + x;
                     if (pos < W.cap) W.staging[pos] = gid * T + (c % T);
                     ++pos;
@@ -1046,7 +1065,7 @@ __device__ __forceinline__ long long face_id_of(const Field &F, Pt b, const int 
 // its own segment
 __device__ __forceinline__ long long find_in_segment(const Field &F, const Blocking &B, const Workspace &W,
                                                      const Pt &b, long long key) {
-    const long long seg = segment_of_coords(b.c[1], b.c[2], b.c[3], F, B);
+    const long long seg = segment_of_coords(b.c[0], b.c[1], b.c[2], b.c[3], F, B);
     const long long lo0 = W.seg_off[seg];
     const long long hi0 = lo0 + W.seg_cnt[seg];
     long long lo = lo0, hi = hi0;
@@ -1145,7 +1164,7 @@ __global__ void __launch_bounds__(NT) k_link(Field F, Blocking B, Workspace W) {
 // sorted by vertex id), or -1 if the cube did not survive the cull (then
 // none of its faces is punctured)
 __device__ __forceinline__ long long find_cube(const Field &F, const Blocking &B, const Workspace &W, const Pt &b) {
-    const long long seg = segment_of_coords(b.c[1], b.c[2], b.c[3], F, B);
+    const long long seg = segment_of_coords(b.c[0], b.c[1], b.c[2], b.c[3], F, B);
     const long long lo0 = W.seg_sstage[seg];
     const long long hi0 = lo0 + W.seg_scnt[seg];
     const long long key = (((long long)b.c[3] * F.nz + b.c[2]) * F.ny + b.c[1]) * F.nx + b.c[0];
@@ -1216,7 +1235,7 @@ __global__ void __launch_bounds__(NT) k_link_survivors(Field F, Blocking B, Work
             if (b.c[slot] + 1 < ext) inside |= 1 << q;
         }
         if (inside != FULL) continue;                // a boundary cube holds no cell
-        const long long seg = segment_of_coords(b.c[1], b.c[2], b.c[3], F, B);
+        const long long seg = segment_of_coords(b.c[0], b.c[1], b.c[2], b.c[3], F, B);
         const long long pos = W.seg_off[seg] + W.surv_off[s];
         // the next cube along axis a: its mask and first puncture's position
         unsigned long long mf = 0;
@@ -1236,7 +1255,7 @@ __global__ void __launch_bounds__(NT) k_link_survivors(Field F, Blocking B, Work
             const long long sf = find_cube(F, B, W, q);
             if (sf >= 0) {
                 mf = W.surv_mask[sf];
-                pf = W.seg_off[segment_of_coords(q.c[1], q.c[2], q.c[3], F, B)] + W.surv_off[sf];
+                pf = W.seg_off[segment_of_coords(q.c[0], q.c[1], q.c[2], q.c[3], F, B)] + W.surv_off[sf];
             }
         }
         constexpr int PER = C / D;
@@ -1607,14 +1626,14 @@ __global__ void __launch_bounds__(NT) k_classify_exact(Field F, Workspace W) {
 // ----------------------------------------------------------------------------
 cudaError_t raise_smem_cap(const void *kernel, size_t smem, bool capturing) {
     static std::mutex mu;
-    static const void *keys[16];
-    static size_t caps[16];
+    static const void *keys[32];
+    static size_t caps[32];
     static int n = 0;
     std::lock_guard<std::mutex> lock(mu);
     int i = 0;
     while (i < n && keys[i] != kernel) ++i;
     if (i == n) {
-        if (n == 16) return cudaErrorInvalidValue;   // more kernels than the library has
+        if (n == 32) return cudaErrorInvalidValue;   // more kernels than the library has
         keys[n] = kernel;
         caps[n] = 0;
         ++n;
@@ -1627,7 +1646,8 @@ cudaError_t raise_smem_cap(const void *kernel, size_t smem, bool capturing) {
 }
 
 size_t detect_smem_bytes(int ndim, const Field &F, const Blocking &B) {
-    const DetectLayout L = ndim == 2 ? detect_layout<2>(F.nx, B.ry, B.rz, F.comps) : detect_layout<3>(F.nx, B.ry, B.rz);
+    const int wx = B.nxb > 1 ? B.wx : F.nx;
+    const DetectLayout L = ndim == 2 ? detect_layout<2>(wx, B.ry, B.rz, F.comps) : detect_layout<3>(wx, B.ry, B.rz);
     return (size_t)L.total;
 }
 
@@ -2036,7 +2056,7 @@ static cudaError_t launch_all(int variant, const Field &F, const Blocking &B, co
         const size_t smem = detect_smem_bytes(N, F, B);
         const cudaError_t e = raise_smem_cap((const void *)k_detect<N>, smem, capturing);
         if (e != cudaSuccess) return e;
-        const long long units = (long long)B.ntc * B.nyb * B.nzb;
+        const long long units = (long long)B.ntc * B.nyb * B.nzb * (B.nxb > 1 ? B.nxb : 1);
         k_detect<N><<<(unsigned)units, NT, smem, s>>>(F, B, W);
     }
     if (ev) cudaEventRecord(ev[1], s);

@@ -76,6 +76,9 @@ struct Blocking {
     int ry, rz;          // rows / planes of base vertices per unit
     int nyb, nzb;        // y and z blocks
     int tc, ntc;         // slices per time chunk, number of time chunks
+    // tiled kernel on rows too wide for its tile: nxb windows of wx cube
+    // columns, one row per unit (ry = rz = 1); nxb <= 1 means whole rows
+    int nxb, wx;
     // incremental mode of the 2D streaming kernel for in-situ streams: 0 off;
     // 1 store the last slice's cube-row words to st_out; 2 take slice 0's
     // words from st_in (only slice 1 is streamed) and store slice 1's to st_out
@@ -114,21 +117,31 @@ struct Workspace {
 constexpr int LB_TILE = 2048;       // survivors per tile of the survivor scan
 constexpr int SEG_TILE = 2048;      // segments per tile of the segment scan
 
-// segment = (t, z, y-block): a contiguous run of face ids
-__host__ __device__ inline long long segment_of_coords(int y, int z, int t, const Field &F, const Blocking &B) {
-    return ((long long)t * F.nz + z) * B.nyb + y / B.ry;
+// segment = (t, z, y-block), or (t, z, y, x-window) for windowed rows: a
+// contiguous run of face ids
+__host__ __device__ inline long long segment_of_coords(int x, int y, int z, int t, const Field &F, const Blocking &B) {
+    const long long s = ((long long)t * F.nz + z) * B.nyb + y / B.ry;
+    return B.nxb > 1 ? s * B.nxb + x / B.wx : s;
 }
 __host__ __device__ inline long long segment_of(long long g, const Field &F, const Blocking &B) {
+    long long s, row;
     if (F.small) {
-        const unsigned row = fdiv((unsigned)g, F.dx);            // (t*nz + z)*ny + y
-        const unsigned tz = fdiv(row, F.dy);
-        const unsigned y = row - tz * (unsigned)F.ny;
-        return (long long)tz * B.nyb + y / B.ry;
+        const unsigned r = fdiv((unsigned)g, F.dx);              // (t*nz + z)*ny + y
+        const unsigned tz = fdiv(r, F.dy);
+        const unsigned y = r - tz * (unsigned)F.ny;
+        s = (long long)tz * B.nyb + y / B.ry;
+        row = r;
+    } else {
+        row = g / F.nx;                          // (t*nz + z)*ny + y
+        const long long y = row % F.ny;
+        const long long tz = row / F.ny;         // t*nz + z
+        s = tz * B.nyb + y / B.ry;
     }
-    const long long row = g / F.nx;             // (t*nz + z)*ny + y
-    const long long y = row % F.ny;
-    const long long tz = row / F.ny;            // t*nz + z
-    return tz * B.nyb + y / B.ry;
+    return B.nxb > 1 ? s * B.nxb + (g - row * F.nx) / B.wx : s;
+}
+// segments of a field: (t, z, y-block[, x-window])
+inline long long segment_count(const Field &F, const Blocking &B) {
+    return (long long)F.nt * F.nz * B.nyb * (B.nxb > 1 ? B.nxb : 1);
 }
 
 // detect-kernel variants
@@ -136,10 +149,10 @@ enum : int {
     VAR_TILE = 0,           // smem-tile kernel: any 2D/3D shape
     VAR_STREAM2 = 1,        // streaming 2D kernel (nx % 4 == 0, 16-byte aligned rows)
     VAR_STREAM2_EXACT = 2,  // same, exact rounding for |f 2^S| > 2^22
-    VAR_STREAM3 = 3,        // streaming 3D kernel (nx % 4 == 0, nx <= 512, 16-byte aligned)
+    VAR_STREAM3 = 3,        // streaming 3D kernel (pitch % 4 == 0, pitch <= 1024, 16-byte aligned)
     VAR_STREAM3_EXACT = 4,  // same, exact rounding
 };
-constexpr int STREAM3_MAX_NX = 512;   // widest row the 3D streaming kernel takes
+constexpr int STREAM3_MAX_NX = 1024;  // widest row the 3D streaming kernel takes
 inline int exact_variant(int v) {
     return v == VAR_STREAM2 ? VAR_STREAM2_EXACT : v == VAR_STREAM3 ? VAR_STREAM3_EXACT : v;
 }
@@ -156,7 +169,7 @@ long long stream2_state_words(const Field &F, const Blocking &B);
 // 3D streaming kernel: smem per CTA for B.ry, B.rz, B.ns; threads; resident
 // CTAs per SM; launch (the smem attribute is set outside graph capture)
 size_t stream3_smem_bytes(int nx, const Blocking &B);
-int stream3_threads();
+int stream3_threads(int nx);
 int stream3_ctas_per_sm(int nx, const Blocking &B);
 // cube rows per unit of the 3D streaming kernel for a row pitch
 int stream3_ry(int nx);

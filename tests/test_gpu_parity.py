@@ -60,7 +60,7 @@ CASES = [
                                                               sigma_range=(2.0, 9.0)), 20),
     ("stream_levels_20x37x7", lambda: synth.random_levels((7, 37, 20), levels=(-1, -.5, 0, .5, 1), seed=17), 20),
     ("stream_noisy_128x33x12", lambda: synth.spiral_woven(128, 12, sigma=0.05, seed=6, ny=33), 20),
-    # shapes taking the streaming 3D kernel (nx % 4 == 0, nx <= 512)
+    # shapes taking the streaming 3D kernel (rows padded to 4 floats, <= 1024)
     ("s3_levels_8x9x7x4", lambda: synth.random_levels((4, 7, 9, 8), seed=21), 20),
     ("s3_levels5_12x5x6x3", lambda: synth.random_levels((3, 6, 5, 12), levels=(-1, -.5, 0, .5, 1), seed=22), 20),
     ("s3_tiny_4x2x2x2", lambda: synth.random_levels((2, 2, 2, 4), seed=23), 20),
@@ -68,6 +68,17 @@ CASES = [
     ("s3_zero_8x6x5x3", lambda: np.zeros((3, 5, 6, 8), np.float32), 20),
     ("s3_wide_132x4x3x2", lambda: synth.random_levels((2, 3, 4, 132), seed=25), 20),
     ("s3_wide_264x3x3x2", lambda: synth.random_levels((2, 3, 3, 264), seed=26), 20),
+    ("s3_wide_600x4x3x2", lambda: synth.random_levels((2, 3, 4, 600), seed=30), 20),
+    ("s3_wide_1021x3x2x2", lambda: synth.random_levels((2, 2, 3, 1021), levels=(-1, -.5, 0, .5, 1), seed=31), 20),
+    ("s3_blobs_1024x9x4x3", lambda: synth.gaussian_blobs((1024, 9, 4), 3, nblobs=40, seed=32,
+                                                          sigma_range=(2.0, 6.0)), 20),
+    # wider than the streaming kernels: the tiled kernel on windows of the row
+    ("tile3_wide_1030x3x3x2", lambda: synth.random_levels((2, 3, 3, 1030), seed=33), 20),
+    ("tile3_wide_1600x2x2x2", lambda: synth.random_levels((2, 2, 2, 1600), levels=(-1, -.5, 0, .5, 1), seed=34), 20),
+    ("tile2_wide_2900x4x3", lambda: synth.random_levels((3, 4, 2900), seed=35), 20),
+    ("tile2_wide_6000x3x2", lambda: synth.random_levels((2, 3, 6000), levels=(-1, -.5, 0, .5, 1), seed=36), 20),
+    ("tile2_blobs_4100x12x4", lambda: synth.gaussian_blobs((4100, 12), 4, nblobs=60, seed=37,
+                                                            sigma_range=(2.0, 6.0)), 20),
     ("s3_levels5_20x17x9x3", lambda: synth.random_levels((3, 9, 17, 20), levels=(-1, -.5, 0, .5, 1), seed=27), 20),
     ("s3_blobs_36x40x20x6", lambda: synth.gaussian_blobs((36, 40, 20), 6, nblobs=16, seed=28,
                                                           sigma_range=(2.0, 6.0)), 20),

@@ -66,6 +66,9 @@ CASES = [
     ("nt1_9x7", lambda: _levels((1, 7, 9, 2), 9), 20),
     ("zero", lambda: np.zeros((3, 8, 9, 2), np.float32), 20),
     ("noise_33x31x6", lambda: np.random.default_rng(10).standard_normal((6, 31, 33, 2)).astype(np.float32), 20),
+    # rows wider than one detect tile: windows of the row, one row per unit
+    ("levels_wide_1700x3x3", lambda: _levels((3, 3, 1700, 2), 11), 20),
+    ("vortex_wide_3500x6x4", lambda: synth.vortex_street(3500, 6, 4, nvort=30, nsrc=12, seed=12), 20),
 ]
 
 
