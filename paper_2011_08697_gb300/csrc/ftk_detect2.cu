@@ -379,11 +379,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
 size_t stream2_smem_bytes(int nx) { return (size_t)stream2_layout(nx).total; }
 int stream2_threads(int nx) { return stream2_consumers(nx) + 64; }
 
-// rows up to 1024 floats: 192 threads, three CTAs per SM; wider rows: up to 320
+// rows up to 1024 floats: 192 threads, three CTAs per SM; up to 2048: up to
+// 320; up to 4096: up to 576 (one CTA per SM)
 template <bool EXACT>
 static void *stream2_kernel(int nx) {
     if (nx <= 1024) return (void *)k_detect2_stream<EXACT, 192, 3>;
-    return (void *)k_detect2_stream<EXACT, 320, 1>;
+    if (nx <= 2048) return (void *)k_detect2_stream<EXACT, 320, 1>;
+    return (void *)k_detect2_stream<EXACT, 576, 1>;
 }
 
 long long stream2_state_words(const Field &F, const Blocking &B) {

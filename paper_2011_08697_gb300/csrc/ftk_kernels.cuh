@@ -158,7 +158,7 @@ inline int exact_variant(int v) {
 }
 constexpr float RANGE_LIMIT = 268435456.0f;   // 2^28: the exact quantisation's range of |f 2^S|
 constexpr int STREAM2_ROWS = 16;      // cube rows per unit of the streaming kernel
-constexpr int STREAM2_MAX_NX = 2048;  // widest row the streaming kernel takes
+constexpr int STREAM2_MAX_NX = 4096;  // widest row the streaming kernel takes
 
 size_t detect_smem_bytes(int ndim, const Field &F, const Blocking &B);
 size_t stream2_smem_bytes(int nx);

@@ -60,6 +60,8 @@ CASES = [
                                                               sigma_range=(2.0, 9.0)), 20),
     ("stream_levels_20x37x7", lambda: synth.random_levels((7, 37, 20), levels=(-1, -.5, 0, .5, 1), seed=17), 20),
     ("stream_noisy_128x33x12", lambda: synth.spiral_woven(128, 12, sigma=0.05, seed=6, ny=33), 20),
+    ("stream_wide_2900x4x3", lambda: synth.random_levels((3, 4, 2900), seed=35), 20),
+    ("stream_wide_4093x5x2", lambda: synth.random_levels((2, 5, 4093), levels=(-1, -.5, 0, .5, 1), seed=38), 20),
     # shapes taking the streaming 3D kernel (rows padded to 4 floats, <= 1024)
     ("s3_levels_8x9x7x4", lambda: synth.random_levels((4, 7, 9, 8), seed=21), 20),
     ("s3_levels5_12x5x6x3", lambda: synth.random_levels((3, 6, 5, 12), levels=(-1, -.5, 0, .5, 1), seed=22), 20),
@@ -75,7 +77,6 @@ CASES = [
     # wider than the streaming kernels: the tiled kernel on windows of the row
     ("tile3_wide_1030x3x3x2", lambda: synth.random_levels((2, 3, 3, 1030), seed=33), 20),
     ("tile3_wide_1600x2x2x2", lambda: synth.random_levels((2, 2, 2, 1600), levels=(-1, -.5, 0, .5, 1), seed=34), 20),
-    ("tile2_wide_2900x4x3", lambda: synth.random_levels((3, 4, 2900), seed=35), 20),
     ("tile2_wide_6000x3x2", lambda: synth.random_levels((2, 3, 6000), levels=(-1, -.5, 0, .5, 1), seed=36), 20),
     ("tile2_blobs_4100x12x4", lambda: synth.gaussian_blobs((4100, 12), 4, nblobs=60, seed=37,
                                                             sigma_range=(2.0, 6.0)), 20),

@@ -1,6 +1,6 @@
 """The allocation-free entry point ftk_track_cp2d_noalloc, called through the
 C ABI, must return exactly what the allocating entry point ftk_track_cp2d
-returns.  It exists for callers that cannot allocate device memory (a host
+returns, and (on the small odd-shaped fields) what the CPU oracle returns.  It exists for callers that cannot allocate device memory (a host
 application that has reserved the GPU's memory for its own pool, code that
 must not trigger the device synchronisation cudaMalloc/cudaFree can cause);
 its scratch is one static device array shared by every call, so the test
@@ -11,7 +11,9 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import cp
 from paper_2011_08697_gb300 import synth
+from parity_util import compare_full
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -83,6 +85,7 @@ def test_noalloc_odd_shapes_and_no_device_allocation():
         st, n, got = _noalloc(F, x, cap=len(ref) + 3)
         assert st == 0, F.lib().ftk_last_error()
         _same(got, ref)
+        compare_full(got, cp.track(f))        # and the oracle itself
         torch.cuda.synchronize()
         free0 = torch.cuda.mem_get_info()[0]
         for _ in range(2):
