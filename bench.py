@@ -686,7 +686,7 @@ def _full_oracle_check(res, f):
         err = float(np.max(np.abs(res["off"] - ref["off"]))) if len(res) else 0.0
         ok = ok and err <= 1e-5
     return {"full_workload": ok, "punctures": int(len(ref["face_id"])), "max_offset_err": err,
-            "compared": "face ids, Morse index, ordinal flag, base vertex, label: equal; offsets <= 1e-5 cell"}, dt
+            "compared": "face ids, Morse index, ordinal flag, base vertex, label: equal; offsets <= 1e-5 cell"}, dt, ref
 
 
 def _measure_plain(wl, args, dev, dist, world, rank, local):
@@ -889,6 +889,176 @@ def _measure_iso(args, dev, world):
     }
 
 
+VEC_WL = dict(name="vortex_street_512x512x32_24vortices_12sources", dims=(512, 512), nt=32, nvort=24, nsrc=12)
+VEC_SAMPLE_SLICES = 3   # slices of the bit-exact / CPU-baseline sample of the vector line
+
+
+def _measure_vec(args, dev, world):
+    """Zeros of a 2D vector field (Sec. 4.1; flow-past-cylinder-shaped
+    synthetic wake): K timed plan executions (L2 flushed between them), the
+    tiled detect pass in vector mode against HBM (8 bytes per vertex), a
+    bit-exact comparison with the oracle on the first VEC_SAMPLE_SLICES
+    slices, and the oracle's time there."""
+    import torch
+    from paper_2011_08697_gb300 import ftk, synth
+    W = VEC_WL
+    nx, ny = W["dims"]
+    v_np = synth.vortex_street(nx, ny, W["nt"], nvort=W["nvort"], nsrc=W["nsrc"], seed=0)
+    nverts = nx * ny * W["nt"]
+    faces = face_count(W["dims"], W["nt"])
+    x = torch.from_numpy(v_np).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    plan = ftk.Plan(v_np.shape, vec2d=True)
+    timed = ftk.Plan(v_np.shape, ftk.make_params(flags=ftk.FTK_FLAG_STAGE_TIMES), vec2d=True)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 1)):
+            plan.execute(x, stream)
+            timed.execute(x, stream)
+        P = plan.count()
+        timed.count()
+        res = plan.download()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            plan.execute(x, stream)
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    tot_ms = sum(step_ms)
+    stages = []
+    with torch.cuda.stream(stream):
+        for k in range(max(3, min(args.steps, 20))):
+            flush.zero_()
+            timed.execute(x, stream)
+            timed.count()
+            stages.append(timed.stage_times())
+    names = ["detect", "scan", "finalize", "link", "label"]
+    st = {n: statistics.mean(s_[i] for s_ in stages) for i, n in enumerate(names)}
+    alg_bytes = 8.0 * nverts
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (st["detect"] / 1e3) / 1e9
+    step_mean = tot_ms / args.steps
+    from oracle import cp
+    sub = np.ascontiguousarray(v_np[:VEC_SAMPLE_SLICES])
+    got = ftk.ftk_track_vec2d(torch.from_numpy(sub).to(dev))
+    t0 = time.perf_counter()
+    ref = cp.track_vec(sub)
+    dt = time.perf_counter() - t0
+    ok = bool(np.array_equal(got["face_id"], ref["face_id"]))
+    err = None
+    if ok:
+        ok = all(np.array_equal(got[a], ref[b]) for a, b in
+                 (("morse_index", "morse"), ("ordinal", "ordinal"), ("base", "base"), ("label", "label")))
+        err = float(np.max(np.abs(got["off"] - ref["off"]))) if len(got) else 0.0
+        ok = ok and err <= 1e-5
+    sub_faces = face_count(W["dims"], VEC_SAMPLE_SLICES)
+    desc = plan.describe()
+    plan.close()
+    timed.close()
+    return {
+        "workload": W["name"], "metric": METRIC, "value": weak_value(faces, world, args.steps, tot_ms),
+        "unit": "simplices/s", "ms_per_step": step_mean, "punctures": int(P),
+        "types": {str(k): int(np.sum(res["morse_index"] == k)) for k in np.unique(res["morse_index"])},
+        "stages_ms": st, "plan": desc,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_detect<2> (vector mode)",
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": st["detect"],
+                     "whole_step_frac": (alg_bytes / (step_mean / 1e3) / 1e9) / peak},
+        "bit_exact_sample": {"ok": ok, "slices": VEC_SAMPLE_SLICES, "punctures": int(len(ref["face_id"])),
+                             "max_offset_err": err,
+                             "compared": "face ids, type, ordinal flag, base vertex, label: equal; offsets <= 1e-5"},
+        "cpu_baseline": {"value": sub_faces / dt, "unit": "simplices/s", "cores": 1, "kind": "oracle",
+                         "sample": f"the first {VEC_SAMPLE_SLICES} slices of the workload ({sub_faces} faces)",
+                         "seconds": dt},
+        "gpu_launches": int(desc["kernels_per_execute"]) * args.steps,
+    }
+
+
+TRAJ_FILTER = dict(min_duration=2.0, smooth_half_window=2)
+
+
+def _measure_traj(f_np, ref, args, dev):
+    """Ordered trajectories, their slices at a time t and the filtered,
+    type-smoothed trajectories (Sec. 4.1, 4.2) of one tracked field, through
+    the C ABI: host wall time per call after a plan execute (each call
+    includes its download; the first builds the polylines on the GPU).  With
+    the oracle's result ``ref``, every polyline, slice crossing and smoothed
+    type is compared with the oracle's walk of its own result."""
+    import torch
+    from paper_2011_08697_gb300 import ftk
+    x = torch.from_numpy(f_np).to(dev)
+    nt = f_np.shape[0]
+    plan = ftk.Plan(f_np.shape)
+    plan.execute(x)
+    plan.count()
+    res = plan.download()
+    ts = res["base"][:, 3].astype(np.float64) + res["off"][:, 3]
+    rng = np.random.default_rng(7)
+    t_cut = 0.5 * (nt - 1)
+    while ts.size and np.min(np.abs(ts - t_cut)) <= 1e-4:   # no point within FP32/FP64 ordering reach
+        t_cut = float(rng.uniform(0.25 * (nt - 1), 0.75 * (nt - 1)))
+    walk, cut, flt = [], [], []
+    for k in range(max(args.steps, 3) + 1):
+        plan.execute(x)
+        plan.count()
+        t0 = time.perf_counter()
+        off, pts, closed = plan.trajectories()
+        t1 = time.perf_counter()
+        sl = plan.slice(t_cut)
+        t2 = time.perf_counter()
+        foff, fpts, fclosed = plan.trajectories(**TRAJ_FILTER)
+        t3 = time.perf_counter()
+        if k:                                   # the first round is the warm-up
+            walk.append(t1 - t0)
+            cut.append(t2 - t1)
+            flt.append(t3 - t2)
+    plan.close()
+    P = len(pts)
+    out = {"trajectories": int(len(off) - 1), "points": int(P), "closed": int(np.sum(closed)),
+           "slice_t": t_cut, "slice_points": int(len(sl)), "filter": TRAJ_FILTER,
+           "kept": int(len(foff) - 1), "kept_points": int(len(fpts)),
+           "ms": {"walk": 1e3 * statistics.median(walk), "slice": 1e3 * statistics.median(cut),
+                  "filter_smooth": 1e3 * statistics.median(flt)},
+           "points_per_s": P / statistics.median(walk),
+           "form": "wall time of each C-ABI call after an execute, host results included"}
+    if ref is not None:
+        from oracle import cp
+        trajs = cp.trajectories(ref["grid"], ref["face_id"], ref["label"])
+        pos = cp.positions(ref)
+        morse = dict(zip(ref["face_id"].tolist(), ref["morse"].tolist()))
+        ok = len(off) == len(trajs) + 1
+        for i, (order, cl) in enumerate(trajs):
+            if not ok:
+                break
+            ok = pts["face_id"][off[i]:off[i + 1]].tolist() == order and bool(closed[i]) == cl
+        want = cp.slice_trajectories(trajs, pos, t_cut)
+        ok_s = len(sl) == len(want)
+        err = 0.0
+        for g, w in zip(sl, want):
+            ok_s = ok_s and (int(g["label"]), int(g["face_a"]), int(g["face_b"])) == w[:3]
+            err = max(err, float(np.max(np.abs(g["pos"] - np.asarray(w[3])))))
+        ok_s = ok_s and err <= 1e-5
+        wf = cp.filter_trajectories(trajs, pos, morse, min_duration=TRAJ_FILTER["min_duration"],
+                                    half_window=TRAJ_FILTER["smooth_half_window"])
+        ok_f = len(foff) == len(wf) + 1
+        for i, (order, cl, types) in enumerate(wf):
+            if not ok_f:
+                break
+            ok_f = (fpts["face_id"][foff[i]:foff[i + 1]].tolist() == order and bool(fclosed[i]) == cl
+                    and fpts["morse_index"][foff[i]:foff[i + 1]].tolist() == types)
+        out["bit_exact"] = {"polylines": bool(ok), "slice": bool(ok_s), "slice_max_pos_err": err,
+                            "filtered_smoothed": bool(ok_f),
+                            "compared": "every polyline (face ids in path order, closed flag), the slice crossings "
+                                        "(label, segment ends; positions <= 1e-5) and the filtered trajectories "
+                                        "with smoothed types, against the oracle's walk of its own full result"}
+    return out
+
+
 def gpu_arm(args):
     import torch
     from paper_2011_08697_gb300 import build as _b, ftk
@@ -906,6 +1076,9 @@ def gpu_arm(args):
     iso_line = None
     if args.with_iso and wl == "blobs3d" and world == 1:
         iso_line = _measure_iso(args, dev, world)
+    vec_line = None
+    if args.with_vec and wl == "blobs3d" and world == 1:
+        vec_line = _measure_vec(args, dev, world)
 
     if rank == 0:
         W = m["W"]
@@ -923,7 +1096,7 @@ def gpu_arm(args):
             "punctures": m["P"], "trajectories": int(len(np.unique(m["res"]["label"]))),
             "stages_ms": m["stages"], "plan": m["desc"], "roofline": m["roofline"],
             "e2e": m["e2e"], "gpu_launches": m["gpu_launches"] + (extra["gpu_launches"] if extra else 0)
-            + (iso_line["gpu_launches"] if iso_line else 0),
+            + (iso_line["gpu_launches"] if iso_line else 0) + (vec_line["gpu_launches"] if vec_line else 0),
             "clocks": m["clocks"],
         }
         if extra is not None:
@@ -938,10 +1111,12 @@ def gpu_arm(args):
             }
         if iso_line is not None:
             line["isovolume"] = iso_line
+        if vec_line is not None:
+            line["vector2d"] = vec_line
         if world == 1:
             # the oracle on the full workload, all host cores: the bit-exact
             # check and the all-core CPU baseline in one run
-            rep, dt = _full_oracle_check(m["res"], m["f_np"])
+            rep, dt, ref3 = _full_oracle_check(m["res"], m["f_np"])
             line["bit_exact"] = rep
             ncpu = os.cpu_count() or 1
             single = _cpu_baseline_single(wl)
@@ -949,12 +1124,17 @@ def gpu_arm(args):
                 "value": m["faces"] / dt, "unit": "simplices/s", "cores": ncpu, "kind": "oracle",
                 "sample": f"the full workload ({m['faces']} faces), one process per base slice on {ncpu} cores",
                 "seconds": dt, "single_core": single}
+            if args.with_traj:
+                line["trajectories_ops"] = _measure_traj(m["f_np"], ref3, args, dev)
             if extra is not None:
-                rep2, dt2 = _full_oracle_check(extra["res"], extra["f_np"])
+                rep2, dt2, _ = _full_oracle_check(extra["res"], extra["f_np"])
                 line["spiral2d"]["bit_exact"] = rep2
                 line["spiral2d"]["cpu_baseline"] = {
                     "value": extra["faces"] / dt2, "unit": "simplices/s", "cores": ncpu, "kind": "oracle",
                     "sample": "the full workload", "seconds": dt2}
+                if args.with_traj:
+                    # timing only: the oracle's pure-Python walk of 1.3 M points is not bounded
+                    line["spiral2d"]["trajectories_ops"] = _measure_traj(extra["f_np"], None, args, dev)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -971,6 +1151,10 @@ def main():
                     help="blobs3d: skip the 2D spiral workload reported beside it")
     ap.add_argument("--no-iso", dest="with_iso", action="store_false",
                     help="blobs3d: skip the isovolume line reported beside it")
+    ap.add_argument("--no-vec", dest="with_vec", action="store_false",
+                    help="blobs3d: skip the 2D vector-field line reported beside it")
+    ap.add_argument("--no-traj", dest="with_traj", action="store_false",
+                    help="blobs3d: skip the trajectory walk / slice / filter timings")
     ap.add_argument("--duration", type=float, default=60.0, help="serve2d: Poisson phase seconds")
     ap.add_argument("--sat-pushes", type=int, default=24, help="serve2d: saturated pushes per stream")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="serve2d: admission budget")
