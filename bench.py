@@ -896,7 +896,7 @@ VEC_SAMPLE_SLICES = 3   # slices of the bit-exact / CPU-baseline sample of the v
 def _measure_vec(args, dev, world):
     """Zeros of a 2D vector field (Sec. 4.1; flow-past-cylinder-shaped
     synthetic wake): K timed plan executions (L2 flushed between them), the
-    tiled detect pass in vector mode against HBM (8 bytes per vertex), a
+    detect pass in vector mode against HBM (8 bytes per vertex), a
     bit-exact comparison with the oracle on the first VEC_SAMPLE_SLICES
     slices, and the oracle's time there."""
     import torch
@@ -937,7 +937,10 @@ def _measure_vec(args, dev, world):
             timed.execute(x, stream)
             timed.count()
             stages.append(timed.stage_times())
-    names = ["detect", "scan", "finalize", "link", "label"]
+    desc = plan.describe()
+    streaming = desc["detect_variant"] != 0
+    names = (["detect", "survive+scan", "emit+locate", "link", "label"] if streaming
+             else ["detect", "scan", "finalize", "link", "label"])
     st = {n: statistics.mean(s_[i] for s_ in stages) for i, n in enumerate(names)}
     alg_bytes = 8.0 * nverts
     peak, peak_kind = measured_peak_hbm()
@@ -957,7 +960,6 @@ def _measure_vec(args, dev, world):
         err = float(np.max(np.abs(got["off"] - ref["off"]))) if len(got) else 0.0
         ok = ok and err <= 1e-5
     sub_faces = face_count(W["dims"], VEC_SAMPLE_SLICES)
-    desc = plan.describe()
     plan.close()
     timed.close()
     return {
@@ -966,7 +968,8 @@ def _measure_vec(args, dev, world):
         "types": {str(k): int(np.sum(res["morse_index"] == k)) for k in np.unique(res["morse_index"])},
         "stages_ms": st, "plan": desc,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_detect<2> (vector mode)",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_detect2_stream<vector>" if streaming else "k_detect<2> (vector mode)",
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": st["detect"],
                      "whole_step_frac": (alg_bytes / (step_mean / 1e3) / 1e9) / peak},
         "bit_exact_sample": {"ok": ok, "slices": VEC_SAMPLE_SLICES, "punctures": int(len(ref["face_id"])),

@@ -167,12 +167,12 @@ ftk_status choose_blocking(int ndim, const Field &F, Blocking &B, int &variant) 
     B.wx = F.nx;
     // the streaming kernels read rows padded to a multiple of 4 floats
     // (F.pitch, chosen by stream_pitch)
-    if (ndim == 2 && F.comps != 2 && F.pitch % 4 == 0 && F.pitch <= STREAM2_MAX_NX) {
+    if (ndim == 2 && F.pitch % 4 == 0 && F.pitch <= (F.comps == 2 ? STREAM2_VEC_MAX_NX : STREAM2_MAX_NX)) {
         variant = VAR_STREAM2;
         B.ry = STREAM2_ROWS; B.rz = 1;
         B.nyb = (F.ny + B.ry - 1) / B.ry;
         B.nzb = 1;
-        choose_time_chunks(F, B, B.nyb, (long long)sms * stream2_ctas_per_sm(F.pitch));
+        choose_time_chunks(F, B, B.nyb, (long long)sms * stream2_ctas_per_sm(F.pitch, F.comps));
         return FTK_OK;
     }
     if (ndim == 3 && F.pitch % 4 == 0 && F.pitch <= STREAM3_MAX_NX) {

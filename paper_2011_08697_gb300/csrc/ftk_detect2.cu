@@ -55,10 +55,11 @@ __host__ __device__ inline int stream2_consumers(int nx) { return ((nx + CX - 1)
 struct Stream2Layout {
     int ring, bars, bm, bmw, cnt, st, total;
 };
-__host__ __device__ inline Stream2Layout stream2_layout(int nx) {
+// comps = 2: a ring slot holds a row of vectors (two floats per vertex)
+__host__ __device__ inline Stream2Layout stream2_layout(int nx, int comps = 1) {
     Stream2Layout L;
     L.ring = 0;
-    L.bars = L.ring + NS2 * nx * 4;
+    L.bars = L.ring + NS2 * nx * comps * 4;
     L.bmw = (RY2 * nx + 31) / 32;
     L.bm = s2_round16(L.bars + (2 * NS2 + 4) * 8);
     L.cnt = L.bm + 2 * L.bmw * 4;     // [2] survivors per slab buffer
@@ -84,7 +85,10 @@ __device__ __forceinline__ uint32_t survivors8(uint32_t c) {
     return mixed & (mixed >> 16) & 0xFFu;
 }
 
-template <bool EXACT, int MAXT, int MINB>
+// VEC: a 2D vector field (two components per vertex, interleaved): the
+// vectors themselves take the gradients' place, so a slice streams only the
+// unit's rows y0 .. y0+RY2 and a G row is the row itself
+template <bool EXACT, int MAXT, int MINB, bool VEC = false>
 __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking B, Workspace W) {
     extern __shared__ __align__(128) unsigned char smem[];
     // the sweep covers the padded row (pitch columns; padding repeats column
@@ -94,7 +98,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     const int NC = (int)blockDim.x - 64;
     const int CW = NC >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Stream2Layout L = stream2_layout(nx);
+    constexpr int CMP = VEC ? 2 : 1;        // floats per vertex
+    const Stream2Layout L = stream2_layout(nx, CMP);
     float *ring = reinterpret_cast<float *>(smem + L.ring);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bars);
     uint64_t *empty = full + NS2;
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
     const int s_last = min(t_end, nt - 1);
     const int nsl = s_last - t0 + 1;      // slices of the unit
     const int nslab = t_end - t0;         // slabs (base slices) owned
-    constexpr int RS = RY2 + 3;           // rows streamed per slice
+    constexpr int RS = VEC ? RY2 + 1 : RY2 + 3;   // rows streamed per slice
     const int sl0 = B.st_mode == 2 ? 1 : 0;   // slice 0's words come from st_in
     const int J = (nsl - sl0) * RS;
 
@@ -143,9 +148,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
                     break;
                 }
                 const int s = t0 + sl0 + j / RS;
-                const int y = min(max(y0 - 1 + j % RS, 0), ny - 1);
-                mbar_arrive_expect_tx(&full[slot], (uint32_t)nx * 4u);
-                tma_row(ring + (size_t)slot * nx, F.f + ((long long)s * ny + y) * nx, (uint32_t)nx * 4u, &full[slot]);
+                const int y = min(max((VEC ? y0 : y0 - 1) + j % RS, 0), ny - 1);
+                const uint32_t bytes = (uint32_t)nx * CMP * 4u;
+                mbar_arrive_expect_tx(&full[slot], bytes);
+                tma_row(ring + (size_t)slot * nx * CMP, F.f + ((long long)s * ny + y) * nx * CMP, bytes, &full[slot]);
                 issued = j + 1;
             }
             if (!ok) {
@@ -318,6 +324,89 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
         }
     };
 
+    // Vector rows: streamed row vi of slice sl is G row u = y0 + vi; the
+    // sign of a quantised component is bit 31 of its encoding minus the
+    // encoding of zero.  Cube row u-1 completes with G rows u-1 and u; at
+    // the top edge cube row u uses row u alone.
+    auto row_vec = [&](int vi, int sl, uint32_t *bq) {
+        const int slot = j % NS2;
+        uint32_t w = 0;
+        if (ok && !mbar_wait(&full[slot], (j / NS2) & 1)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        if (ok) {
+            const float *r = ring + (size_t)slot * nx * 2;
+            float v[18];
+            const float4 c0 = *reinterpret_cast<const float4 *>(r + 2 * xa);
+            const float4 c1 = *reinterpret_cast<const float4 *>(r + 2 * xa + 4);
+            const float4 c2 = *reinterpret_cast<const float4 *>(r + 2 * xb);
+            const float4 c3 = *reinterpret_cast<const float4 *>(r + 2 * xb + 4);
+            const float2 c4 = *reinterpret_cast<const float2 *>(r + 2 * xr1);
+            v[0] = c0.x; v[1] = c0.y; v[2] = c0.z; v[3] = c0.w;
+            v[4] = c1.x; v[5] = c1.y; v[6] = c1.z; v[7] = c1.w;
+            v[8] = c2.x; v[9] = c2.y; v[10] = c2.z; v[11] = c2.w;
+            v[12] = c3.x; v[13] = c3.y; v[14] = c3.z; v[15] = c3.w;
+            v[16] = c4.x; v[17] = c4.y;
+            uint32_t q[18];
+#pragma unroll
+            for (int k = 0; k < 18; ++k) q[k] = qbits<EXACT>(v[k], scale, bad);
+            if (!EXACT) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    qa_and &= q[k];
+                    qa_or |= q[k];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            // columns: k = 0..7 the thread's, 8 the next (clamped to nx-1);
+            // absent columns repeat the last one
+            if (ncol == 4) {
+#pragma unroll
+                for (int k = 8; k < 16; ++k) q[k] = q[k - 2 * (1 + ((k - 8) >> 1))];
+            }
+#pragma unroll
+            for (int k = 8; k >= 0; --k) w = __funnelshift_l(q[2 * k + 1] - MAGIC_BITS, w, 1);
+            w <<= 7;
+#pragma unroll
+            for (int k = 8; k >= 0; --k) w = __funnelshift_l(q[2 * k] - MAGIC_BITS, w, 1);
+            if (dbl7) w = (w & ~0x01000100u) | ((w >> 1) & 0x01000100u);   // column x0+8 absent: repeat 7
+            if (dbl3) w = (w & ~0x00100010u) | ((w >> 1) & 0x00100010u);   // column x0+4 absent: repeat 3
+        }
+        ++j;
+        const int u = y0 + vi;
+        if (u <= ny - 1) {
+            const uint32_t p = pair_word(w);
+            if (vi >= 1) {
+                const int i = vi - 1;
+                const uint32_t sq = combine(pprev, p);
+                if (sl > 0) {
+                    const uint32_t sv8 = survivors8(combine(sq, sst[i * NC])) & vmask;
+                    if (sv8) {
+                        const int idx = i * nx + x0;
+                        atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
+                        nsv += __popc(sv8);
+                        if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
+                    }
+                }
+                sst[i * NC] = sq;
+            }
+            if (u == ny - 1 && vi < RY2) {
+                const int i = vi;
+                if (sl > 0) {
+                    const uint32_t sv8 = survivors8(combine(p, sst[i * NC])) & vmask;
+                    if (sv8) {
+                        const int idx = i * nx + x0;
+                        atomicOr(&bq[idx >> 5], sv8 << (idx & 31));
+                        nsv += __popc(sv8);
+                        if ((idx & 31) > 24) atomicOr(&bq[(idx >> 5) + 1], sv8 >> (32 - (idx & 31)));
+                    }
+                }
+                sst[i * NC] = p;
+            }
+            pprev = p;
+        }
+    };
+
     for (int sl = sl0; sl < nsl && ok; ++sl) {
         // slice sl > 0 completes slab q = sl-1, whose bits go to buffer q & 1:
         // wait until the compactor has released that buffer (slab q-2)
@@ -325,12 +414,17 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
         uint32_t *bq = bm + (q & 1) * L.bmw;
         if (sl > 0 && q >= 2 && !mbar_wait(&freed[q & 1], ((q >> 1) - 1) & 1)) ok = false;
         ok = __all_sync(0xffffffffu, ok);
-        // rows in threes, the buffers rotating (fa, fb, fc) -> (fb, fc, fa) -> (fc, fa, fb)
+        if constexpr (VEC) {
 #pragma unroll 1
-        for (int vi = 0; vi < RS; vi += 3) {
-            row(vi, sl, bq, fa, fb, fc);
-            if (vi + 1 < RS) row(vi + 1, sl, bq, fb, fc, fa);
-            if (vi + 2 < RS) row(vi + 2, sl, bq, fc, fa, fb);
+            for (int vi = 0; vi < RS; ++vi) row_vec(vi, sl, bq);
+        } else {
+            // rows in threes, the buffers rotating (fa, fb, fc) -> (fb, fc, fa) -> (fc, fa, fb)
+#pragma unroll 1
+            for (int vi = 0; vi < RS; vi += 3) {
+                row(vi, sl, bq, fa, fb, fc);
+                if (vi + 1 < RS) row(vi + 1, sl, bq, fb, fc, fa);
+                if (vi + 2 < RS) row(vi + 2, sl, bq, fc, fa, fb);
+            }
         }
         if (sl > 0) {
             const int n = __reduce_add_sync(0xffffffffu, nsv);
@@ -376,13 +470,18 @@ __global__ void __launch_bounds__(MAXT, MINB) k_detect2_stream(Field F, Blocking
 }
 
 // ---- host side: launch configuration ----
-size_t stream2_smem_bytes(int nx) { return (size_t)stream2_layout(nx).total; }
+size_t stream2_smem_bytes(int nx, int comps) { return (size_t)stream2_layout(nx, comps).total; }
 int stream2_threads(int nx) { return stream2_consumers(nx) + 64; }
 
 // rows up to 1024 floats: 192 threads, three CTAs per SM; up to 2048: up to
-// 320; up to 4096: up to 576 (one CTA per SM)
+// 320; up to 4096: up to 576 (one CTA per SM).  Vector rows (two floats per
+// vertex) up to 2048 vertices.
 template <bool EXACT>
-static void *stream2_kernel(int nx) {
+static void *stream2_kernel(int nx, int comps) {
+    if (comps == 2) {
+        if (nx <= 1024) return (void *)k_detect2_stream<EXACT, 192, 2, true>;
+        return (void *)k_detect2_stream<EXACT, 320, 1, true>;
+    }
     if (nx <= 1024) return (void *)k_detect2_stream<EXACT, 192, 3>;
     if (nx <= 2048) return (void *)k_detect2_stream<EXACT, 320, 1>;
     return (void *)k_detect2_stream<EXACT, 576, 1>;
@@ -392,10 +491,10 @@ long long stream2_state_words(const Field &F, const Blocking &B) {
     return (long long)B.nyb * RY2 * stream2_consumers(F.pitch);
 }
 
-int stream2_ctas_per_sm(int nx) {
+int stream2_ctas_per_sm(int nx, int comps) {
     int n = 0;
-    const size_t smem = stream2_smem_bytes(nx);
-    const void *k = stream2_kernel<false>(nx);
+    const size_t smem = stream2_smem_bytes(nx, comps);
+    const void *k = stream2_kernel<false>(nx, comps);
     raise_smem_cap(k, smem, false);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, stream2_threads(nx), smem);
     return n > 0 ? n : 1;
@@ -405,8 +504,8 @@ int stream2_ctas_per_sm(int nx) {
 cudaError_t launch_detect2(int variant, const Field &F, const Blocking &B, const Workspace &W, cudaStream_t s,
                            bool capturing) {
     const bool exact = variant == VAR_STREAM2_EXACT;
-    const size_t smem = stream2_smem_bytes(F.pitch);
-    const void *k = exact ? stream2_kernel<true>(F.pitch) : stream2_kernel<false>(F.pitch);
+    const size_t smem = stream2_smem_bytes(F.pitch, F.comps);
+    const void *k = exact ? stream2_kernel<true>(F.pitch, F.comps) : stream2_kernel<false>(F.pitch, F.comps);
     // the cap only ever grows: a graph may replay a wider field's launch
     // after a narrower one was configured
     const cudaError_t e = raise_smem_cap(k, smem, capturing);

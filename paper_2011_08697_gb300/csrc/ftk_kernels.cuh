@@ -159,11 +159,12 @@ inline int exact_variant(int v) {
 constexpr float RANGE_LIMIT = 268435456.0f;   // 2^28: the exact quantisation's range of |f 2^S|
 constexpr int STREAM2_ROWS = 16;      // cube rows per unit of the streaming kernel
 constexpr int STREAM2_MAX_NX = 4096;  // widest row the streaming kernel takes
+constexpr int STREAM2_VEC_MAX_NX = 2048;   // widest row of vectors it takes
 
 size_t detect_smem_bytes(int ndim, const Field &F, const Blocking &B);
-size_t stream2_smem_bytes(int nx);
+size_t stream2_smem_bytes(int nx, int comps = 1);
 int stream2_threads(int nx);
-int stream2_ctas_per_sm(int nx);
+int stream2_ctas_per_sm(int nx, int comps = 1);
 // words of incremental detect state of a 2D streaming plan (0 if it has none)
 long long stream2_state_words(const Field &F, const Blocking &B);
 // 3D streaming kernel: smem per CTA for B.ry, B.rz, B.ns; threads; resident

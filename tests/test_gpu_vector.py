@@ -66,6 +66,11 @@ CASES = [
     ("nt1_9x7", lambda: _levels((1, 7, 9, 2), 9), 20),
     ("zero", lambda: np.zeros((3, 8, 9, 2), np.float32), 20),
     ("noise_33x31x6", lambda: np.random.default_rng(10).standard_normal((6, 31, 33, 2)).astype(np.float32), 20),
+    # rows of nx % 4 == 0 vertices (up to 2048) take the streaming kernel in
+    # vector mode: a thread of 4 columns, ragged unit rows, 320-thread CTAs
+    ("stream_levels_36x21x4", lambda: _levels((4, 21, 36, 2), 13), 20),
+    ("stream_levels5_12x35x3", lambda: _levels((3, 35, 12, 2), 14, (-1, -.5, 0, .5, 1)), 20),
+    ("stream_vortex_2048x8x3", lambda: synth.vortex_street(2048, 8, 3, nvort=12, nsrc=6, seed=15), 20),
     # rows wider than one detect tile: windows of the row, one row per unit
     ("levels_wide_1700x3x3", lambda: _levels((3, 3, 1700, 2), 11), 20),
     ("vortex_wide_3500x6x4", lambda: synth.vortex_street(3500, 6, 4, nvort=30, nsrc=12, seed=12), 20),
@@ -84,6 +89,17 @@ def test_host_input_and_capacity_growth(F):
     assert len(ref["face_id"]) > 64
     compare_full(_gpu(F, v, host=True), ref)
     compare_full(_gpu(F, v, max_punctures=16), ref)
+
+
+def test_unaligned_device_pointer(F):
+    """Rows of vectors are copied by bulk copies that need 16-byte aligned
+    starts: a view one float into a buffer is tracked from an aligned copy."""
+    v = synth.vortex_street(96, 64, 10, seed=11)
+    buf = torch.empty(v.size + 1, dtype=torch.float32, device="cuda")
+    x = buf[1:].view(v.shape)
+    x.copy_(torch.from_numpy(v))
+    assert x.data_ptr() % 16 != 0
+    compare_full(F.ftk_track_vec2d(x, F.make_params()), cp.track_vec(v))
 
 
 def test_gradient_as_vectors_equals_scalar(F):
