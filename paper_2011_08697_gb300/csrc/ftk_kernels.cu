@@ -2265,10 +2265,11 @@ __global__ void __launch_bounds__(NT) k_traj_root_sizes(Workspace W, const int *
 
 // one thread per trajectory (at its root): walk the path from its smallest
 // end (a loop: from the root, towards its smaller neighbour) and write the
-// punctures' records in path order
+// punctures in path order with their trajectory number (the dependent chain
+// is the neighbour loads alone; k_traj_gather copies the records after)
 __global__ void __launch_bounds__(NT) k_traj_walk(Workspace W, const int *nbr, const int *root, const int *size,
                                                    const int *start, const long long *off, const long long *tidx,
-                                                   int *order, long long *toff, uint8_t *closed, ftk_cp *rec) {
+                                                   int *order, long long *toff, uint8_t *closed, int *tpt) {
     const long long P = W.ctr->punctures;
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
         if (root[i] != (int)i) continue;
@@ -2282,7 +2283,7 @@ __global__ void __launch_bounds__(NT) k_traj_walk(Workspace W, const int *nbr, c
         int j = 0;
         for (; j < n && cur >= 0; ++j) {
             order[o + j] = cur;
-            rec[o + j] = W.packed[cur];
+            tpt[o + j] = (int)t;
             const int a = nbr[2 * cur], b = nbr[2 * cur + 1];
             const int next = a >= 0 && a != prev ? a : (b != prev ? b : -1);
             prev = cur;
@@ -2293,21 +2294,58 @@ __global__ void __launch_bounds__(NT) k_traj_walk(Workspace W, const int *nbr, c
     }
 }
 
+// the records in trajectory, then path order
+__global__ void __launch_bounds__(NT) k_traj_gather(Workspace W, const int *order, ftk_cp *rec) {
+    const long long P = W.ctr->punctures;
+    for (long long k = blockIdx.x * (long long)NT + threadIdx.x; k < P; k += (long long)gridDim.x * NT)
+        rec[k] = W.packed[order[k]];
+}
+
+// time (grid units) of a puncture record
+__device__ __forceinline__ double rec_t(const ftk_cp &r) { return (double)r.base[3] + (double)r.off[3]; }
+__device__ __forceinline__ double rec_c(const ftk_cp &r, int a) { return (double)r.base[a] + (double)r.off[a]; }
+
+// a double as an unsigned key of the same order (sign bit set: every bit
+// flipped; else the sign bit set)
+__device__ __forceinline__ unsigned long long order_key(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : u | 0x8000000000000000ull;
+}
+__device__ __forceinline__ double key_value(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? k & 0x7fffffffffffffffull : ~k));
+}
+
+// extents preset: smallest key = the largest key, largest = the smallest
+__global__ void __launch_bounds__(NT) k_traj_ext_init(unsigned long long *ext, long long ntraj) {
+    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < ntraj; t += (long long)gridDim.x * NT) {
+        ext[2 * t] = ~0ull;
+        ext[2 * t + 1] = 0ull;
+    }
+}
+
+// per point: its trajectory's smallest and largest point time (keys, ext[2t]
+// and ext[2t + 1], preset to the largest and smallest key)
+__global__ void __launch_bounds__(NT) k_traj_extent(const ftk_cp *rec, const int *tpt, long long P,
+                                                     unsigned long long *ext) {
+    for (long long k = blockIdx.x * (long long)NT + threadIdx.x; k < P; k += (long long)gridDim.x * NT) {
+        const unsigned long long key = order_key(rec_t(rec[k]));
+        const long long t = tpt[k];
+        atomicMin(&ext[2 * t], key);
+        atomicMax(&ext[2 * t + 1], key);
+    }
+}
+
 // Post-processing of the trajectories (paper Sec. 4.2, filtering and type
 // smoothing).  Per trajectory: kept iff its time extent (largest minus
 // smallest point time) is at least min_duration, it has at least min_points
 // points and it is not a loop when loops are dropped.
-__global__ void __launch_bounds__(NT) k_traj_keep(const ftk_cp *rec, const long long *toff, const uint8_t *closed,
-                                                   long long ntraj, double min_duration, long long min_points,
-                                                   int drop_loops, int *kept_size, int *kept_one) {
+__global__ void __launch_bounds__(NT) k_traj_keep(const unsigned long long *ext, const long long *toff,
+                                                   const uint8_t *closed, long long ntraj, double min_duration,
+                                                   long long min_points, int drop_loops, int *kept_size,
+                                                   int *kept_one) {
     for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < ntraj; t += (long long)gridDim.x * NT) {
-        const long long a0 = toff[t], n = toff[t + 1] - a0;
-        double lo = 1e300, hi = -1e300;
-        for (long long j = 0; j < n; ++j) {
-            const double tt = (double)rec[a0 + j].base[3] + (double)rec[a0 + j].off[3];
-            lo = tt < lo ? tt : lo;
-            hi = tt > hi ? tt : hi;
-        }
+        const long long n = toff[t + 1] - toff[t];
+        const double lo = key_value(ext[2 * t]), hi = key_value(ext[2 * t + 1]);
         const bool keep = n >= min_points && hi - lo >= min_duration && !(drop_loops && closed[t]);
         kept_size[t] = keep ? (int)n : 0;
         kept_one[t] = keep ? 1 : 0;
@@ -2321,17 +2359,20 @@ __global__ void __launch_bounds__(NT) k_traj_keep(const ftk_cp *rec, const long 
 // neighbours on a side keep theirs).  Every decision reads the original
 // indices.
 __global__ void __launch_bounds__(NT) k_traj_compact(const ftk_cp *rec, const long long *toff, const uint8_t *closed,
-                                                      long long ntraj, int h, const long long *noff,
+                                                      const int *tpt, long long P, int h, const long long *noff,
                                                       const long long *nidx, const int *kept_one, ftk_cp *out,
                                                       long long *out_off, uint8_t *out_closed) {
-    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < ntraj; t += (long long)gridDim.x * NT) {
+    for (long long pk = blockIdx.x * (long long)NT + threadIdx.x; pk < P; pk += (long long)gridDim.x * NT) {
+        const int t = tpt[pk];
         if (!kept_one[t]) continue;
         const long long a0 = toff[t], n = toff[t + 1] - a0;
-        const long long o = noff[t], k = nidx[t];
-        out_off[k] = o;
-        out_closed[k] = closed[t];
+        const long long o = noff[t], j = pk - a0;
+        if (j == 0) {
+            out_off[nidx[t]] = o;
+            out_closed[nidx[t]] = closed[t];
+        }
         const bool loop = closed[t] != 0;
-        for (long long j = 0; j < n; ++j) {
+        {
             ftk_cp r = rec[a0 + j];
             if (h > 0 && (loop ? n > 2 * (long long)h : (j >= h && j + h < n))) {
                 const long long jm = (j - 1 + n) % n;
@@ -2348,38 +2389,36 @@ __global__ void __launch_bounds__(NT) k_traj_compact(const ftk_cp *rec, const lo
     }
 }
 
-// time (grid units) of a puncture record
-__device__ __forceinline__ double rec_t(const ftk_cp &r) { return (double)r.base[3] + (double)r.off[3]; }
-__device__ __forceinline__ double rec_c(const ftk_cp &r, int a) { return (double)r.base[a] + (double)r.off[a]; }
-
-// segments of trajectory t (consecutive points in path order, and the
-// closing segment of a loop) that cross time t0: t_a <= t0 < t_b or
-// t_b <= t0 < t_a.  Pass 1 counts per trajectory; pass 2 writes the crossing
-// points, interpolated linearly in time along the segment.
+// segments (consecutive points in path order, and the closing segment of a
+// loop) that cross time t0: t_a <= t0 < t_b or t_b <= t0 < t_a, one thread
+// per segment, named by its first point k in record order.  Pass 1 flags
+// the crossing segments; pass 2 writes the crossing points at the flags'
+// scan (so in trajectory, then path order), interpolated linearly in time
+// along the segment.
 __global__ void __launch_bounds__(NT) k_traj_slice(const ftk_cp *rec, const long long *toff, const uint8_t *closed,
-                                                    long long ntraj, double t0, int *cnt, const long long *soff,
-                                                    ftk_slice_point *pts) {
-    for (long long t = blockIdx.x * (long long)NT + threadIdx.x; t < ntraj; t += (long long)gridDim.x * NT) {
-        const long long a0 = toff[t], n = toff[t + 1] - a0;
+                                                    const int *tpt, long long P, double t0, int *cnt,
+                                                    const long long *soff, ftk_slice_point *pts) {
+    for (long long k = blockIdx.x * (long long)NT + threadIdx.x; k < P; k += (long long)gridDim.x * NT) {
+        const int t = tpt[k];
+        const long long a0 = toff[t], n = toff[t + 1] - a0, j = k - a0;
         const long long nseg = closed[t] ? n : n - 1;
-        int c = 0;
-        long long w = pts ? soff[t] : 0;
-        for (long long j = 0; j < nseg; ++j) {
-            const ftk_cp &A = rec[a0 + j];
-            const ftk_cp &B = rec[a0 + (j + 1 == n ? 0 : j + 1)];
+        bool hit = false;
+        if (j < nseg) {
+            const ftk_cp &A = rec[k];
+            const ftk_cp &B = rec[j + 1 == n ? a0 : k + 1];
             const double ta = rec_t(A), tb = rec_t(B);
-            if (!((ta <= t0 && t0 < tb) || (tb <= t0 && t0 < ta))) continue;
-            ++c;
-            if (!pts) continue;
-            const double s = (t0 - ta) / (tb - ta);
-            ftk_slice_point p;
-            p.label = A.label;
-            p.face_a = A.face_id < B.face_id ? A.face_id : B.face_id;
-            p.face_b = A.face_id < B.face_id ? B.face_id : A.face_id;
-            for (int a = 0; a < 3; ++a) p.pos[a] = rec_c(A, a) + s * (rec_c(B, a) - rec_c(A, a));
-            pts[w++] = p;
+            hit = (ta <= t0 && t0 < tb) || (tb <= t0 && t0 < ta);
+            if (hit && pts) {
+                const double s = (t0 - ta) / (tb - ta);
+                ftk_slice_point p;
+                p.label = A.label;
+                p.face_a = A.face_id < B.face_id ? A.face_id : B.face_id;
+                p.face_b = A.face_id < B.face_id ? B.face_id : A.face_id;
+                for (int a = 0; a < 3; ++a) p.pos[a] = rec_c(A, a) + s * (rec_c(B, a) - rec_c(A, a));
+                pts[soff[k]] = p;
+            }
         }
-        if (!pts) cnt[t] = c;
+        if (!pts) cnt[k] = hit ? 1 : 0;
     }
 }
 
@@ -2407,16 +2446,17 @@ cudaError_t launch_trajectories(int ndim, const Field &F, const Workspace &W, lo
 
 cudaError_t launch_traj_walk(const Workspace &W, long long P, long long ntraj, const TrajBuffers &T, cudaStream_t s) {
     k_traj_walk<<<sparse_grid(), NT, 0, s>>>(W, T.nbr, T.root, T.size, T.start, T.off, T.tidx, T.order, T.toff,
-                                             T.closed, T.rec);
+                                             T.closed, T.tpt);
+    k_traj_gather<<<resident_grid<k_traj_gather>(), NT, 0, s>>>(W, T.order, T.rec);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(T.toff + ntraj, T.off + P, sizeof(long long), cudaMemcpyDeviceToDevice, s);
 }
 
-cudaError_t launch_traj_slice(const TrajBuffers &T, long long ntraj, double t0, int *cnt, long long *soff,
+cudaError_t launch_traj_slice(const TrajBuffers &T, long long P, double t0, int *cnt, long long *soff,
                               ftk_slice_point *pts, cudaStream_t s) {
-    k_traj_slice<<<sparse_grid(), NT, 0, s>>>(T.rec, T.toff, T.closed, ntraj, t0, cnt, soff, pts);
-    if (!pts) k_scan_one_block<<<1, NT, 0, s>>>(cnt, ntraj, soff);
+    k_traj_slice<<<resident_grid<k_traj_slice>(), NT, 0, s>>>(T.rec, T.toff, T.closed, T.tpt, P, t0, cnt, soff, pts);
+    if (!pts) k_scan_one_block<<<1, NT, 0, s>>>(cnt, P, soff);
     return cudaGetLastError();
 }
 
@@ -2437,21 +2477,23 @@ int uf_limit() { return g_host_uf_limit.load(); }
 
 namespace ftk {
 
-cudaError_t launch_traj_filter(const TrajBuffers &T, long long ntraj, double min_duration, long long min_points,
-                               int drop_loops, int h, int *kept_size, int *kept_one, long long *noff,
-                               long long *nidx, cudaStream_t s) {
-    k_traj_keep<<<sparse_grid(), NT, 0, s>>>(T.rec, T.toff, T.closed, ntraj, min_duration, min_points, drop_loops,
+cudaError_t launch_traj_filter(const TrajBuffers &T, long long P, long long ntraj, double min_duration,
+                               long long min_points, int drop_loops, int h, unsigned long long *ext, int *kept_size,
+                               int *kept_one, long long *noff, long long *nidx, cudaStream_t s) {
+    k_traj_ext_init<<<sparse_grid(), NT, 0, s>>>(ext, ntraj);
+    k_traj_extent<<<resident_grid<k_traj_extent>(), NT, 0, s>>>(T.rec, T.tpt, P, ext);
+    k_traj_keep<<<sparse_grid(), NT, 0, s>>>(ext, T.toff, T.closed, ntraj, min_duration, min_points, drop_loops,
                                              kept_size, kept_one);
     k_scan_one_block<<<1, NT, 0, s>>>(kept_size, ntraj, noff);
     k_scan_one_block<<<1, NT, 0, s>>>(kept_one, ntraj, nidx);
     return cudaGetLastError();
 }
 
-cudaError_t launch_traj_compact(const TrajBuffers &T, long long ntraj, int h, const long long *noff,
+cudaError_t launch_traj_compact(const TrajBuffers &T, long long P, int h, const long long *noff,
                                 const long long *nidx, const int *kept_one, ftk_cp *out, long long *out_off,
                                 uint8_t *out_closed, cudaStream_t s) {
-    k_traj_compact<<<sparse_grid(), NT, 0, s>>>(T.rec, T.toff, T.closed, ntraj, h, noff, nidx, kept_one, out, out_off,
-                                                out_closed);
+    k_traj_compact<<<resident_grid<k_traj_compact>(), NT, 0, s>>>(T.rec, T.toff, T.closed, T.tpt, P, h, noff, nidx,
+                                                                  kept_one, out, out_off, out_closed);
     return cudaGetLastError();
 }
 

@@ -263,15 +263,17 @@ struct TrajBuffers {
     ftk_cp *rec;         // [P] their records
     long long *toff;     // [ntraj + 1] first point of each trajectory
     uint8_t *closed;     // [ntraj] 1 for a loop
+    int *tpt;            // [P] trajectory of each point (record order)
 };
 // edges, roots, sizes and the scans; *ntraj (host) after a synchronisation
 cudaError_t launch_trajectories(int ndim, const Field &F, const Workspace &W, long long P, const TrajBuffers &T,
                                 cudaStream_t s, long long *ntraj);
-// the walk: order, records, toff, closed
+// the walk: order, trajectory of each point, records, toff, closed
 cudaError_t launch_traj_walk(const Workspace &W, long long P, long long ntraj, const TrajBuffers &T, cudaStream_t s);
-// pts == nullptr: counts per trajectory into cnt and their scan into soff
-// (soff[ntraj] = total); else the crossing points at soff
-cudaError_t launch_traj_slice(const TrajBuffers &T, long long ntraj, double t0, int *cnt, long long *soff,
+// pts == nullptr: crossing flags per segment (named by its first point) into
+// cnt[P] and their scan into soff (soff[P] = total); else the crossing
+// points at soff
+cudaError_t launch_traj_slice(const TrajBuffers &T, long long P, double t0, int *cnt, long long *soff,
                               ftk_slice_point *pts, cudaStream_t s);
 
 // bounds of the union-find loops and the look-back waits on the current
@@ -283,10 +285,11 @@ int uf_limit();
 // filtering: kept sizes / flags per trajectory and their scans (noff[ntraj],
 // nidx[ntraj] = totals); compaction of the kept trajectories with type
 // smoothing of half-window h
-cudaError_t launch_traj_filter(const TrajBuffers &T, long long ntraj, double min_duration, long long min_points,
-                               int drop_loops, int h, int *kept_size, int *kept_one, long long *noff,
-                               long long *nidx, cudaStream_t s);
-cudaError_t launch_traj_compact(const TrajBuffers &T, long long ntraj, int h, const long long *noff,
+// (ext: [2 ntraj] scratch for the time extents)
+cudaError_t launch_traj_filter(const TrajBuffers &T, long long P, long long ntraj, double min_duration,
+                               long long min_points, int drop_loops, int h, unsigned long long *ext, int *kept_size,
+                               int *kept_one, long long *noff, long long *nidx, cudaStream_t s);
+cudaError_t launch_traj_compact(const TrajBuffers &T, long long P, int h, const long long *noff,
                                 const long long *nidx, const int *kept_one, ftk_cp *out, long long *out_off,
                                 uint8_t *out_closed, cudaStream_t s);
 

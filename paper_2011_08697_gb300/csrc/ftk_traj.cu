@@ -31,7 +31,7 @@ void ftk::free_traj(ftk_plan *pl) {
     TrajBuffers &T = pl->traj;
     cudaFree(T.nbr); cudaFree(T.root); cudaFree(T.size); cudaFree(T.start); cudaFree(T.rsize);
     cudaFree(T.isroot); cudaFree(T.off); cudaFree(T.tidx); cudaFree(T.order); cudaFree(T.rec);
-    cudaFree(T.toff); cudaFree(T.closed);
+    cudaFree(T.toff); cudaFree(T.closed); cudaFree(T.tpt);
     std::memset(&T, 0, sizeof(T));
     pl->traj_cap = 0;
     pl->traj_valid = false;
@@ -51,7 +51,7 @@ ftk_status alloc_traj(ftk_plan *pl, long long P) {
         cudaMalloc(&T.tidx, sizeof(long long) * (c + 1)) != cudaSuccess ||
         cudaMalloc(&T.order, sizeof(int) * c) != cudaSuccess || cudaMalloc(&T.rec, sizeof(ftk_cp) * c) != cudaSuccess ||
         cudaMalloc(&T.toff, sizeof(long long) * (c + 1)) != cudaSuccess ||
-        cudaMalloc(&T.closed, sizeof(uint8_t) * c) != cudaSuccess) {
+        cudaMalloc(&T.closed, sizeof(uint8_t) * c) != cudaSuccess || cudaMalloc(&T.tpt, sizeof(int) * c) != cudaSuccess) {
         cudaGetLastError();
         free_traj(pl);
         return fail(FTK_ERR_NOMEM, "device allocation of the trajectory buffers failed");
@@ -147,6 +147,7 @@ ftk_status ftk_plan_trajectories_filtered(ftk_plan *pl, const ftk_traj_filter *f
     tr->pts = nullptr;
     tr->closed = nullptr;
     int *ksize = nullptr, *kone = nullptr;
+    unsigned long long *ext = nullptr;
     long long *noff = nullptr, *nidx = nullptr, *d_off = nullptr;
     ftk_cp *d_pts = nullptr;
     uint8_t *d_closed = nullptr;
@@ -155,13 +156,14 @@ ftk_status ftk_plan_trajectories_filtered(ftk_plan *pl, const ftk_traj_filter *f
     cudaStream_t st = pl->stream;
     const size_t nn = (size_t)std::max<long long>(1, n);
     if (cudaMalloc(&ksize, sizeof(int) * nn) != cudaSuccess || cudaMalloc(&kone, sizeof(int) * nn) != cudaSuccess ||
+        cudaMalloc(&ext, sizeof(unsigned long long) * 2 * nn) != cudaSuccess ||
         cudaMalloc(&noff, sizeof(long long) * (nn + 1)) != cudaSuccess ||
         cudaMalloc(&nidx, sizeof(long long) * (nn + 1)) != cudaSuccess) {
         cudaGetLastError();
         s = fail(FTK_ERR_NOMEM, "device allocation failed");
     } else if (n > 0) {
-        if ((e = launch_traj_filter(pl->traj, n, flt->min_duration, flt->min_points, flt->drop_loops,
-                                    flt->smooth_half_window, ksize, kone, noff, nidx, st)) != cudaSuccess ||
+        if ((e = launch_traj_filter(pl->traj, P, n, flt->min_duration, flt->min_points, flt->drop_loops,
+                                    flt->smooth_half_window, ext, ksize, kone, noff, nidx, st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(&tot[0], noff + n, sizeof(long long), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(&tot[1], nidx + n, sizeof(long long), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess) {
@@ -171,7 +173,7 @@ ftk_status ftk_plan_trajectories_filtered(ftk_plan *pl, const ftk_traj_filter *f
                    cudaMalloc(&d_closed, (size_t)std::max<long long>(1, tot[1])) != cudaSuccess) {
             cudaGetLastError();
             s = fail(FTK_ERR_NOMEM, "device allocation failed");
-        } else if ((e = launch_traj_compact(pl->traj, n, flt->smooth_half_window, noff, nidx, kone, d_pts, d_off,
+        } else if ((e = launch_traj_compact(pl->traj, P, flt->smooth_half_window, noff, nidx, kone, d_pts, d_off,
                                             d_closed, st)) != cudaSuccess ||
                    (e = cudaStreamSynchronize(st)) != cudaSuccess) {
             s = cuda_fail(e, "trajectory compaction");
@@ -194,7 +196,7 @@ ftk_status ftk_plan_trajectories_filtered(ftk_plan *pl, const ftk_traj_filter *f
                 s = cuda_fail(e, "filtered trajectory download");
         }
     }
-    cudaFree(ksize); cudaFree(kone); cudaFree(noff); cudaFree(nidx);
+    cudaFree(ksize); cudaFree(kone); cudaFree(ext); cudaFree(noff); cudaFree(nidx);
     cudaFree(d_pts); cudaFree(d_off); cudaFree(d_closed);
     if (s != FTK_OK) {
         ftk_traj_free(tr);
@@ -235,12 +237,13 @@ ftk_status ftk_plan_slice(ftk_plan *pl, double t, ftk_slice **out) {
     cudaError_t e = cudaSuccess;
     cudaStream_t st = pl->stream;
     if (n > 0) {
-        if (cudaMalloc(&cnt, sizeof(int) * (size_t)n) != cudaSuccess ||
-            cudaMalloc(&soff, sizeof(long long) * (size_t)(n + 1)) != cudaSuccess) {
+        // one crossing flag per segment, named by its first point
+        if (cudaMalloc(&cnt, sizeof(int) * (size_t)P) != cudaSuccess ||
+            cudaMalloc(&soff, sizeof(long long) * (size_t)(P + 1)) != cudaSuccess) {
             cudaGetLastError();
             s = fail(FTK_ERR_NOMEM, "device allocation failed");
-        } else if ((e = launch_traj_slice(pl->traj, n, t, cnt, soff, nullptr, st)) != cudaSuccess ||
-                   (e = cudaMemcpyAsync(&total, soff + n, sizeof(long long), cudaMemcpyDeviceToHost, st)) !=
+        } else if ((e = launch_traj_slice(pl->traj, P, t, cnt, soff, nullptr, st)) != cudaSuccess ||
+                   (e = cudaMemcpyAsync(&total, soff + P, sizeof(long long), cudaMemcpyDeviceToHost, st)) !=
                        cudaSuccess ||
                    (e = cudaStreamSynchronize(st)) != cudaSuccess) {
             s = cuda_fail(e, "slice count");
@@ -248,7 +251,7 @@ ftk_status ftk_plan_slice(ftk_plan *pl, double t, ftk_slice **out) {
             if (cudaMalloc(&d_pts, sizeof(ftk_slice_point) * (size_t)total) != cudaSuccess) {
                 cudaGetLastError();
                 s = fail(FTK_ERR_NOMEM, "device allocation failed");
-            } else if ((e = launch_traj_slice(pl->traj, n, t, cnt, soff, d_pts, st)) != cudaSuccess ||
+            } else if ((e = launch_traj_slice(pl->traj, P, t, cnt, soff, d_pts, st)) != cudaSuccess ||
                        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
                 s = cuda_fail(e, "slice points");
             }
