@@ -2234,63 +2234,163 @@ __global__ void __launch_bounds__(NT) k_traj_roots(Workspace W, const int *nbr, 
     }
 }
 
-// exclusive scan of v[0..n) into out[0..n], out[n] = total, by one block of
-// NT threads: each thread sums a contiguous chunk, the block scans the sums
-__global__ void __launch_bounds__(NT) k_scan_one_block(const int *v, long long n, long long *out) {
+// Exclusive scan of v[0..n) into out[0..n], out[n] = total, in three
+// passes over SCAN_BLOCKS chunks: block sums, one block scanning the sums
+// (sums[nb] = total), and each block rescanning its chunk from its sum.
+constexpr int SCAN_BLOCKS = 1024;
+__global__ void __launch_bounds__(NT) k_scan_sums(const int *v, long long n, long long per, long long *sums) {
     __shared__ long long red[NT / 32 + 1];
-    const long long per = (n + NT - 1) / NT;
-    const long long a = threadIdx.x * per, b = min(n, a + per);
+    const long long a = blockIdx.x * per, b = min(n, a + per);
     long long loc = 0;
-    for (long long i = a; i < b; ++i) loc += v[i];
+    for (long long i = a + threadIdx.x; i < b; i += NT) loc += v[i];
     long long tot;
-    long long ex = block_excl_scan<long long>(loc, red, tot);
-    for (long long i = a; i < b; ++i) {
-        out[i] = ex;
-        ex += v[i];
+    block_excl_scan<long long>(loc, red, tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+__global__ void __launch_bounds__(NT) k_scan_top(long long *sums, int nb) {
+    __shared__ long long red[NT / 32 + 1];
+    constexpr int PER = SCAN_BLOCKS / NT;
+    long long loc[PER], s = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x * PER + k;
+        loc[k] = i < nb ? sums[i] : 0;
+        s += loc[k];
     }
-    if (threadIdx.x == 0) out[n] = tot;
+    long long tot;
+    long long ex = block_excl_scan<long long>(s, red, tot);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x * PER + k;
+        if (i < nb) sums[i] = ex;
+        ex += loc[k];
+    }
+    if (threadIdx.x == 0) sums[nb] = tot;
+}
+__global__ void __launch_bounds__(NT) k_scan_apply(const int *v, long long n, long long per, const long long *sums,
+                                                    int nb, long long *out) {
+    __shared__ long long red[NT / 32 + 1];
+    const long long a = blockIdx.x * per, b = min(n, a + per);
+    long long run = sums[blockIdx.x];
+    for (long long i0 = a; i0 < b; i0 += NT) {
+        const long long i = i0 + threadIdx.x;
+        const long long x = i < b ? v[i] : 0;
+        long long tot;
+        const long long ex = block_excl_scan<long long>(x, red, tot);
+        if (i < b) out[i] = run + ex;
+        run += tot;
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = sums[nb];
+}
+
+// the three passes (sums: SCAN_BLOCKS + 1 scratch values)
+static void scan_ints(const int *v, long long n, long long *out, long long *sums, cudaStream_t s) {
+    const long long nb = std::max<long long>(1, std::min<long long>(SCAN_BLOCKS, (n + 2047) / 2048));
+    const long long per = (n + nb - 1) / nb;
+    k_scan_sums<<<(unsigned)nb, NT, 0, s>>>(v, n, per, sums);
+    k_scan_top<<<1, NT, 0, s>>>(sums, (int)nb);
+    k_scan_apply<<<(unsigned)nb, NT, 0, s>>>(v, n, per, sums, (int)nb, out);
 }
 
 // sizes of the trajectories at their roots (0 elsewhere), for the scan of
 // the trajectories' offsets; ones at the roots for their numbering
 __global__ void __launch_bounds__(NT) k_traj_root_sizes(Workspace W, const int *root, const int *size, int *rsize,
-                                                         int *isroot) {
+                                                         int *isroot, int *maxlen) {
     const long long P = W.ctr->punctures;
+    int mx = 0;
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
         const bool r = root[i] == (int)i;
         rsize[i] = r ? size[i] : 0;
         isroot[i] = r ? 1 : 0;
+        mx = r && size[i] > mx ? size[i] : mx;
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(maxlen, mx);
+}
+
+// Ordering the points of every trajectory, all points at once (list
+// ranking by pointer jumping).  A loop is first cut open between its root
+// (smallest index) and the root's larger neighbour, so that every
+// trajectory is a path that starts at its smaller end: the order a walk
+// from that end would give (a loop: from the root towards its smaller
+// neighbour).  A state (node, prev, dist, ended) per point and direction d
+// (first step to partner d) covers 2^k steps after round k; joining it with
+// the state of the node it reached, in the direction that does not step
+// back, doubles that.  ceil(log2(longest trajectory)) rounds end every walk
+// at an end of its path; the distance to the smaller end is the rank.
+
+// partners with every loop cut open: the slot of a loop root that holds its
+// larger neighbour, and that neighbour's slot holding the root, become -1
+// (one slot each, also when two cells join the same two points)
+__global__ void __launch_bounds__(NT) k_traj_cut(Workspace W, const int *nbr, const int *root, const int *start,
+                                                  int *nb2) {
+    const long long P = W.ctr->punctures;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
+        const int a = nbr[2 * i], b = nbr[2 * i + 1];
+        int o0 = a, o1 = b;
+        if (root[i] == (int)i && start[i] == TRAJ_NO_END) {
+            // i is a loop root: cut its larger neighbour (slot 1: sorted)
+            o1 = -1;
+        }
+        // a neighbour j that is a loop root with i as its larger neighbour
+        if (b >= 0 && o1 >= 0 && root[b] == b && start[b] == TRAJ_NO_END && nbr[2 * b + 1] == (int)i) o1 = -1;
+        else if (a >= 0 && root[a] == a && start[a] == TRAJ_NO_END && nbr[2 * a + 1] == (int)i) o0 = -1;
+        nb2[2 * i] = o0;
+        nb2[2 * i + 1] = o1;
     }
 }
 
-// one thread per trajectory (at its root): walk the path from its smallest
-// end (a loop: from the root, towards its smaller neighbour) and write the
-// punctures in path order with their trajectory number (the dependent chain
-// is the neighbour loads alone; k_traj_gather copies the records after)
-__global__ void __launch_bounds__(NT) k_traj_walk(Workspace W, const int *nbr, const int *root, const int *size,
-                                                   const int *start, const long long *off, const long long *tidx,
-                                                   int *order, long long *toff, uint8_t *closed, int *tpt) {
+__global__ void __launch_bounds__(NT) k_traj_rank_init(Workspace W, const int *nb2, int4 *S) {
+    const long long P = W.ctr->punctures;
+    for (long long q = blockIdx.x * (long long)NT + threadIdx.x; q < 2 * P; q += (long long)gridDim.x * NT) {
+        const int i = (int)(q >> 1), j = nb2[q];
+        S[q] = j >= 0 ? make_int4(j, i, 1, 0) : make_int4(i, -1, 0, 1);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_traj_rank_step(Workspace W, const int *nb2, const int4 *Sin, int4 *Sout) {
+    const long long P = W.ctr->punctures;
+    for (long long q = blockIdx.x * (long long)NT + threadIdx.x; q < 2 * P; q += (long long)gridDim.x * NT) {
+        const int4 s = Sin[q];
+        if (s.w) {
+            Sout[q] = s;
+            continue;
+        }
+        const int y = s.x, py = s.y;
+        const int dy = nb2[2 * y] == py ? 1 : 0;     // the direction at y that does not step back
+        const int4 t = Sin[2 * (long long)y + dy];
+        Sout[q] = make_int4(t.x, t.z == 0 ? py : t.y, s.z + t.z, t.w);
+    }
+}
+
+// every point at its rank in its trajectory's range; the roots also write
+// the trajectory's offset and loop flag
+__global__ void __launch_bounds__(NT) k_traj_place(Workspace W, const int4 *S, const int *root, const int *size,
+                                                    const int *start, const long long *off, const long long *tidx,
+                                                    int *order, long long *toff, uint8_t *closed, int *tpt) {
     const long long P = W.ctr->punctures;
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < P; i += (long long)gridDim.x * NT) {
-        if (root[i] != (int)i) continue;
-        const long long t = tidx[i];
-        const long long o = off[i];
-        const int n = size[i];
-        const bool loop = start[i] == TRAJ_NO_END;
-        toff[t] = o;
-        closed[t] = loop ? 1 : 0;
-        int prev = -1, cur = loop ? (int)i : start[i];
-        int j = 0;
-        for (; j < n && cur >= 0; ++j) {
-            order[o + j] = cur;
-            tpt[o + j] = (int)t;
-            const int a = nbr[2 * cur], b = nbr[2 * cur + 1];
-            const int next = a >= 0 && a != prev ? a : (b != prev ? b : -1);
-            prev = cur;
-            cur = next;
-            if (loop && cur == (int)i) cur = -1;
+        const int4 s0 = S[2 * i], s1 = S[2 * i + 1];
+        const int r = root[i];
+        if (r < 0 || !s0.w || !s1.w) {                 // a walk that did not end: not a path
+            atomicOr(&W.ctr->status, ST_PAIRING);
+            continue;
         }
-        if (j != n) atomicOr(&W.ctr->status, ST_PAIRING);   // a path that is not one component
+        const int first = min(s0.x, s1.x);            // the path's smaller end
+        const int rank = s0.x == first ? s0.z : s1.z;
+        const long long t = tidx[r];
+        if (rank >= size[r] || s0.z + s1.z + 1 != size[r]) {   // not one path through all its points
+            atomicOr(&W.ctr->status, ST_PAIRING);
+            continue;
+        }
+        order[off[r] + rank] = (int)i;
+        tpt[off[r] + rank] = (int)t;
+        if (r == (int)i) {
+            toff[t] = off[r];
+            closed[t] = start[r] == TRAJ_NO_END ? 1 : 0;
+        }
     }
 }
 
@@ -2427,7 +2527,7 @@ __global__ void __launch_bounds__(NT) k_traj_slice(const ftk_cp *rec, const long
 namespace ftk {
 
 cudaError_t launch_trajectories(int ndim, const Field &F, const Workspace &W, long long P, const TrajBuffers &T,
-                                cudaStream_t s, long long *ntraj) {
+                                cudaStream_t s, long long *ntraj, int *maxlen) {
     const int grid = sparse_grid();
     cudaError_t e;
     if (ndim == 2) k_traj_edges<2><<<grid, NT, 0, s>>>(F, W, T.nbr);
@@ -2436,17 +2536,28 @@ cudaError_t launch_trajectories(int ndim, const Field &F, const Workspace &W, lo
     if ((e = cudaMemsetAsync(T.size, 0, sizeof(int) * P, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(T.start, 0x7f, sizeof(int) * P, s)) != cudaSuccess) return e;   // TRAJ_NO_END
     k_traj_roots<<<grid, NT, 0, s>>>(W, T.nbr, T.root, T.size, T.start);
-    k_traj_root_sizes<<<grid, NT, 0, s>>>(W, T.root, T.size, T.rsize, T.isroot);
-    k_scan_one_block<<<1, NT, 0, s>>>(T.rsize, P, T.off);
-    k_scan_one_block<<<1, NT, 0, s>>>(T.isroot, P, T.tidx);
+    if ((e = cudaMemsetAsync(T.maxlen, 0, sizeof(int), s)) != cudaSuccess) return e;
+    k_traj_root_sizes<<<grid, NT, 0, s>>>(W, T.root, T.size, T.rsize, T.isroot, T.maxlen);
+    scan_ints(T.rsize, P, T.off, T.scan, s);
+    scan_ints(T.isroot, P, T.tidx, T.scan, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(ntraj, T.tidx + P, sizeof(long long), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(maxlen, T.maxlen, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
     return cudaStreamSynchronize(s);
 }
 
-cudaError_t launch_traj_walk(const Workspace &W, long long P, long long ntraj, const TrajBuffers &T, cudaStream_t s) {
-    k_traj_walk<<<sparse_grid(), NT, 0, s>>>(W, T.nbr, T.root, T.size, T.start, T.off, T.tidx, T.order, T.toff,
-                                             T.closed, T.tpt);
+cudaError_t launch_traj_walk(const Workspace &W, long long P, long long ntraj, long long maxlen, const TrajBuffers &T,
+                             cudaStream_t s) {
+    const int g = resident_grid<k_traj_rank_step>();
+    k_traj_cut<<<g, NT, 0, s>>>(W, T.nbr, T.root, T.start, T.nb2);
+    k_traj_rank_init<<<g, NT, 0, s>>>(W, T.nb2, T.rk[0]);
+    int cur = 0;
+    for (long long span = 1; span < maxlen; span *= 2) {
+        k_traj_rank_step<<<g, NT, 0, s>>>(W, T.nb2, T.rk[cur], T.rk[cur ^ 1]);
+        cur ^= 1;
+    }
+    k_traj_place<<<g, NT, 0, s>>>(W, T.rk[cur], T.root, T.size, T.start, T.off, T.tidx, T.order, T.toff, T.closed,
+                                  T.tpt);
     k_traj_gather<<<resident_grid<k_traj_gather>(), NT, 0, s>>>(W, T.order, T.rec);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -2456,7 +2567,7 @@ cudaError_t launch_traj_walk(const Workspace &W, long long P, long long ntraj, c
 cudaError_t launch_traj_slice(const TrajBuffers &T, long long P, double t0, int *cnt, long long *soff,
                               ftk_slice_point *pts, cudaStream_t s) {
     k_traj_slice<<<resident_grid<k_traj_slice>(), NT, 0, s>>>(T.rec, T.toff, T.closed, T.tpt, P, t0, cnt, soff, pts);
-    if (!pts) k_scan_one_block<<<1, NT, 0, s>>>(cnt, P, soff);
+    if (!pts) scan_ints(cnt, P, soff, T.scan, s);
     return cudaGetLastError();
 }
 
@@ -2484,8 +2595,8 @@ cudaError_t launch_traj_filter(const TrajBuffers &T, long long P, long long ntra
     k_traj_extent<<<resident_grid<k_traj_extent>(), NT, 0, s>>>(T.rec, T.tpt, P, ext);
     k_traj_keep<<<sparse_grid(), NT, 0, s>>>(ext, T.toff, T.closed, ntraj, min_duration, min_points, drop_loops,
                                              kept_size, kept_one);
-    k_scan_one_block<<<1, NT, 0, s>>>(kept_size, ntraj, noff);
-    k_scan_one_block<<<1, NT, 0, s>>>(kept_one, ntraj, nidx);
+    scan_ints(kept_size, ntraj, noff, T.scan, s);
+    scan_ints(kept_one, ntraj, nidx, T.scan, s);
     return cudaGetLastError();
 }
 

@@ -264,12 +264,19 @@ struct TrajBuffers {
     long long *toff;     // [ntraj + 1] first point of each trajectory
     uint8_t *closed;     // [ntraj] 1 for a loop
     int *tpt;            // [P] trajectory of each point (record order)
+    int *nb2;            // [2P] partners with every loop cut open at its root
+    int4 *rk[2];         // [2P] ranking states (node, prev, dist, ended) per point and direction
+    int *maxlen;         // [1] points of the longest trajectory
+    long long *scan;     // [1025] block sums of the scans
 };
-// edges, roots, sizes and the scans; *ntraj (host) after a synchronisation
+// edges, roots, sizes and the scans; *ntraj and *maxlen (the longest
+// trajectory; host, pinned) after a synchronisation
 cudaError_t launch_trajectories(int ndim, const Field &F, const Workspace &W, long long P, const TrajBuffers &T,
-                                cudaStream_t s, long long *ntraj);
-// the walk: order, trajectory of each point, records, toff, closed
-cudaError_t launch_traj_walk(const Workspace &W, long long P, long long ntraj, const TrajBuffers &T, cudaStream_t s);
+                                cudaStream_t s, long long *ntraj, int *maxlen);
+// the path order (ranking rounds for trajectories of up to maxlen points),
+// trajectory of each point, records, toff, closed
+cudaError_t launch_traj_walk(const Workspace &W, long long P, long long ntraj, long long maxlen, const TrajBuffers &T,
+                             cudaStream_t s);
 // pts == nullptr: crossing flags per segment (named by its first point) into
 // cnt[P] and their scan into soff (soff[P] = total); else the crossing
 // points at soff

@@ -31,7 +31,8 @@ void ftk::free_traj(ftk_plan *pl) {
     TrajBuffers &T = pl->traj;
     cudaFree(T.nbr); cudaFree(T.root); cudaFree(T.size); cudaFree(T.start); cudaFree(T.rsize);
     cudaFree(T.isroot); cudaFree(T.off); cudaFree(T.tidx); cudaFree(T.order); cudaFree(T.rec);
-    cudaFree(T.toff); cudaFree(T.closed); cudaFree(T.tpt);
+    cudaFree(T.toff); cudaFree(T.closed); cudaFree(T.tpt); cudaFree(T.nb2); cudaFree(T.rk[0]); cudaFree(T.rk[1]);
+    cudaFree(T.maxlen); cudaFree(T.scan);
     std::memset(&T, 0, sizeof(T));
     pl->traj_cap = 0;
     pl->traj_valid = false;
@@ -51,7 +52,10 @@ ftk_status alloc_traj(ftk_plan *pl, long long P) {
         cudaMalloc(&T.tidx, sizeof(long long) * (c + 1)) != cudaSuccess ||
         cudaMalloc(&T.order, sizeof(int) * c) != cudaSuccess || cudaMalloc(&T.rec, sizeof(ftk_cp) * c) != cudaSuccess ||
         cudaMalloc(&T.toff, sizeof(long long) * (c + 1)) != cudaSuccess ||
-        cudaMalloc(&T.closed, sizeof(uint8_t) * c) != cudaSuccess || cudaMalloc(&T.tpt, sizeof(int) * c) != cudaSuccess) {
+        cudaMalloc(&T.closed, sizeof(uint8_t) * c) != cudaSuccess || cudaMalloc(&T.tpt, sizeof(int) * c) != cudaSuccess ||
+        cudaMalloc(&T.nb2, sizeof(int) * 2 * c) != cudaSuccess || cudaMalloc(&T.rk[0], sizeof(int4) * 2 * c) != cudaSuccess ||
+        cudaMalloc(&T.rk[1], sizeof(int4) * 2 * c) != cudaSuccess || cudaMalloc(&T.maxlen, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&T.scan, sizeof(long long) * 1025) != cudaSuccess) {
         cudaGetLastError();
         free_traj(pl);
         return fail(FTK_ERR_NOMEM, "device allocation of the trajectory buffers failed");
@@ -75,16 +79,19 @@ ftk_status build_traj(ftk_plan *pl, long long *P_out) {
         return FTK_OK;
     }
     cudaStream_t st = pl->stream;
-    long long *h_n = nullptr;
-    if (cudaMallocHost(&h_n, sizeof(long long)) != cudaSuccess) {
+    long long *h_n = nullptr;   // [0] trajectories, [1] points of the longest (as an int)
+    if (cudaMallocHost(&h_n, 2 * sizeof(long long)) != cudaSuccess) {
         cudaGetLastError();
         return fail(FTK_ERR_NOMEM, "pinned allocation failed");
     }
-    cudaError_t e = launch_trajectories(pl->ndim, pl->F, pl->W, P, pl->traj, st, h_n);
-    const long long ntraj = *h_n;
+    h_n[1] = 0;
+    cudaError_t e = launch_trajectories(pl->ndim, pl->F, pl->W, P, pl->traj, st, h_n, reinterpret_cast<int *>(h_n + 1));
+    const long long ntraj = h_n[0];
+    const long long maxlen = *reinterpret_cast<int *>(h_n + 1);
     cudaFreeHost(h_n);
     if (e != cudaSuccess) return cuda_fail(e, "trajectory kernels");
-    if ((e = launch_traj_walk(pl->W, P, ntraj, pl->traj, st)) != cudaSuccess) return cuda_fail(e, "trajectory walk");
+    if ((e = launch_traj_walk(pl->W, P, ntraj, maxlen, pl->traj, st)) != cudaSuccess)
+        return cuda_fail(e, "trajectory walk");
     unsigned status = 0;
     if ((e = cudaMemcpyAsync(&status, &pl->W.ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)

@@ -230,6 +230,19 @@ class _ResultOwner:
             pass
 
 
+class _TrajOwner:
+    """Frees an ftk_traj when the array viewing its points is released."""
+
+    def __init__(self, h):
+        self.h = h
+
+    def __del__(self):
+        try:
+            lib().ftk_traj_free(self.h)
+        except Exception:
+            pass
+
+
 def _take_result(rp) -> np.ndarray:
     """A structured array viewing the result's records in place (no copy);
     the result is freed with the last reference to the array."""
@@ -357,21 +370,24 @@ class Plan:
             flt = ftk_traj_filter(float(min_duration or 0.0), int(min_points), int(bool(drop_loops)),
                                   int(smooth_half_window))
             _check(L.ftk_plan_trajectories_filtered(self._h, ctypes.byref(flt), ctypes.byref(h)))
-        try:
-            n = L.ftk_traj_count(h)
-            off = np.ctypeslib.as_array(ctypes.cast(L.ftk_traj_offsets(h), ctypes.POINTER(ctypes.c_int64)),
-                                        (n + 1,)).copy()
-            P = int(off[-1])
-            pts = np.empty(P, dtype=CP_DTYPE)
-            if P:
-                ctypes.memmove(pts.ctypes.data, L.ftk_traj_points(h), P * CP_DTYPE.itemsize)
-            closed = np.zeros(n, dtype=bool)
-            if n:
-                closed = np.ctypeslib.as_array(ctypes.cast(L.ftk_traj_closed(h), ctypes.POINTER(ctypes.c_uint8)),
-                                               (n,)).astype(bool)
-            return off, pts, closed
-        finally:
-            L.ftk_traj_free(h)
+        owner = _TrajOwner(h)
+        n = L.ftk_traj_count(h)
+        off = np.ctypeslib.as_array(ctypes.cast(L.ftk_traj_offsets(h), ctypes.POINTER(ctypes.c_int64)),
+                                    (n + 1,)).copy()
+        P = int(off[-1])
+        if P:
+            # the points are viewed in place (no copy); the trajectories are
+            # freed with the last reference to the array
+            raw = (ctypes.c_char * (P * CP_DTYPE.itemsize)).from_address(L.ftk_traj_points(h))
+            raw.owner = owner
+            pts = np.frombuffer(raw, dtype=CP_DTYPE)
+        else:
+            pts = np.empty(0, dtype=CP_DTYPE)
+        closed = np.zeros(n, dtype=bool)
+        if n:
+            closed = np.ctypeslib.as_array(ctypes.cast(L.ftk_traj_closed(h), ctypes.POINTER(ctypes.c_uint8)),
+                                           (n,)).astype(bool)
+        return off, pts, closed
 
     def slice(self, t: float) -> np.ndarray:
         """Crossings of the last execute's trajectories with time t (SLICE_DTYPE)."""
