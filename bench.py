@@ -968,7 +968,8 @@ def _measure_vec(args, dev, world):
         "types": {str(k): int(np.sum(res["morse_index"] == k)) for k in np.unique(res["morse_index"])},
         "stages_ms": st, "plan": desc,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": profiled_traffic("vortex2d", "ftk_detect2.cu", "detect_vortex2d") if streaming else None,
                      "kernel": "k_detect2_stream<vector>" if streaming else "k_detect<2> (vector mode)",
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": st["detect"],
                      "whole_step_frac": (alg_bytes / (step_mean / 1e3) / 1e9) / peak},
