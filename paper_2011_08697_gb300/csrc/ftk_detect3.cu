@@ -8,8 +8,9 @@
 //    y0-1 .. y0+ry+1 of planes z0-1 .. z0+rz+1, clamped to the grid, one
 //    contiguous bulk copy each -- into a ring of smem slots (full / empty
 //    mbarriers);
-//  * consumer warps: warp w owns 4 G rows (y) of one 128-column chunk (4
-//    columns per lane) and walks the planes of each slice in z.  Each plane
+//  * consumer warps (four; eight for rows of 513-1024 floats, one per
+//    chunk): warp w owns 4 G rows (y) of one 128-column chunk (4 columns
+//    per lane) and walks the planes of each slice in z.  Each plane
 //    chunk is read from shared memory once, right after it lands: the warp
 //    loads its 4 rows plus one halo row on each side, quantises them
 //    (F = rint(f 2^S) in a magic-number encoding, exact for |F| <= 2^22;
