@@ -75,6 +75,7 @@ void free_workspace(Workspace &W) {
     cudaFree(W.surv);
     cudaFree(W.surv_mask);
     cudaFree(W.surv_off);
+    cudaFree(W.litem);
     cudaFree(W.seg_scnt);
     cudaFree(W.seg_sstage);
     cudaFree(W.tile);
@@ -86,12 +87,14 @@ ftk_status alloc_survivors(Workspace &W, long long scap) {
     cudaFree(W.surv); W.surv = nullptr;
     cudaFree(W.surv_mask); W.surv_mask = nullptr;
     cudaFree(W.surv_off); W.surv_off = nullptr;
+    cudaFree(W.litem); W.litem = nullptr;
     cudaFree(W.tile); W.tile = nullptr;
     W.scap = 0;
     const long long ntile = (scap + LB_TILE - 1) / LB_TILE;
     if (cudaMalloc(&W.surv, scap * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&W.surv_mask, scap * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&W.surv_off, scap * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&W.litem, 3 * scap * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&W.tile, ntile * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         return fail(FTK_ERR_NOMEM, "device allocation of the survivor arrays failed");

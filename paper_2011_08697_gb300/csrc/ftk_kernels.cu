@@ -1202,13 +1202,12 @@ __device__ __forceinline__ int face_cells(const Field &F, const Pt &b, int tt) {
 // or two cells (one on the grid boundary), so the cells visited with two
 // punctured sides must number exactly half the sum of those counts.
 template <int N>
-__global__ void __launch_bounds__(NT) k_link_survivors(Field F, Blocking B, Workspace W) {
+__global__ void __launch_bounds__(NT, 6) k_link_survivors(Field F, Blocking B, Workspace W) {
     constexpr int D = N + 1;
     constexpr int FULL = (1 << D) - 1;
     constexpr int C = MeshDims<N>::C;
     __shared__ unsigned long long red[2][NT / 32];
     if (W.ctr->status & (ST_OVERFLOW | ST_SOVERFLOW)) return;
-    const long long ns = (long long)W.ctr->survivors;
     const long long P = W.ctr->punctures;
     unsigned *status = &W.ctr->status;
     unsigned long long pairs = 0, incid = 0;
@@ -1216,9 +1215,33 @@ __global__ void __launch_bounds__(NT) k_link_survivors(Field F, Blocking B, Work
     // that step first along a, all of which share the next cube along a.
     // Items are axis-major, so a warp's lanes take the same branch (a search
     // for the next cube along y, z or t; none along x).
-    for (long long it = blockIdx.x * (long long)NT + threadIdx.x; it < ns * D; it += (long long)gridDim.x * NT) {
-        const int a = (int)(it / ns);
-        const long long s = it - (long long)a * ns;
+    // 2D: the items come from the lists the survivor evaluation filled, taken
+    // one after the other (every lane of a warp holds a real item; each list
+    // holds fewer than scap <= 2^26 items).  3D (few survivors): every
+    // (survivor, axis) pair, axis-major, filtered here.
+    const long long ns = (long long)W.ctr->survivors;
+    int bnd[D];                  // 2D: bnd[a] = items in the lists up to a
+    {
+        int run = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            run += N == 2 ? (int)W.ctr->nlink[a] : 0;
+            bnd[a] = run;
+        }
+    }
+    const long long total = N == 2 ? (long long)bnd[D - 1] : ns * D;
+    for (long long it = blockIdx.x * (long long)NT + threadIdx.x; it < total; it += (long long)gridDim.x * NT) {
+        int a = 0;
+        long long s;
+        if constexpr (N == 2) {
+#pragma unroll
+            for (int q = 0; q + 1 < D; ++q) a += it >= bnd[q];
+            const int k = (int)it - (a == 0 ? 0 : a == 1 ? bnd[0] : bnd[1]);
+            s = W.litem[(long long)a * W.scap + k];
+        } else {
+            a = (int)(it / ns);
+            s = it - (long long)a * ns;
+        }
         const unsigned long long mo = W.surv_mask[s];
         if (!mo || (a != 0 && !(mo & cells<N>().own_axis[a]))) continue;
         const long long g = W.surv[s];
@@ -1372,6 +1395,30 @@ __device__ __forceinline__ void eval_faces2(const int32_t (&Gc)[8][2], int insid
     }
 }
 
+// 2D: the link items of surviving cube s with punctured-type mask m: one per
+// first-step axis a whose cells the cube owns (axis 0 whenever m != 0: its
+// item also counts the cube's face incidences), appended to list a, one
+// atomic per warp and list.  The lists' order does not matter: the unions
+// they drive end in the same partition, labelled by its smallest face ids.
+template <int N>
+__device__ __forceinline__ void push_link_items(const Workspace &W, long long s, unsigned long long m) {
+    static_assert(N == 2, "the link item lists serve the 2D pipeline");
+    constexpr int D = N + 1;
+    const unsigned am = __activemask();
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const bool want = m != 0 && (a == 0 || (m & cells<N>().own_axis[a]) != 0);
+        const unsigned b = __ballot_sync(am, want);
+        if (!b) continue;
+        const int lead = __ffs(b) - 1;
+        unsigned long long base = 0;
+        if (lane == lead) base = atomicAdd(&W.ctr->nlink[a], (unsigned long long)__popc(b));
+        base = __shfl_sync(am, base, lead);
+        if (want) W.litem[(long long)a * W.scap + (long long)base + __popc(b & ((1u << lane) - 1u))] = (int)s;
+    }
+}
+
 template <int N>
 __device__ unsigned long long eval_cube(const Field &F, long long g) {
     constexpr int D = N + 1;
@@ -1441,8 +1488,11 @@ __global__ void __launch_bounds__(NT) k_survive_eval_thread(Field F, Workspace W
     clear_scan_states(W);
     if (W.ctr->status & ST_SOVERFLOW) return;
     const long long ns = (long long)W.ctr->survivors;
-    for (long long s = blockIdx.x * (long long)NT + threadIdx.x; s < ns; s += (long long)gridDim.x * NT)
-        W.surv_mask[s] = eval_cube<N>(F, W.surv[s]);
+    for (long long s = blockIdx.x * (long long)NT + threadIdx.x; s < ns; s += (long long)gridDim.x * NT) {
+        const unsigned long long m = eval_cube<N>(F, W.surv[s]);
+        W.surv_mask[s] = m;
+        push_link_items<N>(W, s, m);
+    }
 }
 
 // 3D: two surviving cubes per warp per step (grid-stride over pairs of the

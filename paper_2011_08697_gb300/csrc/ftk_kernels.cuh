@@ -29,6 +29,7 @@ struct RunCounters {
     long long surv_total;          // punctures over every surviving cube
     unsigned long long pairs;      // cells linked (two punctured sides)
     unsigned long long incid;      // sum over punctured faces of their cell count
+    unsigned long long nlink[3];   // 2D link items per first-step axis (streaming variant)
 };
 
 // Division by a fixed divisor d for numerators n < 2^31: with
@@ -109,6 +110,8 @@ struct Workspace {
     long long *seg_sstage;          // [nseg] start of the segment's run in surv
     unsigned long long *tile;       // [scap / LB_TILE] look-back state of the survivor scan
     unsigned long long *seg_tile;   // [nseg / SEG_TILE] look-back state of the segment scan
+    int *litem;                     // [3 scap] 2D link items: list a (at a scap) holds the survivors
+                                    // with cells of first-step axis a (axis 0: every punctured one)
     long long scap;
     int uf_limit;                   // union-find bound of the label pass (set at launch; below the
                                     // default only in tests)

@@ -353,7 +353,7 @@ void release(ftk_stream *st) {
 
 // device bytes charged for a plan's workspace
 size_t plan_bytes(long long cap, long long scap, long long nseg) {
-    return (size_t)cap * (8 + 8 + 4 + 16 + 1 + 8 + sizeof(ftk_cp)) + (size_t)scap * (8 + 8 + 4) +
+    return (size_t)cap * (8 + 8 + 4 + 16 + 1 + 8 + sizeof(ftk_cp)) + (size_t)scap * (8 + 8 + 4 + 12) +
            (size_t)nseg * (4 + 8 + 8 + 4 + 8);
 }
 size_t plan_bytes(const ftk_plan *pl) { return plan_bytes(pl->W.cap, pl->W.scap, pl->W.nseg); }
