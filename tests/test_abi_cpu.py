@@ -81,3 +81,16 @@ def test_null_pointers_rejected(L):
     assert L.ftk_plan_execute(None, None, None) == 1
     assert L.ftk_plan_destroy(None) == 0
     L.ftk_result_free(None)
+
+
+@pytest.mark.parametrize("dims", [(2, 6000, 8, 1), (2, 20001, 3, 1), (3, 1030, 5, 4), (3, 4099, 3, 3),
+                                  (2, 4096, 16, 1), (3, 1024, 8, 8)])
+def test_any_row_width_is_accepted(L, dims):
+    """Rows wider than the streaming kernels take (2D: 4096 floats, 3D: 1024)
+    go to the tiled kernel, cut into x windows where a row exceeds its tile:
+    the host-side blocking accepts every width (no device work here)."""
+    p = ftk.make_params()
+    out = ctypes.c_uint64(0)
+    st = L.ftk_stream_footprint(dims[0], dims[1], dims[2], dims[3], ctypes.byref(p), ctypes.byref(out))
+    assert st == 0, L.ftk_last_error().decode()
+    assert out.value > 0
