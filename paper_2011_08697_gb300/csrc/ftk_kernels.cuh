@@ -61,7 +61,7 @@ struct Field {
     int small;           // nx*ny*nz*nt < 2^31: vertex ids decode with FastDiv
     FastDiv dx, dy, dz;  // division by nx, ny, nz
     int comps = 1;       // 2: a 2D vector field, components interleaved per vertex
-                         // (tiled path only, pitch = nx); otherwise a scalar field
+                         // (pitch = nx); otherwise a scalar field
 };
 
 // fills the FastDiv fields of a Field whose extents are set

@@ -77,3 +77,31 @@ extern "C" int shim_cell_table(int n, unsigned long long *own, int *far, int *ax
     for (int i = 0; i < ftk::MeshDims<3>::C; ++i) { own[i] = c.own[i]; far[i] = c.far[i]; axis[i] = c.axis[i]; }
     return ftk::MeshDims<3>::C;
 }
+
+// The segment of a vertex (the runs of face ids the compaction and the
+// sparse stages address by segment), with and without x windows: from the
+// vertex id (FastDiv path when small, else 64-bit division) and from its
+// coordinates.  out[0] = segment_of(g), out[1] = segment_of_coords(...),
+// out[2] = segment_count.
+#include "../paper_2011_08697_gb300/csrc/ftk_kernels.cuh"
+
+extern "C" void shim_segment(int nx, int ny, int nz, int nt, int ry, int nxb, int wx, int small, long long g,
+                             long long *out) {
+    ftk::Field F{};
+    F.nx = nx; F.ny = ny; F.nz = nz; F.nt = nt; F.pitch = nx;
+    ftk::field_divisors(F);
+    F.small = small && F.small;
+    ftk::Blocking B{};
+    B.ry = ry;
+    B.nyb = (ny + ry - 1) / ry;
+    B.nxb = nxb;
+    B.wx = wx;
+    long long r = g;
+    const int x = (int)(r % nx); r /= nx;
+    const int y = (int)(r % ny); r /= ny;
+    const int z = (int)(r % nz); r /= nz;
+    const int t = (int)r;
+    out[0] = ftk::segment_of(g, F, B);
+    out[1] = ftk::segment_of_coords(x, y, z, t, F, B);
+    out[2] = ftk::segment_count(F, B);
+}
